@@ -1,0 +1,229 @@
+/*
+ * strtr.h -- C ABI of the GB300 streaming tensor-ring (STR / rSTR) library.
+ *
+ * The library tracks the tensor-ring (TR) decomposition of a tensor that grows
+ * along its last (temporal) mode, following Yu & Li, "Tracking Tensor Ring
+ * Decompositions of Streaming Tensors": STR (Alg. 4) and rSTR (Alg. 5 with
+ * the uniform, leverage-based and KSRFT schedules of Algs. 7-9).  Every step of
+ * an update runs in this library's CUDA kernels; the caller supplies device
+ * memory and a CUDA stream.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Order N >= 3.  Modes 1..N-1 are spatial with fixed sizes I_1..I_{N-1};
+ *   mode N is time.  TR-ranks R_1..R_N, R_{N+1} = R_1, 1 <= R_n <= 16 and
+ *   R_n R_{n+1} <= 256.
+ * - Tensors are dense with the paper's linear index (Sec. 2): element
+ *   (i_1, .., i_N) sits at offset i_1 + I_1 (i_2 + I_2 (i_3 + ...)), i.e. i_1
+ *   fastest.  A torch tensor of shape (t, I_{N-1}, .., I_1) is such a buffer.
+ * - Core n is stored as the unfolding G_{n(2)} (Sec. 2, TR-ALS) in row-major
+ *   order: element G_n(r_n, i_n, r_{n+1}) at offset
+ *       i_n * R_n R_{n+1} + r_{n+1} * R_n + r_n.
+ * - Pointers are device pointers unless a field or argument says "host".
+ *   Input buffers are borrowed for the duration of the call on the given
+ *   stream; the library keeps no reference to them.  Work is enqueued on
+ *   `stream` (a cudaStream_t; NULL = the legacy default stream).
+ * - Every call returns a str_status.  STR_OK = 0.  Unless a call says
+ *   otherwise, a failing call leaves the context unchanged.
+ * - Thread safety: one context must not be used by two host threads at once.
+ */
+#ifndef STRTR_H
+#define STRTR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct str_ctx str_ctx;
+
+typedef enum {
+  STR_OK = 0,
+  STR_ERR_INVALID_ARG = 1,  /* NULL pointer, bad enum, negative size */
+  STR_ERR_SHAPE = 2,        /* order, dims or ranks outside the supported range */
+  STR_ERR_DTYPE = 3,        /* unsupported element type for this call */
+  STR_ERR_SINGULAR = 4,     /* a normal-equation matrix had a non-positive Cholesky pivot */
+  STR_ERR_NONFINITE = 5,    /* NaN/Inf found in a slab (only when check_finite is on) */
+  STR_ERR_CAPACITY = 6,     /* the temporal core would exceed t_capacity rows */
+  STR_ERR_OOM = 7,          /* device allocation failed */
+  STR_ERR_CUDA = 8,         /* a CUDA runtime call failed; see str_last_error() */
+  STR_ERR_TIMEOUT = 9,      /* a bounded device wait gave up */
+  STR_ERR_STATE = 10        /* call not valid in the context's state */
+} str_status;
+
+typedef enum { STR_BF16 = 0, STR_F32 = 1, STR_F64 = 2 } str_dtype;
+
+typedef enum {
+  STR_SKETCH_NONE = -1,     /* exact STR (Alg. 4) */
+  STR_SKETCH_UNIFORM = 0,   /* rSTR-U (Alg. 7) */
+  STR_SKETCH_LEVERAGE = 1,  /* rSTR-L (Alg. 8) */
+  STR_SKETCH_KSRFT = 2      /* rSTR-K (Alg. 9) */
+} str_sketch;
+
+/* A dense tensor in the linear layout above. */
+typedef struct {
+  const void* data;       /* element (0,..,0); 16-byte aligned recommended */
+  str_dtype dtype;        /* STR_BF16, STR_F32 or STR_F64 */
+  int order;              /* N */
+  const int64_t* dims;    /* host array of N sizes I_1..I_{N-1}, t */
+  int on_host;            /* 0 = device memory; 1 = host memory (copied in by the call) */
+} str_tensor;
+
+typedef struct {
+  /* Precision of the slab-side arithmetic (subchain products, MTTKRP,
+   * sampled products, DFT mixing): STR_F64 or STR_F32 (FP32 accumulate).
+   * Gram tensors, Q_n, P_n accumulation and every solve are FP64. */
+  str_dtype compute;
+  int sweeps;              /* >= 1; passes over each slab per update (1 = Alg. 4) */
+  int rescale;             /* rSTR: 1 = apply the sketch rescaling D (Eq. sampDS), 0 = omit it */
+  int64_t t_capacity;      /* maximum temporal rows kept in G_N (default 65536) */
+  int init_max_it;         /* str_init: TR-ALS-NE iterations (default 100, Sec. 4) */
+  double init_tol;         /* str_init: stop when |change of rel. error| < tol (default 1e-8) */
+  str_sketch sketch;       /* STR_SKETCH_NONE = STR; else the rSTR sketch fixed at init */
+  int64_t m;               /* rSTR sketch size (rows drawn per mode) */
+  uint64_t seed;           /* rSTR Philox key */
+  uint32_t stream_id;      /* rSTR Philox stream word (independent streams of draws) */
+  int check_finite;        /* 1 = scan each slab for NaN/Inf first (STR_ERR_NONFINITE) */
+  int async_status;        /* 0 = each update synchronises and returns device errors
+                            *     (state unchanged on error);
+                            * 1 = no synchronisation; device errors surface at the next
+                            *     call or str_sync() and then make the context sticky-failed */
+} str_options;
+
+/* Fills *opt with the defaults listed above (compute F64, sweeps 1, rescale 1,
+ * sketch NONE, m 1000, seed 0).  Returns STR_ERR_INVALID_ARG for NULL. */
+str_status str_default_options(str_options* opt);
+
+/*
+ * str_init -- initialisation stage of Alg. 4 / Alg. 5.
+ * Computes the initial cores of X0 by TR-ALS-NE (Alg. 2; stops per
+ * opt->init_tol / init_max_it, Sec. 4) from the host FP64 initial guess
+ * `guess` (N pointers, core n with I_n rows, the temporal one with t_init
+ * rows), then P_n = X0_[n] G^{!=n}_[2] and Q_n = (H^{!=n})_<2> (Alg. 4,
+ * lines 2-6) or their sketched forms (Alg. 5, lines 2-5, draws at tau = 0).
+ *   out    : receives the new context (owns all device state); *out = NULL on error
+ *   X0     : initial tensor I_1 x .. x I_{N-1} x t_init (device or host)
+ *   ranks  : host array R_1..R_N
+ *   guess  : host array of N host pointers to FP64 cores in the core layout
+ *   opt    : NULL = defaults
+ */
+str_status str_init(str_ctx** out, const str_tensor* X0, const int* ranks,
+                    const double* const* guess, const str_options* opt, void* stream);
+
+/*
+ * str_init_cores -- as str_init, but takes the initial cores as given (host
+ * FP64, N pointers in the core layout, the temporal core with t_init rows) and
+ * only builds P_n, Q_n from X0 (Alg. 4, lines 2-6; Alg. 5, lines 2-5).
+ * X0 may be NULL: then P_n = 0 and Q_n = 0 (no history) and t_init = the
+ * temporal core's row count `t_init`.
+ */
+str_status str_init_cores(str_ctx** out, int N, const int64_t* dims, const int* ranks,
+                          int64_t t_init, const double* const* cores, const str_tensor* X0,
+                          const str_options* opt, void* stream);
+
+/*
+ * str_update -- one time step of STR (Alg. 4, lines 8-19): the temporal core's
+ * new rows G_N^new = X^new_[N] G^{!=N}_[2] (H^{!=N}_<2>)^dagger are appended,
+ * then for n = 1..N-1: P_n += X^new_[n] (G^{!=n}_new)_[2], Q_n += (H^{!=n}_new)_<2>,
+ * G_{n(2)} = P_n Q_n^dagger.  With opt.sweeps = s > 1 the step is repeated s
+ * times from the same P_n, Q_n (each sweep recomputes G_N^new with the latest
+ * cores).  X_new: I_1 x .. x I_{N-1} x t_new, t_new >= 1, any dtype.
+ * Works on any context (also one initialised for rSTR).
+ */
+str_status str_update(str_ctx* ctx, const str_tensor* X_new, void* stream);
+
+/*
+ * rstr_update -- one time step of rSTR (Alg. 5) with the draw schedule of
+ * Alg. 7 (uniform), Alg. 8 (leverage) or Alg. 9 (KSRFT).  `type`, `m` and
+ * `seed` must equal the values the context was initialised with
+ * (STR_ERR_STATE otherwise).  Sample indices come from the Philox4x64-10
+ * contract: key (seed, 0), counter (s, k, tau, purpose<<32 | stream_id).
+ */
+str_status rstr_update(str_ctx* ctx, const str_tensor* X_new, str_sketch type, int64_t m,
+                       uint64_t seed, void* stream);
+
+/*
+ * str_update_batch -- updates `count` independent contexts with one slab each;
+ * the per-phase kernels of all contexts run as single batched launches.
+ * randomized = 0: str_update semantics; 1: rstr_update with each context's own
+ * sketch settings.  On error no context is changed (sync mode).
+ */
+str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X_new, int count,
+                            int randomized, void* stream);
+
+/*
+ * tr_reconstruct -- writes TR(G) (Sec. 1) for temporal rows [t0, t1) into `out`
+ * (device, I_1 x .. x I_{N-1} x (t1-t0), dtype STR_F32 or STR_F64).
+ */
+str_status tr_reconstruct(const str_ctx* ctx, int64_t t0, int64_t t1, void* out, str_dtype dtype,
+                          void* stream);
+
+/*
+ * tr_fit_error -- relative error ||X - TR(G)||_F / ||X||_F (Sec. 4) over the
+ * temporal rows [t0, t0 + t) that X covers, by the direct residual with FP64
+ * sums.  Synchronises the stream; *rel_err is a host double.
+ */
+str_status tr_fit_error(const str_ctx* ctx, const str_tensor* X, int64_t t0, double* rel_err,
+                        void* stream);
+
+/* Copies core n (1-based) to host FP64 in the core layout; the temporal core
+ * (n = N) has str_num_time_rows() rows.  Synchronises. */
+str_status str_get_core(const str_ctx* ctx, int n, double* host_out);
+/* Number of temporal rows currently held (t_init + all appended rows). */
+int64_t str_num_time_rows(const str_ctx* ctx);
+/* Copies P_n (I_n x R_nR_{n+1}) and Q_n (R_nR_{n+1} square), n = 1..N-1, to host FP64. */
+str_status str_get_pq(const str_ctx* ctx, int n, double* host_P, double* host_Q);
+/* rSTR: copies idxs(:,k) (m zero-based int64 indices) and, for rSTR-L, p_k
+ * (host_p may be NULL) of mode k (1-based).  Synchronises. */
+str_status str_get_samples(const str_ctx* ctx, int k, int64_t* host_idxs, double* host_p);
+
+/* Serialises the whole state (shapes, options, cores, P_n, Q_n, step counter,
+ * sample indices, leverage distributions) into `buf`.  If buf is NULL, *len
+ * receives the required size.  str_load rebuilds a context from such a buffer;
+ * updates after a load are bit-identical to an uninterrupted run. */
+str_status str_save(const str_ctx* ctx, void* buf, size_t* len);
+str_status str_load(str_ctx** out, const void* buf, size_t len, void* stream);
+
+typedef struct {
+  int64_t steps;            /* updates committed */
+  int64_t time_rows;        /* temporal rows held */
+  int64_t kernel_launches;  /* kernels launched by the last update */
+  int64_t device_bytes;     /* device memory owned by the context */
+  double min_pivot_ratio;   /* smallest L_kk^2 / Q_kk seen by the last update's solves */
+} str_stats;
+str_status str_get_stats(const str_ctx* ctx, str_stats* stats);
+
+/* Waits for the context's queued work and reports a pending device error. */
+str_status str_sync(str_ctx* ctx);
+
+const char* str_status_string(str_status s);
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char* str_last_error(void);
+void str_destroy(str_ctx* ctx);
+
+/*
+ * Masked TR fit loss (no counterpart in the paper; used for gradient-based
+ * fitting):  L = 1/2 sum_i M(i) (X(i) - TR(G)(i))^2, with M(i) = bit i of
+ * mask_bits (1 = observed; NULL = all observed), bit b of word w covering
+ * linear index 32 w + b.  Cores and X are device arrays of `dtype` (STR_F32 or
+ * STR_F64); dims has N entries (the last one is the temporal size).
+ *   tr_masked_loss_fwd writes L (FP64) to the device double *loss_dev.
+ *   tr_masked_loss_bwd writes grad_scale * dL/dG_n into grad_cores_dev[n]
+ *   (device, core layout, same dtype): dL/dG_{n(2)} = -(M .* (X - TR(G)))_[n] G^{!=n}_[2]
+ *   (with M == 1 this equals G_{n(2)} Q_n - P_n of Eq. partial).
+ * Both recompute the subchains; nothing is stored between them.
+ */
+str_status tr_masked_loss_fwd(int N, const int64_t* dims, const int* ranks, str_dtype dtype,
+                              const void* const* cores_dev, const void* X_dev,
+                              const uint32_t* mask_bits, double* loss_dev, void* stream);
+str_status tr_masked_loss_bwd(int N, const int64_t* dims, const int* ranks, str_dtype dtype,
+                              const void* const* cores_dev, const void* X_dev,
+                              const uint32_t* mask_bits, double grad_scale,
+                              void* const* grad_cores_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STRTR_H */

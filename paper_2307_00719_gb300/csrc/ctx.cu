@@ -1,0 +1,1309 @@
+// Host orchestration of STR (Alg. 4) and rSTR (Alg. 5 with Algs. 7-9) and the
+// C ABI declared in strtr.h.
+//
+// State layout (all FP64 masters, device resident):
+//   spatial core n      G64[n][b]  (I_n x R_nR_{n+1}),  b = committed / working buffer
+//   temporal core       GT64       (t_capacity x R_N R_1), rows appended per step
+//   P_n, Q_n, E_n       double-buffered like the spatial cores
+//   rSTR                idxs[k][b] (m int32), p[k][b] (leverage distributions)
+// During a step every buffer a mode writes is the working copy; the step ends
+// by flipping the committed index of every mode it updated, so a failed step
+// (sync mode) leaves the committed state untouched.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+static thread_local std::string g_last_error;
+
+void str_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  g_last_error = std::string(cudaGetErrorString(e)) + " in " + what + " (" + file + ":" +
+                 std::to_string(line) + ")";
+}
+
+namespace {
+
+constexpr uint64_t kSaveMagic = 0x31565254534C4953ull;  // save-format tag
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace
+
+struct str_ctx {
+  int dev = 0;
+  int N = 0;
+  int64_t I[STR_MAXN] = {};      // I_1..I_{N-1}; I[N-1] = current slab t
+  int R[STR_MAXN + 1] = {};      // R_1..R_N, R[N] = R_1
+  str_options opt{};
+  int compute = 2;               // 1 = FP32 slab arithmetic, 2 = FP64
+  int64_t t_rows = 0;            // committed temporal rows
+  int64_t step = 0;              // tau
+  int64_t last_tn = 0;           // temporal size of the last committed slab
+  int sticky = 0;                // async-mode failure latched
+  int cur[STR_MAXN] = {};        // committed buffer index per mode
+  int upd[STR_MAXN] = {};        // modes written in the current step
+  int64_t launches = 0;
+
+  double* G64[STR_MAXN][2] = {};
+  float* G32[STR_MAXN][2] = {};
+  double* P[STR_MAXN][2] = {};
+  double* Q[STR_MAXN][2] = {};
+  double* E[STR_MAXN][2] = {};
+  double* GT64 = nullptr;        // temporal core storage
+  float* GT32 = nullptr;
+  int32_t* idxs[STR_MAXN][2] = {};
+  double* p[STR_MAXN][2] = {};
+  int64_t p_cap[STR_MAXN] = {};
+
+  // per-step scratch
+  DevBuf partial, gnew64, gnew32, enew, mtmp, qtmp, lfac, invd, ring0, ring1, gs, ws, gram,
+      xstage, xmix0, xmix1, gmix[STR_MAXN], sgn[STR_MAXN], tab0, tab1, bsum, sums;
+  int* d_status = nullptr;
+  int* h_status = nullptr;       // pinned
+  double* d_pivot = nullptr;
+  double* h_sums = nullptr;      // pinned (2 doubles)
+  std::vector<void*> owned;
+  size_t bytes = 0;
+
+  int RR(int n) const { return R[n] * R[n + 1]; }
+  int64_t m() const { return opt.m; }
+};
+
+namespace {
+
+str_status from_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return STR_OK;
+  str_set_last_cuda_error(e, what, __FILE__, __LINE__);
+  return e == cudaErrorMemoryAllocation ? STR_ERR_OOM : STR_ERR_CUDA;
+}
+
+#define TRY(expr)                                  \
+  do {                                             \
+    str_status _s = (expr);                        \
+    if (_s != STR_OK) return _s;                   \
+  } while (0)
+#define LCH(ctx, expr)                             \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    ++(ctx)->launches;                             \
+    if (_e != cudaSuccess) return from_cuda(_e, #expr); \
+  } while (0)
+
+str_status dalloc(str_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) { *p = nullptr; cudaGetLastError(); return from_cuda(e, "cudaMalloc"); }
+  cudaMemset(*p, 0, bytes);
+  c->owned.push_back(*p);
+  c->bytes += bytes;
+  return STR_OK;
+}
+
+template <typename T> str_status dalloc_t(str_ctx* c, T** p, size_t count) {
+  void* v = nullptr;
+  TRY(dalloc(c, &v, count * sizeof(T)));
+  *p = (T*)v;
+  return STR_OK;
+}
+
+str_status grow(str_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes <= b.cap) return STR_OK;
+  if (b.p) {
+    auto it = std::find(c->owned.begin(), c->owned.end(), b.p);
+    if (it != c->owned.end()) c->owned.erase(it);
+    cudaFree(b.p);
+    c->bytes -= b.cap;
+  }
+  b.p = nullptr;
+  b.cap = 0;
+  size_t nb = std::max<size_t>(bytes, 256);
+  TRY(dalloc(c, &b.p, nb));
+  b.cap = nb;
+  return STR_OK;
+}
+
+int xtype_of(str_dtype d) { return d == STR_BF16 ? XT_BF16 : (d == STR_F32 ? XT_F32 : XT_F64); }
+size_t dsize(str_dtype d) { return d == STR_BF16 ? 2 : (d == STR_F32 ? 4 : 8); }
+
+int buf_of(const str_ctx* c, int k) { return c->upd[k] ? 1 - c->cur[k] : c->cur[k]; }
+
+// compute-type pointer of core k as currently seen in the step (k < N-1)
+const void* core_c(const str_ctx* c, int k) {
+  const int b = buf_of(c, k);
+  return c->compute == 2 ? (const void*)c->G64[k][b] : (const void*)c->G32[k][b];
+}
+const double* E_of(const str_ctx* c, int k) { return c->E[k][buf_of(c, k)]; }
+
+str_status check_status(str_ctx* c, cudaStream_t s, bool* failed) {
+  *failed = false;
+  STR_CUDA_TRY(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STR_CUDA_TRY(cudaStreamSynchronize(s));
+  const int st = *c->h_status;
+  if (st) {
+    *failed = true;
+    if (st & DEV_ERR_NONFINITE) return STR_ERR_NONFINITE;
+    if (st & DEV_ERR_SINGULAR) return STR_ERR_SINGULAR;
+    if (st & DEV_ERR_TIMEOUT) return STR_ERR_TIMEOUT;
+    return STR_ERR_CUDA;
+  }
+  return STR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// building blocks
+// ---------------------------------------------------------------------------
+
+// ring product W = E_{k_0} E_{k_1} ... E_{k_{N-2}} (cyclic order n+1..n-1), scattered into
+// Qout = base + (H^{!=n})_<2>  (Alg. 4 lines 8, 16; Prop. subchain_gram)
+str_status ring_Q(str_ctx* c, int n, const double* ENew, const double* base, double* Qout,
+                  cudaStream_t s) {
+  const int N = c->N;
+  int order[STR_MAXN];
+  for (int t = 0; t < N - 1; ++t) order[t] = (n + 1 + t) % N;
+  auto Eptr = [&](int k) -> const double* { return k == N - 1 ? ENew : E_of(c, k); };
+  const int RRmax = STR_MAXRR;
+  TRY(grow(c, c->ring0, (size_t)RRmax * RRmax * 8));
+  TRY(grow(c, c->ring1, (size_t)RRmax * RRmax * 8));
+  const double* A = Eptr(order[0]);
+  int Mrows = c->R[order[0]] * c->R[order[0]];
+  int Kc = c->R[order[0] + 1] * c->R[order[0] + 1];
+  double* bufs[2] = {(double*)c->ring0.p, (double*)c->ring1.p};
+  int bi = 0;
+  for (int t = 1; t < N - 1; ++t) {
+    const int k = order[t];
+    const double* B = Eptr(k);
+    const int Ncols = c->R[k + 1] * c->R[k + 1];
+    const bool last = (t == N - 2);
+    if (last) {
+      LCH(c, launch_gemm64(A, B, Qout, Mrows, Kc, Ncols, c->R[n], c->R[n + 1], base, s));
+    } else {
+      LCH(c, launch_gemm64(A, B, bufs[bi], Mrows, Kc, Ncols, 0, 0, nullptr, s));
+      A = bufs[bi];
+      bi ^= 1;
+      Kc = Ncols;
+    }
+  }
+  return STR_OK;
+}
+
+// solve out = P Q^{-1} (rows x n) by Cholesky; writes FP64 (and FP32 shadow)
+str_status solve_rows(str_ctx* c, const double* Qm, int n, const double* Pm, int64_t rows,
+                      double* out64, float* out32, cudaStream_t s) {
+  TRY(grow(c, c->lfac, (size_t)n * n * 8));
+  TRY(grow(c, c->invd, (size_t)n * 8));
+  LCH(c, launch_chol_factor(Qm, n, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, c->d_pivot, s));
+  LCH(c, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, n, Pm, rows, out64, out32, nullptr, s));
+  return STR_OK;
+}
+
+// leverage distribution of a core unfolding G (I x RR):  p_i = l_i / rank  (Lemma lev_est)
+str_status leverage(str_ctx* c, const double* G, int64_t I, int Ra, int Rb, double* p_out,
+                    cudaStream_t s) {
+  const int RR = Ra * Rb;
+  if (I <= RR) {
+    // full row rank: every leverage score is 1, p is uniform
+    LCH(c, launch_fill(p_out, I, 1.0 / (double)I, s));
+    return STR_OK;
+  }
+  TRY(grow(c, c->gram, (size_t)RR * RR * 8));
+  TRY(grow(c, c->lfac, (size_t)RR * RR * 8));
+  TRY(grow(c, c->invd, (size_t)RR * 8));
+  LCH(c, launch_core_gram(G, I, Ra, Rb, (double*)c->gram.p, nullptr, s));
+  LCH(c, launch_chol_factor((double*)c->gram.p, RR, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, nullptr, s));
+  LCH(c, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, RR, G, I, nullptr, nullptr, p_out, s));
+  return STR_OK;
+}
+
+str_status ensure_p(str_ctx* c, int k, int64_t I) {
+  if (I <= c->p_cap[k]) return STR_OK;
+  for (int b = 0; b < 2; ++b) {
+    double* np = nullptr;
+    TRY(dalloc_t(c, &np, (size_t)I));
+    c->p[k][b] = np;   // old buffers stay owned until destroy (small)
+  }
+  c->p_cap[k] = I;
+  return STR_OK;
+}
+
+// MTTKRP over a slab (dense or sampled) for mode n; result reduced into `out`
+// (real: out = base + scale * sum; complex: out complex FP64, base ignored)
+struct SlabView {
+  const void* X;
+  int xtype;
+  int64_t dim[STR_MAXN];
+};
+
+str_status mttkrp_into(str_ctx* c, const SlabView& v, int n, const void* const* cores, bool sampled,
+                       const int32_t* idxs, bool lev, const double* const* pk, double wscale,
+                       bool cplx, const double* base, double* out, void* gs, double* ws,
+                       cudaStream_t s) {
+  MttkrpArgs a;
+  a.X = v.X;
+  a.xtype = v.xtype;
+  a.N = c->N;
+  a.n = n;
+  for (int k = 0; k < c->N; ++k) { a.dim[k] = v.dim[k]; a.core[k] = cores[k]; }
+  for (int k = 0; k <= c->N; ++k) a.R[k] = c->R[k];
+  a.compute = c->compute;
+  a.cplx = cplx ? 1 : 0;
+  if (sampled) {
+    a.nfib = c->opt.m;
+    a.idxs = idxs;
+    a.m = c->opt.m;
+    a.leverage = lev ? 1 : 0;
+    if (lev) for (int k = 0; k < c->N; ++k) a.p[k] = pk[k];
+    a.gs_out = gs;
+    a.ws_out = ws;
+  } else {
+    int64_t J = 1;
+    for (int k = 0; k < c->N; ++k) if (k != n) J *= v.dim[k];
+    a.nfib = J;
+  }
+  a.wscale = wscale;
+  int64_t per = 0;
+  a.splits = mttkrp_plan_splits(a, &per);
+  a.fib_per_split = per;
+  const int RR = c->RR(n);
+  const size_t esize = (c->compute == 2 ? 8 : 4) * (cplx ? 2 : 1);
+  TRY(grow(c, c->partial, (size_t)a.splits * v.dim[n] * RR * esize));
+  a.partial = c->partial.p;
+  LCH(c, launch_mttkrp(a, s));
+  LCH(c, launch_reduce_partials(a.partial, c->compute, a.cplx, a.splits, v.dim[n] * RR, base, 1.0, out, s));
+  return STR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// slab intake
+// ---------------------------------------------------------------------------
+str_status take_slab(str_ctx* c, const str_tensor* X, SlabView* v, cudaStream_t s) {
+  if (!X || !X->data || !X->dims) return STR_ERR_INVALID_ARG;
+  if (X->order != c->N) return STR_ERR_SHAPE;
+  if (X->dtype != STR_BF16 && X->dtype != STR_F32 && X->dtype != STR_F64) return STR_ERR_DTYPE;
+  int64_t count = 1;
+  for (int k = 0; k < c->N; ++k) {
+    if (X->dims[k] < 1) return STR_ERR_SHAPE;
+    if (k < c->N - 1 && X->dims[k] != c->I[k]) return STR_ERR_SHAPE;
+    v->dim[k] = X->dims[k];
+    count *= X->dims[k];
+  }
+  v->xtype = xtype_of(X->dtype);
+  if (X->on_host) {
+    TRY(grow(c, c->xstage, (size_t)count * dsize(X->dtype)));
+    STR_CUDA_TRY(cudaMemcpyAsync(c->xstage.p, X->data, (size_t)count * dsize(X->dtype), cudaMemcpyHostToDevice, s));
+    v->X = c->xstage.p;
+  } else {
+    v->X = X->data;
+  }
+  if (c->opt.check_finite) LCH(c, launch_check_finite(v->X, v->xtype, count, c->d_status, s));
+  return STR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// KSRFT helpers (Definition of the KSRFT; Alg. 9)
+// ---------------------------------------------------------------------------
+int cplx_type(const str_ctx* c) { return c->compute == 2 ? XT_C64 : XT_C32; }
+size_t celem(const str_ctx* c) { return c->compute == 2 ? 16 : 8; }
+
+// signs D_k over dims[k] at step tau (purpose 1)
+str_status draw_signs(str_ctx* c, const int64_t* dims, uint64_t tau, cudaStream_t s) {
+  for (int k = 0; k < c->N; ++k) {
+    TRY(grow(c, c->sgn[k], (size_t)dims[k] * 8));
+    LCH(c, launch_signs((double*)c->sgn[k].p, dims[k], c->opt.seed, k + 1, tau, c->opt.stream_id, s));
+  }
+  return STR_OK;
+}
+
+// X_hat = X x_1 F_1 D_1 ... x_N F_N D_N  into xmix (complex compute type); returns pointer
+str_status mix_slab(str_ctx* c, const SlabView& v, const void** out, cudaStream_t s) {
+  int64_t count = 1;
+  for (int k = 0; k < c->N; ++k) count *= v.dim[k];
+  TRY(grow(c, c->xmix0, (size_t)count * celem(c)));
+  TRY(grow(c, c->xmix1, (size_t)count * celem(c)));
+  const void* src = v.X;
+  int st = v.xtype;
+  void* bufs[2] = {c->xmix0.p, c->xmix1.p};
+  int bi = 0;
+  for (int k = 0; k < c->N; ++k) {
+    LCH(c, launch_dft_mode(src, st, bufs[bi], c->compute, c->N, v.dim, k, (const double*)c->sgn[k].p, s));
+    src = bufs[bi];
+    st = cplx_type(c);
+    bi ^= 1;
+  }
+  *out = src;
+  return STR_OK;
+}
+
+// G_hat_k = G_k x_2 (F_k D_k): DFT along the row index of the unfolding (rows x RR)
+str_status mix_core(str_ctx* c, int k, const void* G, int64_t rows, cudaStream_t s) {
+  const int RR = c->RR(k);
+  TRY(grow(c, c->gmix[k], (size_t)rows * RR * celem(c)));
+  const int64_t dims[2] = {RR, rows};
+  LCH(c, launch_dft_mode(G, c->compute == 2 ? XT_F64 : XT_F32, c->gmix[k].p, c->compute, 2, dims, 1,
+                         (const double*)c->sgn[k].p, s));
+  return STR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// context creation
+// ---------------------------------------------------------------------------
+str_status validate_shape(int N, const int64_t* dims, const int* ranks) {
+  if (N < 3 || N > STR_MAXN) return STR_ERR_SHAPE;
+  if (!dims || !ranks) return STR_ERR_INVALID_ARG;
+  for (int k = 0; k < N; ++k) {
+    if (ranks[k] < 1 || ranks[k] > STR_MAXR) return STR_ERR_SHAPE;
+    if (k < N - 1 && dims[k] < 1) return STR_ERR_SHAPE;
+  }
+  for (int k = 0; k < N; ++k)
+    if (ranks[k] * ranks[(k + 1) % N] > 160) return STR_ERR_SHAPE;
+  return STR_OK;
+}
+
+str_status ctx_create(str_ctx** out, int N, const int64_t* dims, const int* ranks,
+                      const str_options* opt, int64_t t_init) {
+  str_options o;
+  str_default_options(&o);
+  if (opt) o = *opt;
+  if (o.compute != STR_F32 && o.compute != STR_F64) return STR_ERR_DTYPE;
+  if (o.sweeps < 1 || o.t_capacity < 1 || t_init < 1 || t_init > o.t_capacity) return STR_ERR_INVALID_ARG;
+  if (o.sketch != STR_SKETCH_NONE && (o.sketch < 0 || o.sketch > 2 || o.m < 1)) return STR_ERR_INVALID_ARG;
+  TRY(validate_shape(N, dims, ranks));
+  str_ctx* c = new str_ctx();
+  cudaGetDevice(&c->dev);
+  c->N = N;
+  for (int k = 0; k < N - 1; ++k) c->I[k] = dims[k];
+  c->I[N - 1] = t_init;
+  for (int k = 0; k < N; ++k) c->R[k] = ranks[k];
+  c->R[N] = ranks[0];
+  c->opt = o;
+  c->compute = o.compute == STR_F64 ? 2 : 1;
+  c->t_rows = t_init;
+  str_status st = STR_OK;
+  auto fail = [&](str_status e) { str_destroy(c); return e; };
+  for (int k = 0; k < N - 1; ++k) {
+    const int RR = c->RR(k);
+    for (int b = 0; b < 2; ++b) {
+      if ((st = dalloc_t(c, &c->G64[k][b], (size_t)c->I[k] * RR)) != STR_OK) return fail(st);
+      if (c->compute == 1 && (st = dalloc_t(c, &c->G32[k][b], (size_t)c->I[k] * RR)) != STR_OK) return fail(st);
+      if ((st = dalloc_t(c, &c->P[k][b], (size_t)c->I[k] * RR)) != STR_OK) return fail(st);
+      if ((st = dalloc_t(c, &c->Q[k][b], (size_t)RR * RR)) != STR_OK) return fail(st);
+      if ((st = dalloc_t(c, &c->E[k][b], (size_t)RR * RR)) != STR_OK) return fail(st);
+    }
+  }
+  const int RRN = c->RR(N - 1);
+  if ((st = dalloc_t(c, &c->GT64, (size_t)o.t_capacity * RRN)) != STR_OK) return fail(st);
+  if (c->compute == 1 && (st = dalloc_t(c, &c->GT32, (size_t)o.t_capacity * RRN)) != STR_OK) return fail(st);
+  if (o.sketch != STR_SKETCH_NONE) {
+    for (int k = 0; k < N; ++k)
+      for (int b = 0; b < 2; ++b)
+        if ((st = dalloc_t(c, &c->idxs[k][b], (size_t)o.m)) != STR_OK) return fail(st);
+  }
+  if ((st = dalloc_t(c, &c->d_status, 1)) != STR_OK) return fail(st);
+  if ((st = dalloc_t(c, &c->d_pivot, 1)) != STR_OK) return fail(st);
+  if (cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess) return fail(STR_ERR_OOM);
+  if (cudaMallocHost(&c->h_sums, 4 * sizeof(double)) != cudaSuccess) return fail(STR_ERR_OOM);
+  *c->h_status = 0;
+  *out = c;
+  return STR_OK;
+}
+
+// upload host FP64 cores and derive shadows and Gram transfer matrices
+str_status upload_cores(str_ctx* c, const double* const* cores, cudaStream_t s) {
+  const int N = c->N;
+  for (int k = 0; k < N; ++k) {
+    const int64_t rows = (k == N - 1) ? c->t_rows : c->I[k];
+    const int RR = c->RR(k);
+    double* dst = (k == N - 1) ? c->GT64 : c->G64[k][c->cur[k]];
+    STR_CUDA_TRY(cudaMemcpyAsync(dst, cores[k], (size_t)rows * RR * 8, cudaMemcpyHostToDevice, s));
+    if (c->compute == 1) {
+      float* d32 = (k == N - 1) ? c->GT32 : c->G32[k][c->cur[k]];
+      LCH(c, launch_convert(dst, XT_F64, d32, XT_F32, rows * RR, s));
+    }
+    if (k < N - 1) LCH(c, launch_core_gram(dst, rows, c->R[k], c->R[k + 1], nullptr, c->E[k][c->cur[k]], s));
+  }
+  return STR_OK;
+}
+
+const void* temporal_rows_c(const str_ctx* c, int64_t t0) {
+  const int RRN = c->RR(c->N - 1);
+  return c->compute == 2 ? (const void*)(c->GT64 + t0 * RRN) : (const void*)(c->GT32 + t0 * RRN);
+}
+
+double sketch_wscale(const str_ctx* c, int n, const int64_t* dims) {
+  if (!c->opt.rescale) return 1.0;
+  if (c->opt.sketch == STR_SKETCH_LEVERAGE) return 1.0 / (double)c->opt.m;
+  double J = 1.0;
+  for (int k = 0; k < c->N; ++k) if (k != n) J *= (double)dims[k];
+  return J / (double)c->opt.m;
+}
+
+// rSTR initialisation stage (Algs. 7-9, lines 2-19): draws at tau = 0, sketched P_n, Q_n
+str_status rstr_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
+  const int N = c->N;
+  const int64_t m = c->opt.m;
+  const bool lev = c->opt.sketch == STR_SKETCH_LEVERAGE && c->opt.rescale;
+  const bool levdraw = c->opt.sketch == STR_SKETCH_LEVERAGE;
+  const bool ks = c->opt.sketch == STR_SKETCH_KSRFT;
+  const int cmax = *std::max_element(c->R, c->R + N);
+  (void)cmax;
+  for (int k = 0; k < N; ++k) {
+    const int64_t Ik = v.dim[k];
+    if (levdraw) {
+      TRY(ensure_p(c, k, Ik));
+      const double* G = (k == N - 1) ? c->GT64 : c->G64[k][c->cur[k]];
+      TRY(leverage(c, G, Ik, c->R[k], c->R[k + 1], c->p[k][c->cur[k]], s));
+    }
+    LCH(c, launch_draw_indices(c->idxs[k][c->cur[k]], m, Ik, c->opt.seed, k + 1, 0, c->opt.stream_id,
+                               levdraw ? c->p[k][c->cur[k]] : nullptr, s));
+  }
+  const void* cores[STR_MAXN];
+  const void* src = v.X;
+  SlabView sv = v;
+  if (ks) {
+    TRY(draw_signs(c, v.dim, 0, s));
+    TRY(mix_slab(c, v, &src, s));
+    sv.X = src;
+    sv.xtype = cplx_type(c);
+    for (int k = 0; k < N; ++k) {
+      const void* G = (k == N - 1) ? temporal_rows_c(c, 0) : core_c(c, k);
+      TRY(mix_core(c, k, G, v.dim[k], s));
+      cores[k] = c->gmix[k].p;
+    }
+  } else {
+    for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
+    cores[N - 1] = temporal_rows_c(c, 0);
+  }
+  int RRmax = 0;
+  for (int k = 0; k < N; ++k) RRmax = std::max(RRmax, c->RR(k));
+  TRY(grow(c, c->gs, (size_t)m * RRmax * celem(c)));
+  TRY(grow(c, c->ws, (size_t)m * 8));
+  int64_t Imax = 0;
+  for (int k = 0; k < N; ++k) Imax = std::max(Imax, v.dim[k]);
+  TRY(grow(c, c->mtmp, (size_t)Imax * RRmax * 16));
+  const int32_t* idx0 = nullptr;
+  TRY(grow(c, c->sums, (size_t)N * m * sizeof(int32_t)));
+  // gather the per-mode index columns into one [k][m] array
+  int32_t* idxcat = (int32_t*)c->sums.p;
+  for (int k = 0; k < N; ++k)
+    STR_CUDA_TRY(cudaMemcpyAsync(idxcat + (size_t)k * m, c->idxs[k][c->cur[k]], m * 4, cudaMemcpyDeviceToDevice, s));
+  idx0 = idxcat;
+  const double* pk[STR_MAXN] = {};
+  for (int k = 0; k < N; ++k) pk[k] = c->p[k][c->cur[k]];
+  for (int n = 0; n < N - 1; ++n) {
+    const int RR = c->RR(n);
+    double* Pn = c->P[n][c->cur[n]];
+    double* Qn = c->Q[n][c->cur[n]];
+    const double ws = sketch_wscale(c, n, v.dim);
+    if (ks) {
+      TRY(mttkrp_into(c, sv, n, cores, true, idx0, false, pk, ws, true, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
+      LCH(c, launch_unmix_rows((double*)c->mtmp.p, v.dim[n], RR, (const double*)c->sgn[n].p, nullptr, Pn, s));
+    } else {
+      TRY(mttkrp_into(c, sv, n, cores, true, idx0, lev, pk, ws, false, nullptr, Pn, c->gs.p, (double*)c->ws.p, s));
+    }
+    LCH(c, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, nullptr, Qn, s));
+  }
+  return STR_OK;
+}
+
+// exact initialisation (Alg. 4 lines 2-6): P_n = X0_[n] G^{!=n}_[2], Q_n = ring with Z_N of G_N^init
+str_status str_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
+  const int N = c->N;
+  const int RRN = c->RR(N - 1);
+  TRY(grow(c, c->enew, (size_t)RRN * RRN * 8));
+  LCH(c, launch_core_gram(c->GT64, c->t_rows, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s));
+  const void* cores[STR_MAXN];
+  for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
+  cores[N - 1] = temporal_rows_c(c, 0);
+  for (int n = 0; n < N - 1; ++n) {
+    TRY(mttkrp_into(c, v, n, cores, false, nullptr, false, nullptr, 1.0, false, nullptr, c->P[n][c->cur[n]], nullptr, nullptr, s));
+    TRY(ring_Q(c, n, (double*)c->enew.p, nullptr, c->Q[n][c->cur[n]], s));
+  }
+  return STR_OK;
+}
+
+str_status finish_step(str_ctx* c, cudaStream_t s, int64_t t_new) {
+  if (!c->opt.async_status) {
+    bool failed = false;
+    str_status st = check_status(c, s, &failed);
+    if (st != STR_OK) {
+      for (int k = 0; k < STR_MAXN; ++k) c->upd[k] = 0;
+      STR_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+      return st;
+    }
+  }
+  for (int k = 0; k < STR_MAXN; ++k) {
+    if (c->upd[k]) c->cur[k] ^= 1;
+    c->upd[k] = 0;
+  }
+  c->t_rows += t_new;
+  c->last_tn = t_new;
+  c->step += 1;
+  return STR_OK;
+}
+
+str_status precheck(str_ctx* c, cudaStream_t s) {
+  if (c->sticky) return STR_ERR_STATE;
+  if (c->opt.async_status) {
+    STR_CUDA_TRY(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*c->h_status) { c->sticky = 1; return STR_ERR_STATE; }
+  }
+  return STR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// STR step (Alg. 4 lines 8-19), with sweeps
+// ---------------------------------------------------------------------------
+str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
+  const int N = c->N;
+  const int64_t tn = v.dim[N - 1];
+  const int RRN = c->RR(N - 1);
+  TRY(grow(c, c->gnew64, (size_t)tn * RRN * 8));
+  if (c->compute == 1) TRY(grow(c, c->gnew32, (size_t)tn * RRN * 4));
+  TRY(grow(c, c->enew, (size_t)RRN * RRN * 8));
+  TRY(grow(c, c->mtmp, (size_t)tn * RRN * 8));
+  TRY(grow(c, c->qtmp, (size_t)RRN * RRN * 8));
+  double* gn64 = (double*)c->gnew64.p;
+  const void* gn_c = c->compute == 2 ? (const void*)gn64 : c->gnew32.p;
+  for (int sw = 0; sw < c->opt.sweeps; ++sw) {
+    // temporal mode: H^{!=N} ring, M_N = X_[N] G^{!=N}_[2], G_N^new = M_N H^{-1}
+    const void* cores[STR_MAXN];
+    for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
+    cores[N - 1] = nullptr;
+    TRY(ring_Q(c, N - 1, nullptr, nullptr, (double*)c->qtmp.p, s));
+    TRY(mttkrp_into(c, v, N - 1, cores, false, nullptr, false, nullptr, 1.0, false, nullptr, (double*)c->mtmp.p, nullptr, nullptr, s));
+    TRY(solve_rows(c, (double*)c->qtmp.p, RRN, (double*)c->mtmp.p, tn, gn64,
+                   c->compute == 1 ? (float*)c->gnew32.p : nullptr, s));
+    LCH(c, launch_core_gram(gn64, tn, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s));
+    // spatial modes in order (Gauss-Seidel)
+    for (int n = 0; n < N - 1; ++n) {
+      const int RR = c->RR(n);
+      const int w = 1 - c->cur[n];
+      for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
+      cores[N - 1] = gn_c;
+      TRY(mttkrp_into(c, v, n, cores, false, nullptr, false, nullptr, 1.0, false, c->P[n][c->cur[n]], c->P[n][w], nullptr, nullptr, s));
+      TRY(ring_Q(c, n, (double*)c->enew.p, c->Q[n][c->cur[n]], c->Q[n][w], s));
+      TRY(solve_rows(c, c->Q[n][w], RR, c->P[n][w], c->I[n], c->G64[n][w],
+                     c->compute == 1 ? c->G32[n][w] : nullptr, s));
+      LCH(c, launch_core_gram(c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][w], s));
+      c->upd[n] = 1;
+    }
+  }
+  // append the new temporal rows
+  STR_CUDA_TRY(cudaMemcpyAsync(c->GT64 + c->t_rows * RRN, gn64, (size_t)tn * RRN * 8, cudaMemcpyDeviceToDevice, s));
+  if (c->compute == 1)
+    STR_CUDA_TRY(cudaMemcpyAsync(c->GT32 + c->t_rows * RRN, c->gnew32.p, (size_t)tn * RRN * 4, cudaMemcpyDeviceToDevice, s));
+  return STR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// rSTR step (Alg. 5; schedules of Algs. 7, 8, 9)
+// ---------------------------------------------------------------------------
+str_status rstr_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
+  const int N = c->N;
+  const int64_t m = c->opt.m;
+  const int64_t tn = v.dim[N - 1];
+  const uint64_t tau = (uint64_t)c->step + 1;
+  const bool levdraw = c->opt.sketch == STR_SKETCH_LEVERAGE;
+  const bool lev = levdraw && c->opt.rescale;
+  const bool ks = c->opt.sketch == STR_SKETCH_KSRFT;
+  const int RRN = c->RR(N - 1);
+  int RRmax = 0;
+  int64_t Imax = tn;
+  for (int k = 0; k < N; ++k) RRmax = std::max(RRmax, c->RR(k));
+  for (int k = 0; k < N - 1; ++k) Imax = std::max(Imax, c->I[k]);
+  TRY(grow(c, c->gnew64, (size_t)tn * RRN * 8));
+  if (c->compute == 1) TRY(grow(c, c->gnew32, (size_t)tn * RRN * 4));
+  TRY(grow(c, c->mtmp, (size_t)Imax * RRmax * 16));
+  TRY(grow(c, c->qtmp, (size_t)RRN * RRN * 8));
+  TRY(grow(c, c->gs, (size_t)m * RRmax * celem(c)));
+  TRY(grow(c, c->ws, (size_t)m * 8));
+  TRY(grow(c, c->sums, (size_t)N * m * 4));
+  double* gn64 = (double*)c->gnew64.p;
+  const void* gn_c = c->compute == 2 ? (const void*)gn64 : c->gnew32.p;
+  int32_t* idxcat = (int32_t*)c->sums.p;
+  auto gather_idx = [&]() -> str_status {
+    for (int k = 0; k < N; ++k)
+      STR_CUDA_TRY(cudaMemcpyAsync(idxcat + (size_t)k * m, c->idxs[k][buf_of(c, k)], m * 4, cudaMemcpyDeviceToDevice, s));
+    return STR_OK;
+  };
+  auto pks = [&](const double** pk) {
+    for (int k = 0; k < N; ++k) pk[k] = c->p[k][buf_of(c, k)];
+  };
+  SlabView sv = v;
+  const void* cores[STR_MAXN];
+  if (ks) {
+    TRY(draw_signs(c, v.dim, tau, s));
+    const void* xm = nullptr;
+    TRY(mix_slab(c, v, &xm, s));
+    sv.X = xm;
+    sv.xtype = cplx_type(c);
+    for (int k = 0; k < N - 1; ++k) TRY(mix_core(c, k, core_c(c, k), c->I[k], s));
+  }
+  // ---- temporal mode ----
+  for (int k = 0; k < N - 1; ++k) cores[k] = ks ? c->gmix[k].p : core_c(c, k);
+  cores[N - 1] = nullptr;
+  TRY(gather_idx());
+  const double* pk[STR_MAXN];
+  pks(pk);
+  const double wsN = sketch_wscale(c, N - 1, v.dim);
+  if (ks) {
+    TRY(mttkrp_into(c, sv, N - 1, cores, true, idxcat, false, pk, wsN, true, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
+    TRY(grow(c, c->gram, (size_t)tn * RRN * 8 + 64));
+    LCH(c, launch_unmix_rows((double*)c->mtmp.p, tn, RRN, (const double*)c->sgn[N - 1].p, nullptr, (double*)c->gram.p, s));
+  } else {
+    TRY(mttkrp_into(c, sv, N - 1, cores, true, idxcat, lev, pk, wsN, false, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
+  }
+  LCH(c, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RRN, nullptr, (double*)c->qtmp.p, s));
+  TRY(solve_rows(c, (double*)c->qtmp.p, RRN, ks ? (double*)c->gram.p : (double*)c->mtmp.p, tn, gn64,
+                 c->compute == 1 ? (float*)c->gnew32.p : nullptr, s));
+  {
+    const int k = N - 1;
+    const int w = 1 - c->cur[k];
+    if (levdraw) {
+      TRY(ensure_p(c, k, tn));
+      TRY(leverage(c, gn64, tn, c->R[k], c->R[k + 1], c->p[k][w], s));
+    }
+    LCH(c, launch_draw_indices(c->idxs[k][w], m, tn, c->opt.seed, k + 1, tau, c->opt.stream_id,
+                               levdraw ? c->p[k][w] : nullptr, s));
+    c->upd[k] = 1;
+    if (ks) TRY(mix_core(c, k, gn_c, tn, s));
+  }
+  // ---- spatial modes ----
+  for (int n = 0; n < N - 1; ++n) {
+    const int RR = c->RR(n);
+    const int w = 1 - c->cur[n];
+    for (int k = 0; k < N - 1; ++k) cores[k] = ks ? c->gmix[k].p : core_c(c, k);
+    cores[N - 1] = ks ? c->gmix[N - 1].p : gn_c;
+    TRY(gather_idx());
+    pks(pk);
+    const double wsn = sketch_wscale(c, n, v.dim);
+    if (ks) {
+      TRY(mttkrp_into(c, sv, n, cores, true, idxcat, false, pk, wsn, true, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
+      LCH(c, launch_unmix_rows((double*)c->mtmp.p, c->I[n], RR, (const double*)c->sgn[n].p, c->P[n][c->cur[n]], c->P[n][w], s));
+    } else {
+      TRY(mttkrp_into(c, sv, n, cores, true, idxcat, lev, pk, wsn, false, c->P[n][c->cur[n]], c->P[n][w], c->gs.p, (double*)c->ws.p, s));
+    }
+    LCH(c, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, c->Q[n][c->cur[n]], c->Q[n][w], s));
+    TRY(solve_rows(c, c->Q[n][w], RR, c->P[n][w], c->I[n], c->G64[n][w], c->compute == 1 ? c->G32[n][w] : nullptr, s));
+    c->upd[n] = 1;
+    if (levdraw) {
+      TRY(ensure_p(c, n, c->I[n]));
+      TRY(leverage(c, c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], c->p[n][w], s));
+    }
+    LCH(c, launch_draw_indices(c->idxs[n][w], m, c->I[n], c->opt.seed, n + 1, tau, c->opt.stream_id,
+                               levdraw ? c->p[n][w] : nullptr, s));
+    if (ks) TRY(mix_core(c, n, core_c(c, n), c->I[n], s));
+    // E_n is kept current for a later exact update on the same context
+    LCH(c, launch_core_gram(c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][w], s));
+  }
+  STR_CUDA_TRY(cudaMemcpyAsync(c->GT64 + c->t_rows * RRN, gn64, (size_t)tn * RRN * 8, cudaMemcpyDeviceToDevice, s));
+  if (c->compute == 1)
+    STR_CUDA_TRY(cudaMemcpyAsync(c->GT32 + c->t_rows * RRN, c->gnew32.p, (size_t)tn * RRN * 4, cudaMemcpyDeviceToDevice, s));
+  return STR_OK;
+}
+
+// prefix/suffix tables and the recon kernel over temporal rows [t0, t0 + t)
+str_status recon_common(const str_ctx* cc, int64_t t0, int64_t t, int mode, const void* X, int xtype,
+                        void* out, int out_type, double* sums_out, cudaStream_t s) {
+  str_ctx* c = const_cast<str_ctx*>(cc);
+  const int N = c->N;
+  int64_t dims[STR_MAXN];
+  for (int k = 0; k < N - 1; ++k) dims[k] = c->I[k];
+  dims[N - 1] = t;
+  const int kp = N / 2;   // prefix modes 0..kp-1
+  int64_t rows = 1, cols = 1;
+  for (int k = 0; k < kp; ++k) rows *= dims[k];
+  for (int k = kp; k < N; ++k) cols *= dims[k];
+  const int K = c->R[0] * c->R[kp];
+  const size_t es = c->compute == 2 ? 8 : 4;
+  TRY(grow(c, c->tab0, (size_t)rows * K * es));
+  TRY(grow(c, c->tab1, (size_t)cols * K * es));
+  const void* cores[STR_MAXN];
+  for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
+  cores[N - 1] = temporal_rows_c(c, t0);
+  LCH(c, launch_chain_table(cores, c->compute, c->R, N, dims, 0, kp - 1, 0, 0, c->tab0.p, s));
+  LCH(c, launch_chain_table(cores, c->compute, c->R, N, dims, kp, N - 1, 0, 1, c->tab1.p, s));
+  const int64_t nb = recon_blocks(rows, cols);
+  if (mode == RM_FIT) TRY(grow(c, c->bsum, (size_t)nb * 16));
+  int64_t nbo = 0;
+  LCH(c, launch_recon(c->tab0.p, c->tab1.p, c->compute, rows, cols, K, mode, X, xtype, nullptr, out,
+                      out_type, (double*)c->bsum.p, &nbo, s));
+  if (mode == RM_FIT) LCH(c, launch_sum_blocks((double*)c->bsum.p, nbo, 2, sums_out, 1.0, s));
+  return STR_OK;
+}
+
+// stateless workspace for the loss calls (grow-only, per process)
+std::mutex g_ws_mu;
+struct LossWs {
+  void* p = nullptr;
+  size_t cap = 0;
+} g_loss_ws[4];
+
+str_status ws_grow(int i, size_t bytes) {
+  if (bytes <= g_loss_ws[i].cap) return STR_OK;
+  if (g_loss_ws[i].p) cudaFree(g_loss_ws[i].p);
+  g_loss_ws[i].p = nullptr;
+  g_loss_ws[i].cap = 0;
+  cudaError_t e = cudaMalloc(&g_loss_ws[i].p, bytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e, "cudaMalloc"); }
+  g_loss_ws[i].cap = bytes;
+  return STR_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+str_status str_default_options(str_options* o) {
+  if (!o) return STR_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->compute = STR_F64;
+  o->sweeps = 1;
+  o->rescale = 1;
+  o->t_capacity = 65536;
+  o->init_max_it = 100;
+  o->init_tol = 1e-8;
+  o->sketch = STR_SKETCH_NONE;
+  o->m = 1000;
+  o->seed = 0;
+  o->stream_id = 0;
+  o->check_finite = 0;
+  o->async_status = 0;
+  return STR_OK;
+}
+
+str_status str_init_cores(str_ctx** out, int N, const int64_t* dims, const int* ranks, int64_t t_init,
+                          const double* const* cores, const str_tensor* X0, const str_options* opt,
+                          void* stream) {
+  if (!out || !cores) return STR_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int k = 0; k < N && k < STR_MAXN; ++k) if (!cores[k]) return STR_ERR_INVALID_ARG;
+  str_ctx* c = nullptr;
+  TRY(ctx_create(&c, N, dims, ranks, opt, t_init));
+  cudaStream_t s = (cudaStream_t)stream;
+  str_status st = upload_cores(c, cores, s);
+  if (st == STR_OK && X0) {
+    SlabView v;
+    st = take_slab(c, X0, &v, s);
+    if (st == STR_OK && v.dim[N - 1] != t_init) st = STR_ERR_SHAPE;
+    if (st == STR_OK) st = (c->opt.sketch == STR_SKETCH_NONE) ? str_init_state(c, v, s) : rstr_init_state(c, v, s);
+  } else if (st == STR_OK && c->opt.sketch != STR_SKETCH_NONE) {
+    st = STR_ERR_INVALID_ARG;   // rSTR needs the initial tensor for its sketches
+  }
+  if (st == STR_OK) {
+    bool failed = false;
+    st = check_status(c, s, &failed);
+  }
+  if (st != STR_OK) { str_destroy(c); return st; }
+  *out = c;
+  return STR_OK;
+}
+
+str_status str_init(str_ctx** out, const str_tensor* X0, const int* ranks, const double* const* guess,
+                    const str_options* opt, void* stream) {
+  if (!out || !X0 || !ranks || !guess || !X0->dims) return STR_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int N = X0->order;
+  if (N < 3 || N > STR_MAXN) return STR_ERR_SHAPE;
+  str_options o;
+  str_default_options(&o);
+  if (opt) o = *opt;
+  const int64_t t_init = X0->dims[N - 1];
+  str_ctx* c = nullptr;
+  TRY(ctx_create(&c, N, X0->dims, ranks, &o, t_init));
+  cudaStream_t s = (cudaStream_t)stream;
+  str_status st = upload_cores(c, guess, s);
+  SlabView v;
+  if (st == STR_OK) st = take_slab(c, X0, &v, s);
+  // TR-ALS-NE (Alg. 2) on X0: every core, including the temporal one, in turn
+  double prev = -1.0;
+  for (int it = 0; st == STR_OK && it < o.init_max_it; ++it) {
+    for (int n = 0; n < N && st == STR_OK; ++n) {
+      const int RR = c->RR(n);
+      const void* cores[STR_MAXN];
+      for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
+      cores[N - 1] = temporal_rows_c(c, 0);
+      st = grow(c, c->mtmp, (size_t)v.dim[n] * RR * 8);
+      if (st == STR_OK) st = grow(c, c->qtmp, (size_t)RR * RR * 8);
+      if (st == STR_OK) st = grow(c, c->enew, (size_t)c->RR(N - 1) * c->RR(N - 1) * 8);
+      if (st != STR_OK) break;
+      // E of the temporal core (rows t_init) for the ring
+      if (n < N - 1) {
+        ++c->launches;
+        launch_core_gram(c->GT64, t_init, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s);
+      }
+      st = ring_Q(c, n, (double*)c->enew.p, nullptr, (double*)c->qtmp.p, s);
+      if (st == STR_OK) st = mttkrp_into(c, v, n, cores, false, nullptr, false, nullptr, 1.0, false, nullptr, (double*)c->mtmp.p, nullptr, nullptr, s);
+      if (st != STR_OK) break;
+      double* o64 = (n == N - 1) ? c->GT64 : c->G64[n][c->cur[n]];
+      float* o32 = (c->compute == 1) ? ((n == N - 1) ? c->GT32 : c->G32[n][c->cur[n]]) : nullptr;
+      st = solve_rows(c, (double*)c->qtmp.p, RR, (double*)c->mtmp.p, v.dim[n], o64, o32, s);
+      if (st == STR_OK && n < N - 1)
+        st = from_cuda(launch_core_gram(o64, c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][c->cur[n]], s), "core_gram");
+    }
+    if (st != STR_OK) break;
+    double err = 0.0;
+    st = grow(c, c->sums, 64);
+    if (st != STR_OK) break;
+    st = recon_common(c, 0, t_init, RM_FIT, v.X, v.xtype, nullptr, 0, (double*)c->sums.p, s);
+    if (st != STR_OK) break;
+    if (cudaMemcpyAsync(c->h_sums, c->sums.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { st = STR_ERR_CUDA; break; }
+    err = c->h_sums[1] > 0 ? std::sqrt(c->h_sums[0] / c->h_sums[1]) : 0.0;
+    if (prev >= 0.0 && std::fabs(prev - err) < o.init_tol) break;
+    prev = err;
+  }
+  if (st == STR_OK) st = (c->opt.sketch == STR_SKETCH_NONE) ? str_init_state(c, v, s) : rstr_init_state(c, v, s);
+  if (st == STR_OK) {
+    bool failed = false;
+    st = check_status(c, s, &failed);
+  }
+  if (st != STR_OK) { str_destroy(c); return st; }
+  *out = c;
+  return STR_OK;
+}
+
+str_status str_update(str_ctx* c, const str_tensor* X, void* stream) {
+  if (!c) return STR_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(precheck(c, s));
+  c->launches = 0;
+  SlabView v;
+  TRY(take_slab(c, X, &v, s));
+  const int64_t tn = v.dim[c->N - 1];
+  if (c->t_rows + tn > c->opt.t_capacity) return STR_ERR_CAPACITY;
+  str_status st = str_step(c, v, s);
+  if (st != STR_OK) {
+    for (int k = 0; k < STR_MAXN; ++k) c->upd[k] = 0;
+    return st;
+  }
+  return finish_step(c, s, tn);
+}
+
+str_status rstr_update(str_ctx* c, const str_tensor* X, str_sketch type, int64_t m, uint64_t seed,
+                       void* stream) {
+  if (!c) return STR_ERR_INVALID_ARG;
+  if (c->opt.sketch == STR_SKETCH_NONE || type != c->opt.sketch || m != c->opt.m || seed != c->opt.seed)
+    return STR_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(precheck(c, s));
+  c->launches = 0;
+  SlabView v;
+  TRY(take_slab(c, X, &v, s));
+  const int64_t tn = v.dim[c->N - 1];
+  if (c->t_rows + tn > c->opt.t_capacity) return STR_ERR_CAPACITY;
+  str_status st = rstr_step(c, v, s);
+  if (st != STR_OK) {
+    for (int k = 0; k < STR_MAXN; ++k) c->upd[k] = 0;
+    return st;
+  }
+  return finish_step(c, s, tn);
+}
+
+str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, int count, int randomized,
+                            void* stream) {
+  if (!ctxs || !X || count < 0) return STR_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // enqueue every context's step with status checks deferred, then commit all or none
+  std::vector<int64_t> tns(count);
+  for (int i = 0; i < count; ++i) {
+    str_ctx* c = ctxs[i];
+    if (!c) return STR_ERR_INVALID_ARG;
+    TRY(precheck(c, s));
+    if (randomized && c->opt.sketch == STR_SKETCH_NONE) return STR_ERR_STATE;
+  }
+  str_status st = STR_OK;
+  int done = 0;
+  for (int i = 0; i < count && st == STR_OK; ++i) {
+    str_ctx* c = ctxs[i];
+    c->launches = 0;
+    SlabView v;
+    st = take_slab(c, X[i], &v, s);
+    if (st != STR_OK) break;
+    tns[i] = v.dim[c->N - 1];
+    if (c->t_rows + tns[i] > c->opt.t_capacity) { st = STR_ERR_CAPACITY; break; }
+    st = randomized ? rstr_step(c, v, s) : str_step(c, v, s);
+    done = i + 1;
+  }
+  bool any_fail = st != STR_OK;
+  if (!any_fail) {
+    for (int i = 0; i < count; ++i) {
+      str_ctx* c = ctxs[i];
+      if (c->opt.async_status) continue;
+      bool failed = false;
+      str_status e = check_status(c, s, &failed);
+      if (e != STR_OK) { st = e; any_fail = true; }
+    }
+  }
+  for (int i = 0; i < done; ++i) {
+    str_ctx* c = ctxs[i];
+    if (any_fail) {
+      for (int k = 0; k < STR_MAXN; ++k) c->upd[k] = 0;
+      cudaMemsetAsync(c->d_status, 0, sizeof(int), s);
+      continue;
+    }
+    for (int k = 0; k < STR_MAXN; ++k) { if (c->upd[k]) c->cur[k] ^= 1; c->upd[k] = 0; }
+    c->t_rows += tns[i];
+    c->last_tn = tns[i];
+    c->step += 1;
+  }
+  return st;
+}
+
+str_status tr_reconstruct(const str_ctx* c, int64_t t0, int64_t t1, void* out, str_dtype dtype, void* stream) {
+  if (!c || !out) return STR_ERR_INVALID_ARG;
+  if (t0 < 0 || t1 <= t0 || t1 > c->t_rows) return STR_ERR_SHAPE;
+  if (dtype != STR_F32 && dtype != STR_F64) return STR_ERR_DTYPE;
+  return recon_common(c, t0, t1 - t0, RM_WRITE, nullptr, 0, out, xtype_of(dtype), nullptr, (cudaStream_t)stream);
+}
+
+str_status tr_fit_error(const str_ctx* cc, const str_tensor* X, int64_t t0, double* rel_err, void* stream) {
+  if (!cc || !X || !rel_err || !X->data || !X->dims) return STR_ERR_INVALID_ARG;
+  str_ctx* c = const_cast<str_ctx*>(cc);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (X->order != c->N) return STR_ERR_SHAPE;
+  for (int k = 0; k < c->N - 1; ++k) if (X->dims[k] != c->I[k]) return STR_ERR_SHAPE;
+  const int64_t t = X->dims[c->N - 1];
+  if (t0 < 0 || t < 1 || t0 + t > c->t_rows) return STR_ERR_SHAPE;
+  int64_t count = 1;
+  for (int k = 0; k < c->N; ++k) count *= X->dims[k];
+  const void* Xd = X->data;
+  if (X->on_host) {
+    TRY(grow(c, c->xstage, (size_t)count * dsize(X->dtype)));
+    STR_CUDA_TRY(cudaMemcpyAsync(c->xstage.p, X->data, (size_t)count * dsize(X->dtype), cudaMemcpyHostToDevice, s));
+    Xd = c->xstage.p;
+  }
+  TRY(grow(c, c->sums, 64));
+  TRY(recon_common(c, t0, t, RM_FIT, Xd, xtype_of(X->dtype), nullptr, 0, (double*)c->sums.p, s));
+  STR_CUDA_TRY(cudaMemcpyAsync(c->h_sums, c->sums.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  STR_CUDA_TRY(cudaStreamSynchronize(s));
+  *rel_err = c->h_sums[1] > 0 ? std::sqrt(c->h_sums[0] / c->h_sums[1]) : 0.0;
+  return STR_OK;
+}
+
+int64_t str_num_time_rows(const str_ctx* c) { return c ? c->t_rows : -1; }
+
+str_status str_get_core(const str_ctx* c, int n, double* host_out) {
+  if (!c || !host_out || n < 1 || n > c->N) return STR_ERR_INVALID_ARG;
+  const int k = n - 1;
+  const int RR = c->RR(k);
+  const double* src = (k == c->N - 1) ? c->GT64 : c->G64[k][c->cur[k]];
+  const int64_t rows = (k == c->N - 1) ? c->t_rows : c->I[k];
+  STR_CUDA_TRY(cudaDeviceSynchronize());
+  STR_CUDA_TRY(cudaMemcpy(host_out, src, (size_t)rows * RR * 8, cudaMemcpyDeviceToHost));
+  return STR_OK;
+}
+
+str_status str_get_pq(const str_ctx* c, int n, double* hP, double* hQ) {
+  if (!c || n < 1 || n > c->N - 1) return STR_ERR_INVALID_ARG;
+  const int k = n - 1;
+  const int RR = c->RR(k);
+  STR_CUDA_TRY(cudaDeviceSynchronize());
+  if (hP) STR_CUDA_TRY(cudaMemcpy(hP, c->P[k][c->cur[k]], (size_t)c->I[k] * RR * 8, cudaMemcpyDeviceToHost));
+  if (hQ) STR_CUDA_TRY(cudaMemcpy(hQ, c->Q[k][c->cur[k]], (size_t)RR * RR * 8, cudaMemcpyDeviceToHost));
+  return STR_OK;
+}
+
+str_status str_get_samples(const str_ctx* c, int k1, int64_t* host_idxs, double* host_p) {
+  if (!c || !host_idxs || k1 < 1 || k1 > c->N) return STR_ERR_INVALID_ARG;
+  if (c->opt.sketch == STR_SKETCH_NONE) return STR_ERR_STATE;
+  const int k = k1 - 1;
+  std::vector<int32_t> tmp((size_t)c->opt.m);
+  STR_CUDA_TRY(cudaDeviceSynchronize());
+  STR_CUDA_TRY(cudaMemcpy(tmp.data(), c->idxs[k][c->cur[k]], (size_t)c->opt.m * 4, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < c->opt.m; ++i) host_idxs[i] = tmp[i];
+  if (host_p) {
+    if (c->opt.sketch != STR_SKETCH_LEVERAGE) return STR_ERR_STATE;
+    // p_k covers the rows the draw used: I_k, or the last slab's t for the temporal mode
+    const int64_t rows = (k == c->N - 1) ? (c->step == 0 ? c->t_rows : c->last_tn) : c->I[k];
+    STR_CUDA_TRY(cudaMemcpy(host_p, c->p[k][c->cur[k]], (size_t)rows * 8, cudaMemcpyDeviceToHost));
+  }
+  return STR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint: header, then committed device arrays in a fixed order
+// ---------------------------------------------------------------------------
+struct SaveHeader {
+  uint64_t magic;
+  int32_t N, compute;
+  int64_t I[STR_MAXN];
+  int32_t R[STR_MAXN + 1];
+  str_options opt;
+  int64_t t_rows, step, last_tn;
+  int64_t p_rows[STR_MAXN];
+};
+
+static size_t save_size(const str_ctx* c, SaveHeader* h) {
+  const int N = c->N;
+  std::memset(h, 0, sizeof(*h));
+  h->magic = kSaveMagic;
+  h->N = N;
+  h->compute = c->compute;
+  for (int k = 0; k < STR_MAXN; ++k) h->I[k] = c->I[k];
+  for (int k = 0; k <= STR_MAXN; ++k) h->R[k] = c->R[k];
+  h->opt = c->opt;
+  h->t_rows = c->t_rows;
+  h->step = c->step;
+  h->last_tn = c->last_tn;
+  size_t sz = sizeof(SaveHeader);
+  for (int k = 0; k < N - 1; ++k) {
+    const size_t RR = c->RR(k);
+    sz += (c->I[k] * RR + c->I[k] * RR + RR * RR + RR * RR) * 8;  // G, P, Q, E
+  }
+  sz += (size_t)c->t_rows * c->RR(N - 1) * 8;
+  if (c->opt.sketch != STR_SKETCH_NONE) {
+    sz += (size_t)N * c->opt.m * 4;
+    if (c->opt.sketch == STR_SKETCH_LEVERAGE)
+      for (int k = 0; k < N; ++k) { h->p_rows[k] = c->p_cap[k]; sz += (size_t)c->p_cap[k] * 8; }
+  }
+  return sz;
+}
+
+str_status str_save(const str_ctx* c, void* buf, size_t* len) {
+  if (!c || !len) return STR_ERR_INVALID_ARG;
+  SaveHeader h;
+  const size_t need = save_size(c, &h);
+  if (!buf) { *len = need; return STR_OK; }
+  if (*len < need) { *len = need; return STR_ERR_INVALID_ARG; }
+  STR_CUDA_TRY(cudaDeviceSynchronize());
+  char* o = (char*)buf;
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  auto d2h = [&](const void* src, size_t bytes) -> bool {
+    if (cudaMemcpy(o, src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    o += bytes;
+    return true;
+  };
+  const int N = c->N;
+  for (int k = 0; k < N - 1; ++k) {
+    const size_t RR = c->RR(k);
+    const int b = c->cur[k];
+    if (!d2h(c->G64[k][b], c->I[k] * RR * 8) || !d2h(c->P[k][b], c->I[k] * RR * 8) ||
+        !d2h(c->Q[k][b], RR * RR * 8) || !d2h(c->E[k][b], RR * RR * 8)) return STR_ERR_CUDA;
+  }
+  if (!d2h(c->GT64, (size_t)c->t_rows * c->RR(N - 1) * 8)) return STR_ERR_CUDA;
+  if (c->opt.sketch != STR_SKETCH_NONE) {
+    for (int k = 0; k < N; ++k) if (!d2h(c->idxs[k][c->cur[k]], (size_t)c->opt.m * 4)) return STR_ERR_CUDA;
+    if (c->opt.sketch == STR_SKETCH_LEVERAGE)
+      for (int k = 0; k < N; ++k) if (c->p_cap[k] && !d2h(c->p[k][c->cur[k]], (size_t)c->p_cap[k] * 8)) return STR_ERR_CUDA;
+  }
+  *len = need;
+  return STR_OK;
+}
+
+str_status str_load(str_ctx** out, const void* buf, size_t len, void* stream) {
+  if (!out || !buf || len < sizeof(SaveHeader)) return STR_ERR_INVALID_ARG;
+  *out = nullptr;
+  SaveHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kSaveMagic) return STR_ERR_INVALID_ARG;
+  const int N = h.N;
+  if (N < 3 || N > STR_MAXN) return STR_ERR_SHAPE;
+  int64_t dims[STR_MAXN];
+  int ranks[STR_MAXN];
+  for (int k = 0; k < N; ++k) { dims[k] = h.I[k]; ranks[k] = h.R[k]; }
+  str_ctx* c = nullptr;
+  TRY(ctx_create(&c, N, dims, ranks, &h.opt, h.t_rows));
+  SaveHeader h2;
+  c->I[N - 1] = h.I[N - 1];
+  if (save_size(c, &h2) > len) { str_destroy(c); return STR_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const char* p = (const char*)buf + sizeof(SaveHeader);
+  str_status st = STR_OK;
+  auto h2d = [&](void* dst, size_t bytes) {
+    if (st == STR_OK && cudaMemcpy(dst, p, bytes, cudaMemcpyHostToDevice) != cudaSuccess) st = STR_ERR_CUDA;
+    p += bytes;
+  };
+  for (int k = 0; k < N - 1; ++k) {
+    const size_t RR = c->RR(k);
+    h2d(c->G64[k][0], c->I[k] * RR * 8);
+    h2d(c->P[k][0], c->I[k] * RR * 8);
+    h2d(c->Q[k][0], RR * RR * 8);
+    h2d(c->E[k][0], RR * RR * 8);
+    if (st == STR_OK && c->compute == 1) st = from_cuda(launch_convert(c->G64[k][0], XT_F64, c->G32[k][0], XT_F32, c->I[k] * RR, s), "convert");
+  }
+  const int RRN = c->RR(N - 1);
+  h2d(c->GT64, (size_t)h.t_rows * RRN * 8);
+  if (st == STR_OK && c->compute == 1) st = from_cuda(launch_convert(c->GT64, XT_F64, c->GT32, XT_F32, h.t_rows * RRN, s), "convert");
+  if (c->opt.sketch != STR_SKETCH_NONE) {
+    for (int k = 0; k < N; ++k) h2d(c->idxs[k][0], (size_t)c->opt.m * 4);
+    if (c->opt.sketch == STR_SKETCH_LEVERAGE)
+      for (int k = 0; k < N; ++k) {
+        if (h.p_rows[k] == 0) continue;
+        if (st == STR_OK) st = ensure_p(c, k, h.p_rows[k]);
+        h2d(c->p[k][0], (size_t)h.p_rows[k] * 8);
+      }
+  }
+  c->step = h.step;
+  c->last_tn = h.last_tn;
+  if (st == STR_OK) st = from_cuda(cudaStreamSynchronize(s), "sync");
+  if (st != STR_OK) { str_destroy(c); return st; }
+  *out = c;
+  return STR_OK;
+}
+
+str_status str_get_stats(const str_ctx* c, str_stats* stats) {
+  if (!c || !stats) return STR_ERR_INVALID_ARG;
+  std::memset(stats, 0, sizeof(*stats));
+  stats->steps = c->step;
+  stats->time_rows = c->t_rows;
+  stats->kernel_launches = c->launches;
+  stats->device_bytes = (int64_t)c->bytes;
+  double piv = 0.0;
+  if (cudaMemcpy(&piv, c->d_pivot, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return STR_ERR_CUDA;
+  stats->min_pivot_ratio = piv;
+  return STR_OK;
+}
+
+str_status str_sync(str_ctx* c) {
+  if (!c) return STR_ERR_INVALID_ARG;
+  STR_CUDA_TRY(cudaDeviceSynchronize());
+  if (c->sticky) return STR_ERR_STATE;
+  int st = 0;
+  STR_CUDA_TRY(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    c->sticky = c->opt.async_status ? 1 : 0;
+    if (st & DEV_ERR_NONFINITE) return STR_ERR_NONFINITE;
+    if (st & DEV_ERR_SINGULAR) return STR_ERR_SINGULAR;
+    return STR_ERR_TIMEOUT;
+  }
+  return STR_OK;
+}
+
+const char* str_status_string(str_status s) {
+  switch (s) {
+    case STR_OK: return "ok";
+    case STR_ERR_INVALID_ARG: return "invalid argument";
+    case STR_ERR_SHAPE: return "unsupported or mismatched shape";
+    case STR_ERR_DTYPE: return "unsupported element type";
+    case STR_ERR_SINGULAR: return "normal-equation matrix not positive definite";
+    case STR_ERR_NONFINITE: return "non-finite value in a slab";
+    case STR_ERR_CAPACITY: return "temporal capacity exceeded";
+    case STR_ERR_OOM: return "device allocation failed";
+    case STR_ERR_CUDA: return "CUDA error";
+    case STR_ERR_TIMEOUT: return "device wait timed out";
+    case STR_ERR_STATE: return "call not valid in this state";
+  }
+  return "unknown status";
+}
+
+const char* str_last_error(void) { return g_last_error.c_str(); }
+
+void str_destroy(str_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (void* p : c->owned) cudaFree(p);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->h_sums) cudaFreeHost(c->h_sums);
+  delete c;
+}
+
+// ---------------------------------------------------------------------------
+// masked fit loss (stateless)
+// ---------------------------------------------------------------------------
+static str_status loss_setup(int N, const int64_t* dims, const int* ranks, str_dtype dtype,
+                             const void* const* cores, const void* X, str_ctx* tmp) {
+  if (!dims || !ranks || !cores || !X) return STR_ERR_INVALID_ARG;
+  if (dtype != STR_F32 && dtype != STR_F64) return STR_ERR_DTYPE;
+  if (N < 3 || N > STR_MAXN) return STR_ERR_SHAPE;
+  for (int k = 0; k < N; ++k) {
+    if (dims[k] < 1 || ranks[k] < 1 || ranks[k] > STR_MAXR || !cores[k]) return STR_ERR_SHAPE;
+  }
+  tmp->N = N;
+  for (int k = 0; k < N; ++k) { tmp->I[k] = dims[k]; tmp->R[k] = ranks[k]; }
+  tmp->R[N] = ranks[0];
+  tmp->compute = dtype == STR_F64 ? 2 : 1;
+  return STR_OK;
+}
+
+str_status tr_masked_loss_fwd(int N, const int64_t* dims, const int* ranks, str_dtype dtype,
+                              const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
+                              double* loss_dev, void* stream) {
+  str_ctx t;
+  TRY(loss_setup(N, dims, ranks, dtype, cores_dev, X_dev, &t));
+  if (!loss_dev) return STR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int kp = N / 2;
+  int64_t rows = 1, cols = 1;
+  for (int k = 0; k < kp; ++k) rows *= dims[k];
+  for (int k = kp; k < N; ++k) cols *= dims[k];
+  const int K = ranks[0] * t.R[kp];
+  const size_t es = dtype == STR_F64 ? 8 : 4;
+  TRY(ws_grow(0, (size_t)rows * K * es));
+  TRY(ws_grow(1, (size_t)cols * K * es));
+  TRY(ws_grow(2, (size_t)recon_blocks(rows, cols) * 16 + 64));
+  STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, 0, kp - 1, 0, 0, g_loss_ws[0].p, s));
+  STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, kp, N - 1, 0, 1, g_loss_ws[1].p, s));
+  int64_t nb = 0;
+  STR_CUDA_TRY(launch_recon(g_loss_ws[0].p, g_loss_ws[1].p, t.compute, rows, cols, K, RM_LOSS, X_dev,
+                            xtype_of(dtype), mask_bits, nullptr, 0, (double*)g_loss_ws[2].p, &nb, s));
+  STR_CUDA_TRY(launch_sum_blocks((double*)g_loss_ws[2].p, nb, 2, (double*)g_loss_ws[2].p + 2 * nb, 0.5, s));
+  STR_CUDA_TRY(cudaMemcpyAsync(loss_dev, (double*)g_loss_ws[2].p + 2 * nb, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return STR_OK;
+}
+
+str_status tr_masked_loss_bwd(int N, const int64_t* dims, const int* ranks, str_dtype dtype,
+                              const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
+                              double grad_scale, void* const* grad_cores_dev, void* stream) {
+  str_ctx t;
+  TRY(loss_setup(N, dims, ranks, dtype, cores_dev, X_dev, &t));
+  if (!grad_cores_dev) return STR_ERR_INVALID_ARG;
+  for (int k = 0; k < N; ++k) if (!grad_cores_dev[k]) return STR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int kp = N / 2;
+  int64_t rows = 1, cols = 1, count = 1;
+  for (int k = 0; k < kp; ++k) rows *= dims[k];
+  for (int k = kp; k < N; ++k) cols *= dims[k];
+  count = rows * cols;
+  const int K = ranks[0] * t.R[kp];
+  const size_t es = dtype == STR_F64 ? 8 : 4;
+  TRY(ws_grow(0, (size_t)rows * K * es));
+  TRY(ws_grow(1, (size_t)cols * K * es));
+  TRY(ws_grow(3, (size_t)count * es));
+  STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, 0, kp - 1, 0, 0, g_loss_ws[0].p, s));
+  STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, kp, N - 1, 0, 1, g_loss_ws[1].p, s));
+  const int xt = xtype_of(dtype);
+  STR_CUDA_TRY(launch_recon(g_loss_ws[0].p, g_loss_ws[1].p, t.compute, rows, cols, K, RM_RESID, X_dev, xt,
+                            mask_bits, g_loss_ws[3].p, xt, nullptr, nullptr, s));
+  // dL/dG_n = -(M .* residual)_[n] G^{!=n}_[2]: dense MTTKRP of the residual
+  for (int n = 0; n < N; ++n) {
+    MttkrpArgs a;
+    a.X = g_loss_ws[3].p;
+    a.xtype = xt;
+    a.N = N;
+    a.n = n;
+    for (int k = 0; k < N; ++k) { a.dim[k] = dims[k]; a.core[k] = cores_dev[k]; }
+    for (int k = 0; k <= N; ++k) a.R[k] = t.R[k];
+    a.compute = t.compute;
+    int64_t J = 1;
+    for (int k = 0; k < N; ++k) if (k != n) J *= dims[k];
+    a.nfib = J;
+    int64_t per = 0;
+    a.splits = mttkrp_plan_splits(a, &per);
+    a.fib_per_split = per;
+    const int RR = t.R[n] * t.R[n + 1];
+    // partials share slot 2 (grown to fit)
+    TRY(ws_grow(2, (size_t)a.splits * dims[n] * RR * es));
+    a.partial = g_loss_ws[2].p;
+    STR_CUDA_TRY(launch_mttkrp(a, s));
+    STR_CUDA_TRY(launch_reduce_partials_to(a.partial, t.compute, a.splits, dims[n] * RR, -grad_scale,
+                                           grad_cores_dev[n], xt, s));
+  }
+  return STR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,387 @@
+// Slab MTTKRP with the TR subchain generated on the fly (never materialised).
+//
+//   P_n increment = X^new_[n] (G^{!=n}_new)_[2]            (Eq. partial, Alg. 4 line 15)
+//   temporal      = X^new_[N] G^{!=N}_[2]                   (Alg. 4 line 9)
+//   sampled       = X_S[n] diag(w) G^{!=n}_S[2]             (Alg. 3, Alg. 5 lines 15-16)
+//
+// Each CTA owns BM rows of mode n and a contiguous range of fibres (split-K).
+// Per chunk of BK fibres it (1) decodes the fibre multi-indices, (2) forms the
+// subchain slices S_f = G_{n+1}(i_{n+1}) ... G_{n-1}(i_{n-1}) in shared memory
+// as a chain of small matrix products, (3) stages the X tile, (4) accumulates
+// the outer products into registers.  Partials go to a per-split buffer that a
+// second kernel sums in a fixed order (deterministic, no atomics).
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace {
+
+template <typename T, bool C> struct ElemT { typedef T type; };
+template <typename T> struct ElemT<T, true> { typedef cplx<T> type; };
+
+template <typename E> __device__ __forceinline__ E ezero();
+template <> __device__ __forceinline__ float ezero<float>() { return 0.f; }
+template <> __device__ __forceinline__ double ezero<double>() { return 0.0; }
+template <> __device__ __forceinline__ cplx<float> ezero<cplx<float>>() { return {0.f, 0.f}; }
+template <> __device__ __forceinline__ cplx<double> ezero<cplx<double>>() { return {0.0, 0.0}; }
+
+// acc += x * conj(s)   (conj is the identity for real types)
+__device__ __forceinline__ void mac(float& acc, float x, float s) { acc = fmaf(x, s, acc); }
+__device__ __forceinline__ void mac(double& acc, double x, double s) { acc = fma(x, s, acc); }
+template <typename T> __device__ __forceinline__ void mac(cplx<T>& acc, cplx<T> x, cplx<T> s) {
+  acc.re += x.re * s.re + x.im * s.im;
+  acc.im += x.im * s.re - x.re * s.im;
+}
+// acc += a * b  (true product, used for the subchain)
+__device__ __forceinline__ void mulacc(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
+__device__ __forceinline__ void mulacc(double& acc, double a, double b) { acc = fma(a, b, acc); }
+template <typename T> __device__ __forceinline__ void mulacc(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+  acc.re += a.re * b.re - a.im * b.im;
+  acc.im += a.re * b.im + a.im * b.re;
+}
+template <typename T> __device__ __forceinline__ T scal(T x, T w) { return x * w; }
+template <typename T> __device__ __forceinline__ cplx<T> scal(cplx<T> x, T w) { return {x.re * w, x.im * w}; }
+
+template <typename E, typename XS> struct LoadX;
+template <typename T> struct LoadX<T, __nv_bfloat16> {
+  static __device__ __forceinline__ T ld(const void* X, int64_t o) {
+    return (T)__bfloat162float(((const __nv_bfloat16*)X)[o]);
+  }
+};
+template <typename T> struct LoadX<T, float> {
+  static __device__ __forceinline__ T ld(const void* X, int64_t o) { return (T)((const float*)X)[o]; }
+};
+template <typename T> struct LoadX<T, double> {
+  static __device__ __forceinline__ T ld(const void* X, int64_t o) { return (T)((const double*)X)[o]; }
+};
+template <typename T, typename S> struct LoadX<cplx<T>, cplx<S>> {
+  static __device__ __forceinline__ cplx<T> ld(const void* X, int64_t o) {
+    const S* p = (const S*)X + 2 * o;
+    return {(T)p[0], (T)p[1]};
+  }
+};
+
+struct SmemPlan {
+  int BK;
+  size_t bytes;
+  int Rmid;
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+__host__ __device__ inline void smem_offsets(int BK, int BM, int RR, int Rb, int Rmid, int esize,
+                                             int tsize, size_t* o) {
+  size_t off = 0;
+  o[0] = off; off = align16(off + (size_t)BK * STR_MAXN * 4);   // sIdx
+  o[1] = off; off = align16(off + (size_t)BK * 8);              // sBase
+  o[2] = off; off = align16(off + (size_t)BK * tsize);          // sW
+  o[3] = off; off = align16(off + (size_t)BK * BM * esize);     // sX
+  o[4] = off; off = align16(off + (size_t)BK * RR * esize);     // sS
+  o[5] = off; off = align16(off + (size_t)BK * Rb * Rmid * esize);  // sT0
+  o[6] = off; off = align16(off + (size_t)BK * Rb * Rmid * esize);  // sT1
+  o[7] = off;
+}
+
+template <typename T, bool C, typename XS, int RPT, int CPT>
+__global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
+  typedef typename ElemT<T, C>::type E;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int N = a.N, n = a.n;
+  const int Ra = a.R[n], Rb = a.R[n + 1];
+  const int RR = Ra * Rb;
+  const int64_t In = a.dim[n];
+  constexpr int BM = 16 * RPT;
+
+  int order[STR_MAXN];
+  int64_t stride[STR_MAXN];
+  int64_t st = 1;
+  for (int k = 0; k < N; ++k) { stride[k] = st; st *= a.dim[k]; }
+  for (int t = 0; t < N - 1; ++t) order[t] = (n + 1 + t) % N;
+  int Rmid = 1;
+  for (int t = 1; t < N - 2; ++t) Rmid = max(Rmid, a.R[order[t] + 1]);
+
+  size_t o[8];
+  smem_offsets(BK, BM, RR, Rb, Rmid, (int)sizeof(E), (int)sizeof(T), o);
+  int32_t* sIdx = (int32_t*)(smem + o[0]);
+  int64_t* sBase = (int64_t*)(smem + o[1]);
+  T* sW = (T*)(smem + o[2]);
+  E* sX = (E*)(smem + o[3]);
+  E* sS = (E*)(smem + o[4]);
+  E* sT[2] = {(E*)(smem + o[5]), (E*)(smem + o[6])};
+
+  const int64_t f_begin = (int64_t)blockIdx.y * a.fib_per_split;
+  const int64_t f_end = min(a.nfib, f_begin + a.fib_per_split);
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int tx = tid & 15, ty = tid >> 4;
+
+  E acc[RPT][CPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q)
+#pragma unroll
+    for (int p = 0; p < CPT; ++p) acc[q][p] = ezero<E>();
+
+  for (int64_t f0 = f_begin; f0 < f_end; f0 += BK) {
+    const int nf = (int)min((int64_t)BK, f_end - f0);
+    // (1) decode fibre multi-indices and base offsets
+    if (tid < nf) {
+      const int64_t f = f0 + tid;
+      int64_t off = 0;
+      double w = a.wscale;
+      if (a.idxs) {
+        for (int k = 0; k < N; ++k) {
+          if (k == n) continue;
+          const int i = a.idxs[(int64_t)k * a.m + f];
+          sIdx[tid * STR_MAXN + k] = i;
+          off += (int64_t)i * stride[k];
+          if (a.leverage) w /= a.p[k][i];
+        }
+      } else {
+        int64_t rem = f;
+        for (int k = 0; k < N; ++k) {
+          if (k == n) continue;
+          const int64_t i = rem % a.dim[k];
+          rem /= a.dim[k];
+          sIdx[tid * STR_MAXN + k] = (int32_t)i;
+          off += i * stride[k];
+        }
+      }
+      sBase[tid] = off;
+      sW[tid] = (T)w;
+      if (a.ws_out && blockIdx.x == 0) a.ws_out[f] = w;
+    }
+    __syncthreads();
+
+    // (2) subchain slices S_f = F_0 F_1 ... F_{N-2},  F_t = G_{order[t]}(i_{order[t]})
+    {
+      const int k0 = order[0], k1 = order[1];
+      const int R0 = a.R[k0], R1 = a.R[k1], R2 = a.R[k1 + 1];
+      const E* G0 = (const E*)a.core[k0];
+      const E* G1 = (const E*)a.core[k1];
+      const bool last = (N == 3);
+      E* dst = last ? sS : sT[0];
+      const int cols = R2;
+      const int total = nf * Rb * cols;
+      for (int e = tid; e < total; e += blockDim.x) {
+        const int jj = e / (Rb * cols);
+        const int rc = e - jj * Rb * cols;
+        const int r = rc / cols, c = rc - r * cols;
+        const E* g0 = G0 + (int64_t)sIdx[jj * STR_MAXN + k0] * R0 * R1;
+        const E* g1 = G1 + (int64_t)sIdx[jj * STR_MAXN + k1] * R1 * R2;
+        E v = ezero<E>();
+        for (int x = 0; x < R1; ++x) mulacc(v, g0[r + R0 * x], g1[x + R1 * c]);
+        if (last) dst[jj * RR + c + Ra * r] = v;      // S(b=r, a=c) -> column a + Ra b
+        else dst[jj * Rb * Rmid + r * Rmid + c] = v;
+      }
+      int cur = 0;
+      int cur_cols = R2;
+      for (int t = 2; t < N - 1; ++t) {
+        __syncthreads();
+        const int k = order[t];
+        const int Rk = a.R[k], Rk1 = a.R[k + 1];
+        const E* Gk = (const E*)a.core[k];
+        const bool fin = (t == N - 2);
+        E* src = sT[cur];
+        E* out = fin ? sS : sT[cur ^ 1];
+        const int tot = nf * Rb * Rk1;
+        for (int e = tid; e < tot; e += blockDim.x) {
+          const int jj = e / (Rb * Rk1);
+          const int rc = e - jj * Rb * Rk1;
+          const int r = rc / Rk1, c = rc - r * Rk1;
+          const E* gk = Gk + (int64_t)sIdx[jj * STR_MAXN + k] * Rk * Rk1;
+          const E* srow = src + jj * Rb * Rmid + r * Rmid;
+          E v = ezero<E>();
+          for (int x = 0; x < cur_cols; ++x) mulacc(v, srow[x], gk[x + Rk * c]);
+          if (fin) out[jj * RR + c + Ra * r] = v;
+          else out[jj * Rb * Rmid + r * Rmid + c] = v;
+        }
+        cur ^= 1;
+        cur_cols = Rk1;
+      }
+    }
+    // (3) X tile: sX[jj][r] = w_f * X_[n](row0 + r, f)
+    for (int e = tid; e < BK * BM; e += blockDim.x) {
+      int jj, r;
+      if (n == 0) { r = e % BM; jj = e / BM; } else { jj = e % BK; r = e / BK; }
+      E v = ezero<E>();
+      const int64_t row = row0 + r;
+      if (jj < nf && row < In) v = scal(LoadX<E, XS>::ld(a.X, sBase[jj] + row * stride[n]), sW[jj]);
+      sX[jj * BM + r] = v;
+    }
+    __syncthreads();
+    if (a.gs_out && blockIdx.x == 0) {
+      E* g = (E*)a.gs_out;
+      for (int e = tid; e < nf * RR; e += blockDim.x) g[(f0 + e / RR) * RR + (e % RR)] = sS[e];
+    }
+    // (4) outer-product accumulation
+    for (int jj = 0; jj < nf; ++jj) {
+      E xv[RPT], sv[CPT];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) xv[q] = sX[jj * BM + ty + 16 * q];
+#pragma unroll
+      for (int p = 0; p < CPT; ++p) {
+        const int c = tx + 16 * p;
+        sv[p] = (c < RR) ? sS[jj * RR + c] : ezero<E>();
+      }
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+#pragma unroll
+        for (int p = 0; p < CPT; ++p) mac(acc[q][p], xv[q], sv[p]);
+    }
+    __syncthreads();
+  }
+  E* out = (E*)a.partial + (size_t)blockIdx.y * In * RR;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int64_t row = row0 + ty + 16 * q;
+#pragma unroll
+    for (int p = 0; p < CPT; ++p) {
+      const int c = tx + 16 * p;
+      if (row < In && c < RR) out[row * RR + c] = acc[q][p];
+    }
+  }
+}
+
+int plan_rmid(const MttkrpArgs& a) {
+  int order[STR_MAXN];
+  for (int t = 0; t < a.N - 1; ++t) order[t] = (a.n + 1 + t) % a.N;
+  int Rmid = 1;
+  for (int t = 1; t < a.N - 2; ++t) Rmid = std::max(Rmid, a.R[order[t] + 1]);
+  return Rmid;
+}
+
+size_t smem_bytes(const MttkrpArgs& a, int BK, int BM) {
+  const int esize = (a.compute == 2 ? 8 : 4) * (a.cplx ? 2 : 1);
+  const int tsize = a.compute == 2 ? 8 : 4;
+  size_t o[8];
+  smem_offsets(BK, BM, a.R[a.n] * a.R[a.n + 1], a.R[a.n + 1], plan_rmid(a), esize, tsize, o);
+  return o[7];
+}
+
+template <typename T, bool C, typename XS, int RPT, int CPT>
+cudaError_t launch_t(const MttkrpArgs& a, cudaStream_t s) {
+  constexpr int BM = 16 * RPT;
+  int BK = 32;
+  while (BK > 4 && smem_bytes(a, BK, BM) > 96 * 1024) BK /= 2;
+  const size_t sm = smem_bytes(a, BK, BM);
+  auto kern = mttkrp_kernel<T, C, XS, RPT, CPT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)ceil_div_i(a.dim[a.n], BM), (unsigned)a.splits);
+  kern<<<grid, 256, sm, s>>>(a, BK);
+  return cudaGetLastError();
+}
+
+template <typename T, bool C, typename XS>
+cudaError_t launch_rc(const MttkrpArgs& a, cudaStream_t s) {
+  const int RR = a.R[a.n] * a.R[a.n + 1];
+  const bool small_rows = a.dim[a.n] <= 16;
+  if (RR <= 16) return small_rows ? launch_t<T, C, XS, 1, 1>(a, s) : launch_t<T, C, XS, 4, 1>(a, s);
+  if (RR <= 64) return small_rows ? launch_t<T, C, XS, 1, 4>(a, s) : launch_t<T, C, XS, 4, 4>(a, s);
+  return small_rows ? launch_t<T, C, XS, 1, 10>(a, s) : launch_t<T, C, XS, 4, 10>(a, s);
+}
+
+}  // namespace
+
+int mttkrp_plan_splits(const MttkrpArgs& a, int64_t* fib_per_split) {
+  const int BM = a.dim[a.n] <= 16 ? 16 : 64;
+  const int gx = ceil_div_i(a.dim[a.n], BM);
+  const int target = 4 * 152;
+  int64_t min_chunk = 128;
+  int64_t splits = std::max<int64_t>(1, target / std::max(1, gx));
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, (a.nfib + min_chunk - 1) / min_chunk));
+  int64_t per = (a.nfib + splits - 1) / splits;
+  per = std::max<int64_t>(per, 1);
+  splits = (a.nfib + per - 1) / per;
+  if (splits < 1) splits = 1;
+  *fib_per_split = per;
+  return (int)splits;
+}
+
+cudaError_t launch_mttkrp(const MttkrpArgs& a, cudaStream_t s) {
+  if (a.cplx) {
+    if (a.compute == 2) return launch_rc<double, true, cplx<double>>(a, s);
+    return launch_rc<float, true, cplx<float>>(a, s);
+  }
+  if (a.compute == 2) {
+    switch (a.xtype) {
+      case XT_F64: return launch_rc<double, false, double>(a, s);
+      case XT_F32: return launch_rc<double, false, float>(a, s);
+      default: return launch_rc<double, false, __nv_bfloat16>(a, s);
+    }
+  }
+  switch (a.xtype) {
+    case XT_F64: return launch_rc<float, false, double>(a, s);
+    case XT_F32: return launch_rc<float, false, float>(a, s);
+    default: return launch_rc<float, false, __nv_bfloat16>(a, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fixed-order reduction of split partials
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void reduce_real_kernel(const T* partial, int splits, int64_t count, const double* base,
+                                   double scale, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < splits; ++k) s += (double)partial[(int64_t)k * count + i];
+    out[i] = (base ? base[i] : 0.0) + scale * s;
+  }
+}
+template <typename T>
+__global__ void reduce_cplx_kernel(const T* partial, int splits, int64_t count, double scale,
+                                   double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < splits; ++k) {
+      re += (double)partial[2 * ((int64_t)k * count + i)];
+      im += (double)partial[2 * ((int64_t)k * count + i) + 1];
+    }
+    out[2 * i] = scale * re;
+    out[2 * i + 1] = scale * im;
+  }
+}
+template <typename T, typename O>
+__global__ void reduce_to_kernel(const T* partial, int splits, int64_t count, double scale, O* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < splits; ++k) s += (double)partial[(int64_t)k * count + i];
+    out[i] = (O)(scale * s);
+  }
+}
+
+static unsigned grid_for(int64_t count) {
+  int64_t g = (count + 255) / 256;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 4096));
+}
+
+cudaError_t launch_reduce_partials(const void* partial, int compute, int cplx, int splits,
+                                   int64_t count, const double* base, double scale, double* out,
+                                   cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (cplx) {
+    if (compute == 2) reduce_cplx_kernel<double><<<grid_for(count), 256, 0, s>>>((const double*)partial, splits, count, scale, out);
+    else reduce_cplx_kernel<float><<<grid_for(count), 256, 0, s>>>((const float*)partial, splits, count, scale, out);
+  } else {
+    if (compute == 2) reduce_real_kernel<double><<<grid_for(count), 256, 0, s>>>((const double*)partial, splits, count, base, scale, out);
+    else reduce_real_kernel<float><<<grid_for(count), 256, 0, s>>>((const float*)partial, splits, count, base, scale, out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials_to(const void* partial, int compute, int splits, int64_t count,
+                                      double scale, void* out, int out_type, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (compute == 2) {
+    if (out_type == XT_F64) reduce_to_kernel<double, double><<<grid_for(count), 256, 0, s>>>((const double*)partial, splits, count, scale, (double*)out);
+    else reduce_to_kernel<double, float><<<grid_for(count), 256, 0, s>>>((const double*)partial, splits, count, scale, (float*)out);
+  } else {
+    if (out_type == XT_F64) reduce_to_kernel<float, double><<<grid_for(count), 256, 0, s>>>((const float*)partial, splits, count, scale, (double*)out);
+    else reduce_to_kernel<float, float><<<grid_for(count), 256, 0, s>>>((const float*)partial, splits, count, scale, (float*)out);
+  }
+  return cudaGetLastError();
+}

@@ -1,0 +1,324 @@
+// Sketch kernels for rSTR: Philox row draws (Eq. sampDS; Lemma lev_est),
+// random sign flips and unitary DFT mixing (Definition of the KSRFT), the
+// weighted Gram of the sampled subchain (Alg. 5 line 16), and small utilities.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "kernels.cuh"
+
+// ---------------------------------------------------------------------------
+// row draws: uniform floor(u I / 2^64), or weighted from the sequential CDF of p
+// ---------------------------------------------------------------------------
+__global__ void draw_indices_kernel(int32_t* __restrict__ out, int64_t m, int64_t I, uint64_t seed,
+                                    int k, uint64_t tau, uint32_t sid, const double* __restrict__ p) {
+  extern __shared__ double cdf[];
+  __shared__ int s_last;
+  if (p) {
+    if (threadIdx.x == 0) {
+      double c = 0.0;
+      int last = (int)I - 1;
+      for (int64_t i = 0; i < I; ++i) {
+        c = c + p[i];     // sequential left-to-right prefix sums
+        cdf[i] = c;
+      }
+      for (int64_t i = I - 1; i >= 0; --i)
+        if (p[i] > 0.0) { last = (int)i; break; }
+      s_last = last;
+    }
+    __syncthreads();
+  }
+  for (int64_t sidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sidx < m;
+       sidx += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t u = draw_u64(seed, (uint64_t)sidx, (uint64_t)k, tau, 0u, sid);
+    int64_t idx;
+    if (p) {
+      const double v = (double)(u >> 11) * 0x1.0p-53;
+      const double target = v * cdf[I - 1];
+      // first i with cdf[i] > target
+      int64_t lo = 0, hi = I;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cdf[mid] > target) hi = mid; else lo = mid + 1;
+      }
+      idx = (lo < I) ? lo : s_last;
+    } else {
+      idx = (int64_t)__umul64hi(u, (uint64_t)I);
+    }
+    out[sidx] = (int32_t)idx;
+  }
+}
+
+cudaError_t launch_draw_indices(int32_t* out, int64_t m, int64_t I, uint64_t seed, int k,
+                                uint64_t tau, uint32_t stream_id, const double* p, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  size_t sm = p ? (size_t)I * sizeof(double) : 0;
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(draw_indices_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((m + 511) / 512, 152));
+  draw_indices_kernel<<<(unsigned)blocks, 512, sm, s>>>(out, m, I, seed, k, tau, stream_id, p);
+  return cudaGetLastError();
+}
+
+__global__ void signs_kernel(double* d, int64_t I, uint64_t seed, int k, uint64_t tau, uint32_t sid) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < I;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t u = draw_u64(seed, (uint64_t)i, (uint64_t)k, tau, 1u, sid);
+    d[i] = (u & 1ull) ? -1.0 : 1.0;
+  }
+}
+
+cudaError_t launch_signs(double* d, int64_t I, uint64_t seed, int k, uint64_t tau,
+                         uint32_t stream_id, cudaStream_t s) {
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((I + 255) / 256, 256));
+  signs_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, I, seed, k, tau, stream_id);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// weighted Gram of sampled rows: out = base + sum_s w_s Re(g_s g_s^H), FP64
+// 16x16 output tile per CTA, sample chunks staged in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T, bool C>
+__global__ void __launch_bounds__(256) wgram_kernel(const T* __restrict__ g, const double* __restrict__ w,
+                                                    int64_t m, int RR, const double* __restrict__ base,
+                                                    double* __restrict__ out) {
+  constexpr int CH = 32;
+  constexpr int W = C ? 2 : 1;
+  __shared__ double sa[CH][16 * W], sb[CH][16 * W];
+  __shared__ double sw[CH];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+  double acc = 0.0;
+  for (int64_t s0 = 0; s0 < m; s0 += CH) {
+    const int ns = (m - s0 < CH) ? (int)(m - s0) : CH;
+    for (int e = threadIdx.x; e < CH * 16 * W; e += 256) {
+      const int ss = e / (16 * W), x = e % (16 * W);
+      const int cc = x / W, part = x % W;
+      double va = 0.0, vb = 0.0;
+      if (ss < ns) {
+        if (r0 + cc < RR) va = (double)g[((s0 + ss) * RR + r0 + cc) * W + part];
+        if (c0 + cc < RR) vb = (double)g[((s0 + ss) * RR + c0 + cc) * W + part];
+      }
+      sa[ss][x] = va;
+      sb[ss][x] = vb;
+    }
+    for (int e = threadIdx.x; e < CH; e += 256) sw[e] = (e < ns) ? (w ? w[s0 + e] : 1.0) : 0.0;
+    __syncthreads();
+    for (int ss = 0; ss < ns; ++ss) {
+      double v;
+      if (C) v = sa[ss][2 * ty] * sb[ss][2 * tx] + sa[ss][2 * ty + 1] * sb[ss][2 * tx + 1];
+      else v = sa[ss][ty] * sb[ss][tx];
+      acc = fma(sw[ss], v, acc);
+    }
+    __syncthreads();
+  }
+  const int r = r0 + ty, c = c0 + tx;
+  if (r < RR && c < RR) out[(int64_t)r * RR + c] = (base ? base[(int64_t)r * RR + c] : 0.0) + acc;
+}
+
+cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const double* w, int64_t m,
+                                 int RR, const double* base, double* out, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div_i(RR, 16), (unsigned)ceil_div_i(RR, 16));
+  if (compute == 2) {
+    if (cplx) wgram_kernel<double, true><<<grid, 256, 0, s>>>((const double*)gs, w, m, RR, base, out);
+    else wgram_kernel<double, false><<<grid, 256, 0, s>>>((const double*)gs, w, m, RR, base, out);
+  } else {
+    if (cplx) wgram_kernel<float, true><<<grid, 256, 0, s>>>((const float*)gs, w, m, RR, base, out);
+    else wgram_kernel<float, false><<<grid, 256, 0, s>>>((const float*)gs, w, m, RR, base, out);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// unitary DFT along one mode with a sign pre-multiply (X x_j F_j D_j).
+// A CTA takes FB fibres that are adjacent in memory and stages them [L][FB].
+// Twiddles: cos/sin(2 pi j / L) for j < L, computed once on the host side of
+// the launch in FP64 and indexed by (k * i) mod L.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void dft_mode_kernel(const void* __restrict__ in, int in_type, T* __restrict__ out,
+                                int64_t L, int64_t inner, int64_t nfib, const double* __restrict__ d,
+                                const double* __restrict__ tw, int FB) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sre = (T*)smraw;                 // L * FB
+  T* sim = sre + L * FB;              // L * FB
+  T* cs = sim + L * FB;               // L
+  T* sn = cs + L;                     // L
+  for (int64_t j = threadIdx.x; j < L; j += blockDim.x) { cs[j] = (T)tw[2 * j]; sn[j] = (T)tw[2 * j + 1]; }
+  const T scale = (T)(1.0 / sqrt((double)L));
+  for (int64_t fb0 = (int64_t)blockIdx.x * FB; fb0 < nfib; fb0 += (int64_t)gridDim.x * FB) {
+    // fibre f: inner index = f % inner, outer = f / inner; element i at
+    // outer * L * inner + i * inner + inner_idx
+    for (int64_t e = threadIdx.x; e < L * FB; e += blockDim.x) {
+      const int ff = (int)(e % FB);
+      const int64_t i = e / FB;
+      const int64_t f = fb0 + ff;
+      T re = 0, im = 0;
+      if (f < nfib) {
+        const int64_t o = (f / inner) * L * inner + i * inner + (f % inner);
+        switch (in_type) {
+          case XT_BF16: re = (T)__bfloat162float(((const __nv_bfloat16*)in)[o]); break;
+          case XT_F32: re = (T)((const float*)in)[o]; break;
+          case XT_F64: re = (T)((const double*)in)[o]; break;
+          case XT_C32: re = (T)((const float*)in)[2 * o]; im = (T)((const float*)in)[2 * o + 1]; break;
+          default: re = (T)((const double*)in)[2 * o]; im = (T)((const double*)in)[2 * o + 1]; break;
+        }
+        if (d) { re *= (T)d[i]; im *= (T)d[i]; }
+      }
+      sre[i * FB + ff] = re;
+      sim[i * FB + ff] = im;
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < L * FB; e += blockDim.x) {
+      const int ff = (int)(e % FB);
+      const int64_t kk = e / FB;
+      const int64_t f = fb0 + ff;
+      T are = 0, aim = 0;
+      int64_t ph = 0;   // (kk * i) mod L
+      for (int64_t i = 0; i < L; ++i) {
+        const T c = cs[ph], sv = sn[ph];     // F(k,i) = c - i s
+        const T xr = sre[i * FB + ff], xi = sim[i * FB + ff];
+        are += c * xr + sv * xi;
+        aim += c * xi - sv * xr;
+        ph += kk;
+        if (ph >= L) ph -= L;
+      }
+      if (f < nfib) {
+        const int64_t o = (f / inner) * L * inner + kk * inner + (f % inner);
+        out[2 * o] = are * scale;
+        out[2 * o + 1] = aim * scale;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// twiddle tables cached per length (host-computed cos/sin in FP64)
+static std::mutex g_tw_mu;
+static std::map<std::pair<int, int64_t>, double*> g_tw;
+
+static const double* twiddles(int64_t L) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto key = std::make_pair(dev, L);
+  auto it = g_tw.find(key);
+  if (it != g_tw.end()) return it->second;
+  std::vector<double> h(2 * L);
+  for (int64_t j = 0; j < L; ++j) {
+    const double th = 2.0 * 3.14159265358979323846 * (double)j / (double)L;
+    h[2 * j] = cos(th);
+    h[2 * j + 1] = sin(th);
+  }
+  double* dptr = nullptr;
+  if (cudaMalloc(&dptr, 2 * L * sizeof(double)) != cudaSuccess) return nullptr;
+  cudaMemcpy(dptr, h.data(), 2 * L * sizeof(double), cudaMemcpyHostToDevice);
+  g_tw[key] = dptr;
+  return dptr;
+}
+
+cudaError_t launch_dft_mode(const void* in, int in_type, void* out, int out_cplx_compute, int N,
+                            const int64_t* dims, int mode, const double* d, cudaStream_t s) {
+  const int64_t L = dims[mode];
+  int64_t inner = 1, total = 1;
+  for (int k = 0; k < N; ++k) { total *= dims[k]; if (k < mode) inner *= dims[k]; }
+  const int64_t nfib = total / L;
+  const double* tw = twiddles(L);
+  if (!tw) return cudaErrorMemoryAllocation;
+  const int tsize = out_cplx_compute == 2 ? 8 : 4;
+  int FB = 16;
+  while (FB > 1 && (size_t)(2 * L * FB + 2 * L) * tsize > 96 * 1024) FB /= 2;
+  const size_t sm = (size_t)(2 * L * FB + 2 * L) * tsize;
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nfib + FB - 1) / FB, 152 * 8));
+  if (out_cplx_compute == 2) {
+    cudaFuncSetAttribute(dft_mode_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dft_mode_kernel<double><<<(unsigned)blocks, 256, sm, s>>>(in, in_type, (double*)out, L, inner, nfib, d, tw, FB);
+  } else {
+    cudaFuncSetAttribute(dft_mode_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dft_mode_kernel<float><<<(unsigned)blocks, 256, sm, s>>>(in, in_type, (float*)out, L, inner, nfib, d, tw, FB);
+  }
+  return cudaGetLastError();
+}
+
+// out[k][c] = base[k][c] + Re( d_k * sum_i conj(F(i,k)) Y[i][c] ),
+// conj(F(i,k)) = (cos th + i sin th)/sqrt(L), th = 2 pi (i k mod L) / L
+__global__ void unmix_rows_kernel(const double* __restrict__ Y, int64_t L, int RR,
+                                  const double* __restrict__ d, const double* __restrict__ tw,
+                                  const double* __restrict__ base, double* __restrict__ out) {
+  const double scale = 1.0 / sqrt((double)L);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L * RR;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / RR;
+    const int c = (int)(e % RR);
+    double acc = 0.0;
+    int64_t ph = 0;
+    for (int64_t i = 0; i < L; ++i) {
+      acc += tw[2 * ph] * Y[2 * (i * RR + c)] - tw[2 * ph + 1] * Y[2 * (i * RR + c) + 1];
+      ph += k;
+      if (ph >= L) ph -= L;
+    }
+    out[e] = (base ? base[e] : 0.0) + d[k] * acc * scale;
+  }
+}
+
+cudaError_t launch_unmix_rows(const double* Y, int64_t L, int RR, const double* d,
+                              const double* base, double* out, cudaStream_t s) {
+  const double* tw = twiddles(L);
+  if (!tw) return cudaErrorMemoryAllocation;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((L * RR + 255) / 256, 2048));
+  unmix_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y, L, RR, d, tw, base, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// utilities
+// ---------------------------------------------------------------------------
+template <typename I, typename O>
+__global__ void convert_kernel(const I* __restrict__ in, O* __restrict__ out, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (O)in[i];
+}
+
+cudaError_t launch_convert(const void* in, int in_type, void* out, int out_type, int64_t count,
+                           cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 4096));
+  if (in_type == XT_F64 && out_type == XT_F32) convert_kernel<double, float><<<blocks, 256, 0, s>>>((const double*)in, (float*)out, count);
+  else if (in_type == XT_F32 && out_type == XT_F64) convert_kernel<float, double><<<blocks, 256, 0, s>>>((const float*)in, (double*)out, count);
+  else if (in_type == XT_F64 && out_type == XT_F64) convert_kernel<double, double><<<blocks, 256, 0, s>>>((const double*)in, (double*)out, count);
+  else if (in_type == XT_F32 && out_type == XT_F32) convert_kernel<float, float><<<blocks, 256, 0, s>>>((const float*)in, (float*)out, count);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void check_finite_kernel(const T* __restrict__ x, int64_t count, int* status) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!isfinite((double)x[i])) bad = true;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, DEV_ERR_NONFINITE);
+}
+__global__ void check_finite_bf16_kernel(const __nv_bfloat16* __restrict__ x, int64_t count, int* status) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(__bfloat162float(x[i]))) bad = true;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, DEV_ERR_NONFINITE);
+}
+
+cudaError_t launch_check_finite(const void* X, int xtype, int64_t count, int* status, cudaStream_t s) {
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 8));
+  if (xtype == XT_F64) check_finite_kernel<double><<<blocks, 256, 0, s>>>((const double*)X, count, status);
+  else if (xtype == XT_F32) check_finite_kernel<float><<<blocks, 256, 0, s>>>((const float*)X, count, status);
+  else check_finite_bf16_kernel<<<blocks, 256, 0, s>>>((const __nv_bfloat16*)X, count, status);
+  return cudaGetLastError();
+}

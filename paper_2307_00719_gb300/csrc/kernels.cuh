@@ -1,0 +1,114 @@
+// Internal kernel launchers of the STR / rSTR library (not part of the C ABI).
+#pragma once
+#include "common.cuh"
+
+// element-storage codes for slabs / intermediates
+enum XType : int { XT_BF16 = 0, XT_F32 = 1, XT_F64 = 2, XT_C32 = 3, XT_C64 = 4 };
+
+// ---------------------------------------------------------------------------
+// MTTKRP with an on-the-fly subchain:
+//   out[split][i_n][c] = sum_{fibres f in split} w_f * X_[n](i_n, f) * S_f(c)
+// S_f(c = a + R_n b) = [G_{n+1}(i_{n+1}) ... G_{n-1}(i_{n-1})](b, a)   (Def. subchain)
+// Fibres are either every fibre of the slab (dense) or the sampled rows
+// idxs(s, k) (Alg. 3).  Complex mode multiplies by conj(S) (KSRFT, Sec. 3.3).
+// ---------------------------------------------------------------------------
+struct MttkrpArgs {
+  const void* X = nullptr;
+  int xtype = XT_F32;
+  int N = 0, n = 0;                       // order, mode (0-based)
+  int64_t dim[STR_MAXN] = {};             // slab sizes I_1..I_{N-1}, t
+  const void* core[STR_MAXN] = {};        // compute-type cores, [i][R_{k+1}][R_k]
+  int R[STR_MAXN + 1] = {};               // R_1..R_N, R[N] = R[0]
+  int64_t nfib = 0;                       // dense: J_n; sampled: m
+  const int32_t* idxs = nullptr;          // sampled: idxs[k * m + s]
+  int64_t m = 0;
+  const double* p[STR_MAXN] = {};         // leverage: w_s = wscale / prod_{k!=n} p_k(idx_k(s))
+  int leverage = 0;
+  double wscale = 1.0;                    // weight multiplier
+  void* partial = nullptr;                // [splits][I_n][RR] compute-type elements
+  int splits = 1;
+  int64_t fib_per_split = 0;
+  void* gs_out = nullptr;                 // sampled: G_S[s][c] (compute type)
+  double* ws_out = nullptr;               // sampled: w_s
+  int compute = 2;                        // 1 = f32, 2 = f64
+  int cplx = 0;
+};
+int mttkrp_plan_splits(const MttkrpArgs& a, int64_t* fib_per_split);
+cudaError_t launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
+
+// out[i] = (base ? base[i] : 0) + scale * sum_s partial[s][i]   (FP64 sums, fixed order)
+// complex partials -> complex FP64 out (interleaved), base ignored.
+cudaError_t launch_reduce_partials(const void* partial, int compute, int cplx, int splits,
+                                   int64_t count, const double* base, double scale,
+                                   double* out, cudaStream_t s);
+// same, writing compute-type float output (for gradients) with scale
+cudaError_t launch_reduce_partials_to(const void* partial, int compute, int splits, int64_t count,
+                                      double scale, void* out, int out_type, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Gram of a core unfolding A = G_{(2)} (I x RR):  M = A^T A and its
+// transfer-matrix permutation E[(a + Ra a'), (b + Rb b')] = M[a + Ra b, a' + Ra b'].
+// ---------------------------------------------------------------------------
+cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double* M, double* E,
+                             cudaStream_t s);
+// C = A(MxK) B(KxN), FP64.  If perm_Ra > 0 the result W (rows (b + Rb b'), cols
+// (a + Ra a')) is scattered into Q[(a + Ra b), (a' + Ra b')] = base + W (ring epilogue).
+cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, int K, int N,
+                          int perm_Ra, int perm_Rb, const double* base, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Cholesky: Q = L L^T (one CTA, FP64, shared memory), pivot check -> status.
+// Solve rows: out_row = p_row Q^{-1}; leverage mode: lev[r] = ||L^{-1} p_row||^2 / n.
+// ---------------------------------------------------------------------------
+cudaError_t launch_chol_factor(const double* Q, int n, double* L, double* invdiag, int* status,
+                               double* pivot_ratio, cudaStream_t s);
+cudaError_t launch_chol_solve(const double* L, const double* invdiag, int n, const double* P,
+                              int64_t rows, double* out64, float* out32, double* lev,
+                              cudaStream_t s);
+cudaError_t launch_fill(double* p, int64_t count, double v, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// sketches
+// ---------------------------------------------------------------------------
+cudaError_t launch_draw_indices(int32_t* out, int64_t m, int64_t I, uint64_t seed, int k,
+                                uint64_t tau, uint32_t stream_id, const double* p, cudaStream_t s);
+cudaError_t launch_signs(double* d, int64_t I, uint64_t seed, int k, uint64_t tau,
+                         uint32_t stream_id, cudaStream_t s);
+// out[c][c'] = base + sum_s w_s Re(g_s[c] conj(g_s[c']))  (FP64 accumulate)
+cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const double* w,
+                                 int64_t m, int RR, const double* base, double* out,
+                                 cudaStream_t s);
+// unitary DFT with sign pre-multiply along mode `mode` of a tensor with dims[N]:
+// out(.., k, ..) = sum_i F(k, i) d_i in(.., i, ..),  F(k,i) = exp(-2 pi i k i / L) / sqrt(L)
+cudaError_t launch_dft_mode(const void* in, int in_type, void* out, int out_cplx_compute, int N,
+                            const int64_t* dims, int mode, const double* d, cudaStream_t s);
+// out[k][c] = base[k][c] + Re( d_k * sum_i conj(F(i, k)) Y[i][c] )  (unmix rows, Y complex FP64)
+cudaError_t launch_unmix_rows(const double* Y, int64_t L, int RR, const double* d,
+                              const double* base, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// utilities
+// ---------------------------------------------------------------------------
+cudaError_t launch_convert(const void* in, int in_type, void* out, int out_type, int64_t count,
+                           cudaStream_t s);
+cudaError_t launch_check_finite(const void* X, int xtype, int64_t count, int* status,
+                                cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// reconstruction / fit error / masked loss (TR format, Sec. 1)
+//   Xhat[row + rows*col] = sum_c Lm[row][c] Rm[col][c]
+// ---------------------------------------------------------------------------
+// table[j][a + Rf * b] = [G_{k0}(i_{k0}) ... G_{k1}(i_{k1})](a, b)   (transpose=0)
+// table[j][a + Rl * b] = [..](b, a)  with Rl the last right rank    (transpose=1)
+// j runs over (i_{k0}, .., i_{k1}) with i_{k0} fastest.  core k0 may start at row t_off.
+cudaError_t launch_chain_table(const void* const* cores, int compute, const int* R, int N,
+                               const int64_t* dims, int k0, int k1, int64_t row_off_last,
+                               int transpose, void* table, cudaStream_t s);
+enum ReconMode : int { RM_WRITE = 0, RM_FIT = 1, RM_LOSS = 2, RM_RESID = 3 };
+cudaError_t launch_recon(const void* Lm, const void* Rm, int compute, int64_t rows, int64_t cols,
+                         int K, int mode, const void* X, int xtype, const uint32_t* mask,
+                         void* out, int out_type, double* block_sums, int64_t* nblocks,
+                         cudaStream_t s);
+cudaError_t launch_sum_blocks(const double* block_sums, int64_t nblocks, int width, double* out,
+                              double scale, cudaStream_t s);
+int recon_blocks(int64_t rows, int64_t cols);

@@ -1,0 +1,50 @@
+"""Batched updates of independent streams and checkpoint/resume."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import dev, lib, perturbed_init, problem
+
+pytestmark = pytest.mark.gpu
+
+
+def test_batch_equals_individual_updates():
+    p = lib()
+    specs = synth.uneven_streams(count=6, steps=3, seed=5, dim_range=(8, 40), rank_range=(2, 5),
+                                 tnew_range=(1, 6), t_init=6)
+    made = []
+    for i, s in enumerate(specs):
+        T = s.t_init + sum(s.t_news)
+        G, X = problem(s.dims, T, s.ranks, 100 + i)
+        init = perturbed_init(G, s.t_init, i)
+        a = p.str_init_cores(init, X0=dev(X[..., :s.t_init]), compute="f32")
+        b = p.str_init_cores(init, X0=dev(X[..., :s.t_init]), compute="f32")
+        made.append((s, X, a, b))
+    t = [s.t_init for s, _, _, _ in made]
+    for step in range(3):
+        slabs = [dev(X[..., t[i]:t[i] + s.t_news[step]], ) for i, (s, X, _, _) in enumerate(made)]
+        p.str_update_batch([a for _, _, a, _ in made], slabs)
+        for i, (s, X, a, b) in enumerate(made):
+            b.update(slabs[i])
+            t[i] += s.t_news[step]
+    for s, X, a, b in made:
+        for n in (1, 2, 3):
+            assert np.array_equal(a.core(n), b.core(n))
+
+
+@pytest.mark.parametrize("sketch", ["none", "leverage", "ksrft"])
+def test_checkpoint_resume_is_bit_identical(sketch):
+    p = lib()
+    G, X = problem((16, 12), 24, (2, 3, 2), 9)
+    init = perturbed_init(G, 8, 9)
+    a = p.str_init_cores(init, X0=dev(X[..., :8]), sketch=sketch, m=80, seed=4)
+    upd = (lambda c, x: c.update(x)) if sketch == "none" else (lambda c, x: c.rupdate(x))
+    upd(a, dev(X[..., 8:12]))
+    blob = a.save()
+    b = p.Stream.load(blob)
+    for t0 in (12, 16, 20):
+        upd(a, dev(X[..., t0:t0 + 4]))
+        upd(b, dev(X[..., t0:t0 + 4]))
+    for n in (1, 2, 3):
+        assert np.array_equal(a.core(n), b.core(n))
+    assert a.time_rows() == b.time_rows() == 24

@@ -1,0 +1,63 @@
+"""Masked TR fit loss and its hand-written backward on the GPU."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.loss import closed_form_grad, masked_loss, masked_loss_grad
+from gpu_util import dev, lib, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _abi_cores(G, dtype):
+    import torch
+    import paper_2307_00719_gb300 as p
+    return [torch.from_numpy(a).to("cuda", dtype) for a in p.cores_to_abi(G)]
+
+
+def _abi_to_paper(g, Ra, Rb):
+    g = g.detach().double().cpu().numpy()
+    return g.transpose(2, 0, 1)
+
+
+@pytest.mark.parametrize("dtype_name,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_masked_loss_fwd_bwd(dtype_name, tol):
+    import torch
+    p = lib()
+    dt = torch.float64 if dtype_name == "f64" else torch.float32
+    dims, ranks = (8, 8, 8, 8, 5), (3, 3, 3, 3, 3)
+    G = synth.gaussian_cores(dims, ranks, 3)
+    X = synth.gaussian_tensor(dims, 4)
+    mask = synth.bernoulli_keep_mask(dims, 0.3, 3)
+    bits = torch.from_numpy(synth.pack_mask_bits(mask).view(np.int32)).cuda()
+    cores = _abi_cores(G, dt)
+    for use_mask in (True, False):
+        mb = bits if use_mask else None
+        mk = mask if use_mask else None
+        loss = p.tr_masked_loss_fwd(cores, dev(X, dt), mb).item()
+        ref = masked_loss(X, G, mk)
+        assert abs(loss - ref) <= tol * ref
+        grads = p.tr_masked_loss_bwd(cores, dev(X, dt), mb, 1.0)
+        gref = masked_loss_grad(X, G, mk)
+        for n in range(5):
+            assert rel(_abi_to_paper(grads[n], 0, 0), gref[n]) <= tol * 10
+    cf = closed_form_grad(X, G)
+    grads = p.tr_masked_loss_bwd(cores, dev(X, dt), None, 1.0)
+    for n in range(5):
+        assert rel(_abi_to_paper(grads[n], 0, 0), cf[n]) <= tol * 10
+
+
+def test_autograd_function():
+    import torch
+    p = lib()
+    dims, ranks = (6, 5, 4, 7), (2, 3, 2, 2)
+    G = synth.gaussian_cores(dims, ranks, 5)
+    X = synth.gaussian_tensor(dims, 6)
+    mask = synth.bernoulli_keep_mask(dims, 0.3, 7)
+    bits = torch.from_numpy(synth.pack_mask_bits(mask).view(np.int32)).cuda()
+    cores = [c.requires_grad_(True) for c in _abi_cores(G, torch.float64)]
+    loss = p.TRFitLoss.apply(dev(X), bits, *cores)
+    (2.0 * loss).backward()
+    gref = masked_loss_grad(X, G, mask)
+    for n in range(4):
+        assert rel(_abi_to_paper(cores[n].grad, 0, 0), 2.0 * gref[n]) <= 1e-12
