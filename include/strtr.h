@@ -12,7 +12,7 @@
  * --------------------------------
  * - Order N >= 3.  Modes 1..N-1 are spatial with fixed sizes I_1..I_{N-1};
  *   mode N is time.  TR-ranks R_1..R_N, R_{N+1} = R_1, 1 <= R_n <= 16 and
- *   R_n R_{n+1} <= 256.
+ *   R_n R_{n+1} <= 160.
  * - Tensors are dense with the paper's linear index (Sec. 2): element
  *   (i_1, .., i_N) sits at offset i_1 + I_1 (i_2 + I_2 (i_3 + ...)), i.e. i_1
  *   fastest.  A torch tensor of shape (t, I_{N-1}, .., I_1) is such a buffer.
@@ -90,6 +90,8 @@ typedef struct {
                             *     (state unchanged on error);
                             * 1 = no synchronisation; device errors surface at the next
                             *     call or str_sync() and then make the context sticky-failed */
+  int profile;             /* 1 = time every kernel launch with CUDA events on the launch
+                            *     stream (per-class totals in str_stats) */
 } str_options;
 
 /* Fills *opt with the defaults listed above (compute F64, sweeps 1, rescale 1,
@@ -186,13 +188,31 @@ str_status str_get_samples(const str_ctx* ctx, int k, int64_t* host_idxs, double
 str_status str_save(const str_ctx* ctx, void* buf, size_t* len);
 str_status str_load(str_ctx** out, const void* buf, size_t len, void* stream);
 
+/* kernel classes of the per-class profile counters */
+enum {
+  STR_K_MTTKRP = 0,   /* slab / sampled MTTKRP with on-the-fly subchain */
+  STR_K_REDUCE = 1,   /* fixed-order split reduction into P_n */
+  STR_K_GRAM = 2,     /* core Gram and ring contraction */
+  STR_K_FACTOR = 3,   /* Cholesky factorisation */
+  STR_K_SOLVE = 4,    /* triangular row solves, leverage scores */
+  STR_K_SKETCH = 5,   /* draws, sign flips, weighted sampled Gram */
+  STR_K_DFT = 6,      /* KSRFT mixing / unmixing */
+  STR_K_OTHER = 7,    /* conversions, reconstruction, checks */
+  STR_K_CLASSES = 8
+};
+
 typedef struct {
   int64_t steps;            /* updates committed */
   int64_t time_rows;        /* temporal rows held */
   int64_t kernel_launches;  /* kernels launched by the last update */
   int64_t device_bytes;     /* device memory owned by the context */
   double min_pivot_ratio;   /* smallest L_kk^2 / Q_kk seen by the last update's solves */
+  int64_t class_launches[STR_K_CLASSES];  /* with opt.profile: launches per class */
+  double class_ms[STR_K_CLASSES];         /* with opt.profile: summed event time per class */
 } str_stats;
+/* Fills *stats.  The profile counters cover the launches since the previous
+ * str_get_stats call (they are reset by it); reading them waits for those
+ * launches to finish. */
 str_status str_get_stats(const str_ctx* ctx, str_stats* stats);
 
 /* Waits for the context's queued work and reports a pending device error. */

@@ -39,7 +39,7 @@ class StrOptions(Structure):
     _fields_ = [("compute", c_int), ("sweeps", c_int), ("rescale", c_int), ("t_capacity", c_int64),
                 ("init_max_it", c_int), ("init_tol", c_double), ("sketch", c_int), ("m", c_int64),
                 ("seed", c_uint64), ("stream_id", c_uint32), ("check_finite", c_int),
-                ("async_status", c_int)]
+                ("async_status", c_int), ("profile", c_int)]
 
 
 class StrTensor(Structure):
@@ -49,7 +49,11 @@ class StrTensor(Structure):
 
 class StrStats(Structure):
     _fields_ = [("steps", c_int64), ("time_rows", c_int64), ("kernel_launches", c_int64),
-                ("device_bytes", c_int64), ("min_pivot_ratio", c_double)]
+                ("device_bytes", c_int64), ("min_pivot_ratio", c_double),
+                ("class_launches", c_int64 * 8), ("class_ms", c_double * 8)]
+
+
+KERNEL_CLASSES = ("mttkrp", "reduce", "gram", "factor", "solve", "sketch", "dft", "other")
 
 
 class _SaveHeader(Structure):
@@ -286,7 +290,10 @@ class Stream:
     def stats(self) -> dict:
         s = StrStats()
         _check(lib().str_get_stats(self.handle, byref(s)), "str_get_stats")
-        return {f: getattr(s, f) for f, _ in StrStats._fields_}
+        out = {f: getattr(s, f) for f, _ in StrStats._fields_[:5]}
+        out["class_launches"] = dict(zip(KERNEL_CLASSES, list(s.class_launches)))
+        out["class_ms"] = dict(zip(KERNEL_CLASSES, list(s.class_ms)))
+        return out
 
     def sync(self):
         _check(lib().str_sync(self.handle), "str_sync")

@@ -71,6 +71,12 @@ struct str_ctx {
   double* h_sums = nullptr;      // pinned (2 doubles)
   std::vector<void*> owned;
   size_t bytes = 0;
+  // profiling: pending (class, start, end) event triples and the event pool
+  struct Ev { int cls; cudaEvent_t a, b; };
+  std::vector<Ev> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t prof_launch[STR_K_CLASSES] = {};
+  double prof_ms[STR_K_CLASSES] = {};
 
   int RR(int n) const { return R[n] * R[n + 1]; }
   int64_t m() const { return opt.m; }
@@ -89,12 +95,29 @@ str_status from_cuda(cudaError_t e, const char* what) {
     str_status _s = (expr);                        \
     if (_s != STR_OK) return _s;                   \
   } while (0)
-#define LCH(ctx, expr)                             \
-  do {                                             \
-    cudaError_t _e = (expr);                       \
-    ++(ctx)->launches;                             \
-    if (_e != cudaSuccess) return from_cuda(_e, #expr); \
+cudaEvent_t ev_get(str_ctx* c) {
+  if (!c->pool.empty()) { cudaEvent_t e = c->pool.back(); c->pool.pop_back(); return e; }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// launch with optional event timing on the launch stream
+#define LCHK(ctx, cls, expr)                                           \
+  do {                                                                 \
+    str_ctx* _c = (ctx);                                               \
+    cudaEvent_t _a = nullptr, _b = nullptr;                            \
+    if (_c->opt.profile) { _a = ev_get(_c); cudaEventRecord(_a, s); }  \
+    cudaError_t _e = (expr);                                           \
+    ++_c->launches;                                                    \
+    if (_c->opt.profile) {                                             \
+      _b = ev_get(_c);                                                 \
+      cudaEventRecord(_b, s);                                          \
+      _c->pending.push_back({(cls), _a, _b});                          \
+    }                                                                  \
+    if (_e != cudaSuccess) return from_cuda(_e, #expr);                \
   } while (0)
+#define LCH(ctx, expr) LCHK(ctx, STR_K_OTHER, expr)
 
 str_status dalloc(str_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
@@ -183,9 +206,9 @@ str_status ring_Q(str_ctx* c, int n, const double* ENew, const double* base, dou
     const int Ncols = c->R[k + 1] * c->R[k + 1];
     const bool last = (t == N - 2);
     if (last) {
-      LCH(c, launch_gemm64(A, B, Qout, Mrows, Kc, Ncols, c->R[n], c->R[n + 1], base, s));
+      LCHK(c, STR_K_GRAM, launch_gemm64(A, B, Qout, Mrows, Kc, Ncols, c->R[n], c->R[n + 1], base, s));
     } else {
-      LCH(c, launch_gemm64(A, B, bufs[bi], Mrows, Kc, Ncols, 0, 0, nullptr, s));
+      LCHK(c, STR_K_GRAM, launch_gemm64(A, B, bufs[bi], Mrows, Kc, Ncols, 0, 0, nullptr, s));
       A = bufs[bi];
       bi ^= 1;
       Kc = Ncols;
@@ -199,8 +222,8 @@ str_status solve_rows(str_ctx* c, const double* Qm, int n, const double* Pm, int
                       double* out64, float* out32, cudaStream_t s) {
   TRY(grow(c, c->lfac, (size_t)n * n * 8));
   TRY(grow(c, c->invd, (size_t)n * 8));
-  LCH(c, launch_chol_factor(Qm, n, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, c->d_pivot, s));
-  LCH(c, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, n, Pm, rows, out64, out32, nullptr, s));
+  LCHK(c, STR_K_FACTOR, launch_chol_factor(Qm, n, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, c->d_pivot, s));
+  LCHK(c, STR_K_SOLVE, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, n, Pm, rows, out64, out32, nullptr, s));
   return STR_OK;
 }
 
@@ -210,15 +233,15 @@ str_status leverage(str_ctx* c, const double* G, int64_t I, int Ra, int Rb, doub
   const int RR = Ra * Rb;
   if (I <= RR) {
     // full row rank: every leverage score is 1, p is uniform
-    LCH(c, launch_fill(p_out, I, 1.0 / (double)I, s));
+    LCHK(c, STR_K_SOLVE, launch_fill(p_out, I, 1.0 / (double)I, s));
     return STR_OK;
   }
   TRY(grow(c, c->gram, (size_t)RR * RR * 8));
   TRY(grow(c, c->lfac, (size_t)RR * RR * 8));
   TRY(grow(c, c->invd, (size_t)RR * 8));
-  LCH(c, launch_core_gram(G, I, Ra, Rb, (double*)c->gram.p, nullptr, s));
-  LCH(c, launch_chol_factor((double*)c->gram.p, RR, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, nullptr, s));
-  LCH(c, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, RR, G, I, nullptr, nullptr, p_out, s));
+  LCHK(c, STR_K_GRAM, launch_core_gram(G, I, Ra, Rb, (double*)c->gram.p, nullptr, s));
+  LCHK(c, STR_K_FACTOR, launch_chol_factor((double*)c->gram.p, RR, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, nullptr, s));
+  LCHK(c, STR_K_SOLVE, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, RR, G, I, nullptr, nullptr, p_out, s));
   return STR_OK;
 }
 
@@ -275,8 +298,8 @@ str_status mttkrp_into(str_ctx* c, const SlabView& v, int n, const void* const* 
   const size_t esize = (c->compute == 2 ? 8 : 4) * (cplx ? 2 : 1);
   TRY(grow(c, c->partial, (size_t)a.splits * v.dim[n] * RR * esize));
   a.partial = c->partial.p;
-  LCH(c, launch_mttkrp(a, s));
-  LCH(c, launch_reduce_partials(a.partial, c->compute, a.cplx, a.splits, v.dim[n] * RR, base, 1.0, out, s));
+  LCHK(c, STR_K_MTTKRP, launch_mttkrp(a, s));
+  LCHK(c, STR_K_REDUCE, launch_reduce_partials(a.partial, c->compute, a.cplx, a.splits, v.dim[n] * RR, base, 1.0, out, s));
   return STR_OK;
 }
 
@@ -316,7 +339,7 @@ size_t celem(const str_ctx* c) { return c->compute == 2 ? 16 : 8; }
 str_status draw_signs(str_ctx* c, const int64_t* dims, uint64_t tau, cudaStream_t s) {
   for (int k = 0; k < c->N; ++k) {
     TRY(grow(c, c->sgn[k], (size_t)dims[k] * 8));
-    LCH(c, launch_signs((double*)c->sgn[k].p, dims[k], c->opt.seed, k + 1, tau, c->opt.stream_id, s));
+    LCHK(c, STR_K_SKETCH, launch_signs((double*)c->sgn[k].p, dims[k], c->opt.seed, k + 1, tau, c->opt.stream_id, s));
   }
   return STR_OK;
 }
@@ -332,7 +355,7 @@ str_status mix_slab(str_ctx* c, const SlabView& v, const void** out, cudaStream_
   void* bufs[2] = {c->xmix0.p, c->xmix1.p};
   int bi = 0;
   for (int k = 0; k < c->N; ++k) {
-    LCH(c, launch_dft_mode(src, st, bufs[bi], c->compute, c->N, v.dim, k, (const double*)c->sgn[k].p, s));
+    LCHK(c, STR_K_DFT, launch_dft_mode(src, st, bufs[bi], c->compute, c->N, v.dim, k, (const double*)c->sgn[k].p, s));
     src = bufs[bi];
     st = cplx_type(c);
     bi ^= 1;
@@ -346,7 +369,7 @@ str_status mix_core(str_ctx* c, int k, const void* G, int64_t rows, cudaStream_t
   const int RR = c->RR(k);
   TRY(grow(c, c->gmix[k], (size_t)rows * RR * celem(c)));
   const int64_t dims[2] = {RR, rows};
-  LCH(c, launch_dft_mode(G, c->compute == 2 ? XT_F64 : XT_F32, c->gmix[k].p, c->compute, 2, dims, 1,
+  LCHK(c, STR_K_DFT, launch_dft_mode(G, c->compute == 2 ? XT_F64 : XT_F32, c->gmix[k].p, c->compute, 2, dims, 1,
                          (const double*)c->sgn[k].p, s));
   return STR_OK;
 }
@@ -426,7 +449,7 @@ str_status upload_cores(str_ctx* c, const double* const* cores, cudaStream_t s) 
       float* d32 = (k == N - 1) ? c->GT32 : c->G32[k][c->cur[k]];
       LCH(c, launch_convert(dst, XT_F64, d32, XT_F32, rows * RR, s));
     }
-    if (k < N - 1) LCH(c, launch_core_gram(dst, rows, c->R[k], c->R[k + 1], nullptr, c->E[k][c->cur[k]], s));
+    if (k < N - 1) LCHK(c, STR_K_GRAM, launch_core_gram(dst, rows, c->R[k], c->R[k + 1], nullptr, c->E[k][c->cur[k]], s));
   }
   return STR_OK;
 }
@@ -460,7 +483,7 @@ str_status rstr_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
       const double* G = (k == N - 1) ? c->GT64 : c->G64[k][c->cur[k]];
       TRY(leverage(c, G, Ik, c->R[k], c->R[k + 1], c->p[k][c->cur[k]], s));
     }
-    LCH(c, launch_draw_indices(c->idxs[k][c->cur[k]], m, Ik, c->opt.seed, k + 1, 0, c->opt.stream_id,
+    LCHK(c, STR_K_SKETCH, launch_draw_indices(c->idxs[k][c->cur[k]], m, Ik, c->opt.seed, k + 1, 0, c->opt.stream_id,
                                levdraw ? c->p[k][c->cur[k]] : nullptr, s));
   }
   const void* cores[STR_MAXN];
@@ -503,11 +526,11 @@ str_status rstr_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
     const double ws = sketch_wscale(c, n, v.dim);
     if (ks) {
       TRY(mttkrp_into(c, sv, n, cores, true, idx0, false, pk, ws, true, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
-      LCH(c, launch_unmix_rows((double*)c->mtmp.p, v.dim[n], RR, (const double*)c->sgn[n].p, nullptr, Pn, s));
+      LCHK(c, STR_K_DFT, launch_unmix_rows((double*)c->mtmp.p, v.dim[n], RR, (const double*)c->sgn[n].p, nullptr, Pn, s));
     } else {
       TRY(mttkrp_into(c, sv, n, cores, true, idx0, lev, pk, ws, false, nullptr, Pn, c->gs.p, (double*)c->ws.p, s));
     }
-    LCH(c, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, nullptr, Qn, s));
+    LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, nullptr, Qn, s));
   }
   return STR_OK;
 }
@@ -517,7 +540,7 @@ str_status str_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
   const int N = c->N;
   const int RRN = c->RR(N - 1);
   TRY(grow(c, c->enew, (size_t)RRN * RRN * 8));
-  LCH(c, launch_core_gram(c->GT64, c->t_rows, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s));
+  LCHK(c, STR_K_GRAM, launch_core_gram(c->GT64, c->t_rows, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s));
   const void* cores[STR_MAXN];
   for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
   cores[N - 1] = temporal_rows_c(c, 0);
@@ -581,7 +604,7 @@ str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
     TRY(mttkrp_into(c, v, N - 1, cores, false, nullptr, false, nullptr, 1.0, false, nullptr, (double*)c->mtmp.p, nullptr, nullptr, s));
     TRY(solve_rows(c, (double*)c->qtmp.p, RRN, (double*)c->mtmp.p, tn, gn64,
                    c->compute == 1 ? (float*)c->gnew32.p : nullptr, s));
-    LCH(c, launch_core_gram(gn64, tn, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s));
+    LCHK(c, STR_K_GRAM, launch_core_gram(gn64, tn, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s));
     // spatial modes in order (Gauss-Seidel)
     for (int n = 0; n < N - 1; ++n) {
       const int RR = c->RR(n);
@@ -592,7 +615,7 @@ str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
       TRY(ring_Q(c, n, (double*)c->enew.p, c->Q[n][c->cur[n]], c->Q[n][w], s));
       TRY(solve_rows(c, c->Q[n][w], RR, c->P[n][w], c->I[n], c->G64[n][w],
                      c->compute == 1 ? c->G32[n][w] : nullptr, s));
-      LCH(c, launch_core_gram(c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][w], s));
+      LCHK(c, STR_K_GRAM, launch_core_gram(c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][w], s));
       c->upd[n] = 1;
     }
   }
@@ -657,11 +680,11 @@ str_status rstr_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
   if (ks) {
     TRY(mttkrp_into(c, sv, N - 1, cores, true, idxcat, false, pk, wsN, true, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
     TRY(grow(c, c->gram, (size_t)tn * RRN * 8 + 64));
-    LCH(c, launch_unmix_rows((double*)c->mtmp.p, tn, RRN, (const double*)c->sgn[N - 1].p, nullptr, (double*)c->gram.p, s));
+    LCHK(c, STR_K_DFT, launch_unmix_rows((double*)c->mtmp.p, tn, RRN, (const double*)c->sgn[N - 1].p, nullptr, (double*)c->gram.p, s));
   } else {
     TRY(mttkrp_into(c, sv, N - 1, cores, true, idxcat, lev, pk, wsN, false, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
   }
-  LCH(c, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RRN, nullptr, (double*)c->qtmp.p, s));
+  LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RRN, nullptr, (double*)c->qtmp.p, s));
   TRY(solve_rows(c, (double*)c->qtmp.p, RRN, ks ? (double*)c->gram.p : (double*)c->mtmp.p, tn, gn64,
                  c->compute == 1 ? (float*)c->gnew32.p : nullptr, s));
   {
@@ -671,7 +694,7 @@ str_status rstr_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
       TRY(ensure_p(c, k, tn));
       TRY(leverage(c, gn64, tn, c->R[k], c->R[k + 1], c->p[k][w], s));
     }
-    LCH(c, launch_draw_indices(c->idxs[k][w], m, tn, c->opt.seed, k + 1, tau, c->opt.stream_id,
+    LCHK(c, STR_K_SKETCH, launch_draw_indices(c->idxs[k][w], m, tn, c->opt.seed, k + 1, tau, c->opt.stream_id,
                                levdraw ? c->p[k][w] : nullptr, s));
     c->upd[k] = 1;
     if (ks) TRY(mix_core(c, k, gn_c, tn, s));
@@ -687,22 +710,22 @@ str_status rstr_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
     const double wsn = sketch_wscale(c, n, v.dim);
     if (ks) {
       TRY(mttkrp_into(c, sv, n, cores, true, idxcat, false, pk, wsn, true, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
-      LCH(c, launch_unmix_rows((double*)c->mtmp.p, c->I[n], RR, (const double*)c->sgn[n].p, c->P[n][c->cur[n]], c->P[n][w], s));
+      LCHK(c, STR_K_DFT, launch_unmix_rows((double*)c->mtmp.p, c->I[n], RR, (const double*)c->sgn[n].p, c->P[n][c->cur[n]], c->P[n][w], s));
     } else {
       TRY(mttkrp_into(c, sv, n, cores, true, idxcat, lev, pk, wsn, false, c->P[n][c->cur[n]], c->P[n][w], c->gs.p, (double*)c->ws.p, s));
     }
-    LCH(c, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, c->Q[n][c->cur[n]], c->Q[n][w], s));
+    LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, c->Q[n][c->cur[n]], c->Q[n][w], s));
     TRY(solve_rows(c, c->Q[n][w], RR, c->P[n][w], c->I[n], c->G64[n][w], c->compute == 1 ? c->G32[n][w] : nullptr, s));
     c->upd[n] = 1;
     if (levdraw) {
       TRY(ensure_p(c, n, c->I[n]));
       TRY(leverage(c, c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], c->p[n][w], s));
     }
-    LCH(c, launch_draw_indices(c->idxs[n][w], m, c->I[n], c->opt.seed, n + 1, tau, c->opt.stream_id,
+    LCHK(c, STR_K_SKETCH, launch_draw_indices(c->idxs[n][w], m, c->I[n], c->opt.seed, n + 1, tau, c->opt.stream_id,
                                levdraw ? c->p[n][w] : nullptr, s));
     if (ks) TRY(mix_core(c, n, core_c(c, n), c->I[n], s));
     // E_n is kept current for a later exact update on the same context
-    LCH(c, launch_core_gram(c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][w], s));
+    LCHK(c, STR_K_GRAM, launch_core_gram(c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][w], s));
   }
   STR_CUDA_TRY(cudaMemcpyAsync(c->GT64 + c->t_rows * RRN, gn64, (size_t)tn * RRN * 8, cudaMemcpyDeviceToDevice, s));
   if (c->compute == 1)
@@ -1164,6 +1187,23 @@ str_status str_get_stats(const str_ctx* c, str_stats* stats) {
   double piv = 0.0;
   if (cudaMemcpy(&piv, c->d_pivot, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return STR_ERR_CUDA;
   stats->min_pivot_ratio = piv;
+  str_ctx* m = const_cast<str_ctx*>(c);
+  for (auto& e : m->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(e.b) != cudaSuccess || cudaEventElapsedTime(&ms, e.a, e.b) != cudaSuccess)
+      return STR_ERR_CUDA;
+    m->prof_ms[e.cls] += ms;
+    m->prof_launch[e.cls] += 1;
+    m->pool.push_back(e.a);
+    m->pool.push_back(e.b);
+  }
+  m->pending.clear();
+  for (int k = 0; k < STR_K_CLASSES; ++k) {
+    stats->class_launches[k] = m->prof_launch[k];
+    stats->class_ms[k] = m->prof_ms[k];
+    m->prof_launch[k] = 0;
+    m->prof_ms[k] = 0.0;
+  }
   return STR_OK;
 }
 
@@ -1205,6 +1245,8 @@ void str_destroy(str_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   for (void* p : c->owned) cudaFree(p);
+  for (auto& e : c->pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto e : c->pool) cudaEventDestroy(e);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_sums) cudaFreeHost(c->h_sums);
   delete c;
