@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Throughput of the streaming tensor-ring update on GB300.
+
+Workload (one "step" = one STR update, every row of the hot path):
+  order-4 tensor 64x64x64xT, T = 400, TR-ranks all 8, Gaussian cores, noise at
+  SNR 30 dB, initial decomposition on 40 slices, then updates of 10 slices,
+  5 sweeps per update, FP32 slab and FP32 slab-side arithmetic (FP64 Gram,
+  P_n/Q_n and solves).  Inputs are synthetic and already resident in HBM.
+
+Printed as one JSON line by rank 0.  `--impl reference` times the FP64 CPU
+oracle on the same workload (a bounded sample per step) instead.
+Secondary rows (same line): the plain FP64 GPU arm of the same workload, and
+rSTR-U/L/K updates on a 512x512xT BF16 workload (ranks 10, sketch size 2000).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "STR/rSTR tensor entries/s per update, % roofline, rel. fit err vs FP64"
+W2 = synth.WORKLOADS["order4"]
+W3 = synth.WORKLOADS["rand3"]
+WORKLOAD_DESC = ("order4: 64x64x64xT, T=400, TR-ranks all 8, Gaussian cores, SNR 30 dB, "
+                 "init on 40 slices, updates of 10 slices, 5 sweeps, FP32 slab")
+FLUSH_BYTES = 256 << 20     # > 129 MB L2
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-rstr", action="store_true", help="skip the rSTR rows")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU arm")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# workload construction (GPU)
+# ---------------------------------------------------------------------------
+def build_tensor(p, torch, w, seed):
+    """X = TR(G_true) + noise, built on the GPU with the library's reconstruct."""
+    G = synth.gaussian_cores(tuple(w.dims) + (w.T,), w.ranks, seed)
+    truth = p.str_init_cores(G, X0=None, t_capacity=w.T)
+    X = truth.reconstruct(0, w.T)                          # FP64, i_1 fastest
+    truth.close()
+    if w.noise > 0:
+        g = torch.Generator(device="cuda").manual_seed(seed + 100)
+        E = torch.randn(X.shape[::-1], generator=g, device="cuda", dtype=torch.float64)
+        E = E.permute(list(range(E.dim() - 1, -1, -1)))
+        X = X + (w.noise * torch.linalg.vector_norm(X) / torch.linalg.vector_norm(E)) * E
+    return G, p.paper_layout(X)
+
+
+def init_cores(p, torch, w, G, X, seed, iters=20):
+    """Initial decomposition of the first t_init slices by TR-ALS-NE on the GPU,
+    started from the true cores perturbed by 0.3 N(0,1)."""
+    rng = np.random.default_rng(seed + 200)
+    guess = [g + 0.3 * rng.standard_normal(g.shape) for g in G]
+    guess[-1] = guess[-1][:, :w.t_init, :]
+    ctx = p.str_init(p.paper_layout(X[..., :w.t_init]), w.ranks, guess, init_max_it=iters)
+    cores = ctx.cores()
+    ctx.close()
+    return cores
+
+
+def slab(X, w, j, dtype=None):
+    nsl = (w.T - w.t_init) // w.t_new
+    t0 = w.t_init + (j % nsl) * w.t_new
+    s = X[..., t0:t0 + w.t_new]
+    return s if dtype is None else s.to(dtype)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# timed loops
+# ---------------------------------------------------------------------------
+def timed_updates(p, torch, ctx, slabs, steps, warmup, randomized=False, flush=None, profile=False):
+    """Warm-up, then `steps` updates, each bracketed by CUDA events on the
+    launching stream with an L2 flush before it (outside the events)."""
+    stream = torch.cuda.current_stream()
+    upd = ctx.rupdate if randomized else ctx.update
+    for j in range(warmup):
+        upd(slabs(j))
+    torch.cuda.synchronize()
+    ctx.stats()                                   # reset profile counters
+    times = []
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for j in range(steps):
+        if flush is not None:
+            flush.zero_()
+        a, b = evs[j]
+        a.record(stream)
+        upd(slabs(warmup + j))
+        b.record(stream)
+    torch.cuda.synchronize()
+    for a, b in evs:
+        times.append(a.elapsed_time(b))
+    st = ctx.stats()
+    # every update of a workload launches the same kernels; kernel_launches is the last one's count
+    launches = sum(st["class_launches"].values()) if profile else steps * st["kernel_launches"]
+    return times, launches, st
+
+
+def main_ours(a):
+    import torch
+    import paper_2307_00719_gb300 as p
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    seed = W2.seed + 1000 * rank                       # independent replica per rank
+    G, X = build_tensor(p, torch, W2, seed)
+    cores0 = init_cores(p, torch, W2, G, X, seed)
+    X32 = p.paper_layout(X.float())
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    E = int(np.prod(W2.dims)) * W2.t_new
+    cap = W2.t_init + (a.warmup + a.steps + 2) * W2.t_new
+
+    def make(compute, xsrc, profile=0):
+        return p.str_init_cores(cores0, X0=p.paper_layout(xsrc[..., :W2.t_init]), compute=compute,
+                                sweeps=W2.sweeps, t_capacity=cap, async_status=1, profile=profile)
+
+    # ---- main arm: FP32, device-resident slabs, L2 flushed between steps ----
+    ctx = make("f32", X32)
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, launches, _ = timed_updates(p, torch, ctx, lambda j: slab(X32, W2, j), a.steps, a.warmup,
+                                       flush=flush)
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * a.steps * E / (total_ms / 1e3)
+    fit32 = ctx.fit_error(X32[..., :ctx.time_rows()])
+    cores32 = ctx.cores()
+    ctx.close()
+
+    # ---- profile pass: per-class kernel times (same steps, events per launch) ----
+    ctxp = make("f32", X32, profile=1)
+    ptimes, _, pst = timed_updates(p, torch, ctxp, lambda j: slab(X32, W2, j), a.steps, a.warmup,
+                                   flush=flush, profile=True)
+    ctxp.close()
+    k_ms, k_n = pst["class_ms"], pst["class_launches"]
+    mt_avg_ms = k_ms["mttkrp"] / max(1, k_n["mttkrp"])
+    RR = W2.ranks[0] * W2.ranks[1]
+    flop_per_launch = 2.0 * E * RR                     # 2 E R_n R_{n+1} per MTTKRP launch
+    achieved = flop_per_launch / (mt_avg_ms / 1e3) / 1e12
+    sm_clock = (clk.get("sm_mhz") or 1900.0)
+    peak = 152 * 128 * 2 * 2070e6 / 1e12               # FP32 FMA lanes x 2 flop x max SM clock
+    tot = sum(k_ms.values())
+    roofline = {"kernel": "mttkrp_kernel (FP32 SIMT, on-the-fly subchain)", "bound": "alu",
+                "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "algorithmic_per_launch": {"flop": flop_per_launch, "bytes": E * 4},
+                "avg_launch_ms": round(mt_avg_ms, 5),
+                "hbm_equiv": {"achieved_gbs": round(E * 4 / (mt_avg_ms / 1e3) / 1e9, 1),
+                              "peak_gbs": measured_peak("hbm_gbs", 6685.5)},
+                "peak_note": "FP32 SIMT peak from 152 SMs x 128 FMA/clk x 2 x 2070 MHz; "
+                             f"median SM clock under load {sm_clock} MHz"}
+    kernel_share = {k: round(v / tot, 4) for k, v in k_ms.items() if tot > 0 and v > 0}
+
+    out = {"metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD_DESC, "entries_per_update": E,
+                      "l2": "flushed between steps (256 MB write outside the timed events)",
+                      "parallelism": f"replicas x{world} (independent streams, no collective)"},
+           "roofline": roofline, "kernel_time_share": kernel_share,
+           "gpu_launches": int(launches), "clocks": clk}
+
+    # ---- e2e: public API with pinned host slabs, status + core read back per step ----
+    ctx_e = p.str_init_cores(cores0, X0=p.paper_layout(X32[..., :W2.t_init]), compute="f32",
+                             sweeps=W2.sweeps, t_capacity=cap)
+    nsl = min(a.steps + a.warmup, (W2.T - W2.t_init) // W2.t_new)
+    host = []
+    for j in range(nsl):
+        d = slab(X32, W2, j)
+        rev = list(range(d.dim() - 1, -1, -1))
+        h = torch.empty(list(d.shape)[::-1], dtype=d.dtype, pin_memory=True)
+        h.copy_(d.permute(rev))
+        host.append(h.permute(rev))
+    for j in range(a.warmup):
+        ctx_e.update(host[j % nsl])
+        ctx_e.core(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(a.steps):
+        ctx_e.update(host[(a.warmup + j) % nsl])
+        ctx_e.core(1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    ctx_e.close()
+    out["e2e"] = {"value": world * a.steps * E / e2e_s, "unit": "entries/s",
+                  "h2d_bytes_per_step": E * 4, "d2h_bytes_per_step": 4 + 64 * 64 * 8,
+                  "note": "str_update with on_host=1 pinned slab (copy inside the call, status read) "
+                          "+ str_get_core(1), wall clock"}
+
+    # ---- plain FP64 GPU arm (same steps): throughput and fit error reference ----
+    if not a.no_fp64:
+        X64 = X
+        ctx64 = make("f64", X64)
+        t64, _, _ = timed_updates(p, torch, ctx64, lambda j: slab(X64, W2, j), min(a.steps, 4), a.warmup,
+                                  flush=flush)
+        steps64 = min(a.steps, 4)
+        fit64 = ctx64.fit_error(X64[..., :ctx64.time_rows()])
+        out["fp64_arm"] = {"value": steps64 * E / (sum(t64) / 1e3), "unit": "entries/s",
+                           "ms_per_step": sum(t64) / steps64, "steps": steps64}
+        # the FP32 arm over the same first warmup+steps64 updates vs FP64
+        ctxc = make("f32", X32)
+        for j in range(a.warmup + steps64):
+            ctxc.update(slab(X32, W2, j))
+        fitc = ctxc.fit_error(X32[..., :ctxc.time_rows()])
+        core_rel = max(float(np.linalg.norm(c - d) / np.linalg.norm(d))
+                       for c, d in zip(ctxc.cores(), ctx64.cores()))
+        ctxc.close()
+        ctx64.close()
+        out["fit_error"] = {"f32_arm": fitc, "f64_arm": fit64, "rel_diff": abs(fitc - fit64) / fit64,
+                            "max_core_rel_diff": core_rel, "f32_arm_after_all_steps": fit32,
+                            "updates_compared": a.warmup + steps64}
+    # ---- rSTR rows ----
+    if not a.no_rstr:
+        out["rstr"] = rstr_rows(p, torch, flush, rank)
+    # ---- CPU oracle baseline (rank 0, N = 1) ----
+    if rank == 0 and world == 1 and not a.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(X, cores0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except Exception:
+        return fallback
+
+
+def rstr_rows(p, torch, flush, rank, steps=4, warmup=2):
+    """rSTR-U/L/K updates on the 512x512xT BF16 workload (sketch 2000, Philox seed 7)."""
+    seed = W3.seed + 1000 * rank
+    G, X = build_tensor(p, torch, W3, seed)
+    Xb = p.paper_layout(X.to(torch.bfloat16))
+    del X
+    rng = np.random.default_rng(seed + 300)
+    init = [g + 0.05 * rng.standard_normal(g.shape) for g in G]
+    init[-1] = init[-1][:, :W3.t_init, :]
+    E = int(np.prod(W3.dims)) * W3.t_new
+    rows = {}
+    for sk in ("uniform", "leverage", "ksrft"):
+        ctx = p.str_init_cores(init, X0=p.paper_layout(Xb[..., :W3.t_init]), compute="f32", sketch=sk,
+                               m=W3.sketch_m, seed=W3.philox_seed, async_status=1,
+                               t_capacity=W3.t_init + (steps + warmup + 2) * W3.t_new)
+        times, launches, _ = timed_updates(p, torch, ctx, lambda j: slab(Xb, W3, j), steps, warmup,
+                                           randomized=True, flush=flush)
+        ctxp = p.str_init_cores(init, X0=p.paper_layout(Xb[..., :W3.t_init]), compute="f32", sketch=sk,
+                                m=W3.sketch_m, seed=W3.philox_seed, async_status=1, profile=1,
+                                t_capacity=W3.t_init + (steps + warmup + 2) * W3.t_new)
+        _, _, pst = timed_updates(p, torch, ctxp, lambda j: slab(Xb, W3, j), steps, warmup,
+                                  randomized=True, flush=flush, profile=True)
+        tot = sum(pst["class_ms"].values())
+        rows[sk] = {"value": steps * E / (sum(times) / 1e3), "unit": "entries/s",
+                    "ms_per_step": sum(times) / steps, "gpu_launches_per_step": launches / steps,
+                    "kernel_time_share": {k: round(v / tot, 4) for k, v in pst["class_ms"].items() if v > 0}}
+        ctx.close()
+        ctxp.close()
+    rows["workload"] = ("rand3: 512x512xT, T=200, TR-ranks all 10, BF16 slab, FP32 slab-side arithmetic, "
+                        "sketch size 2000, Philox seed 7, updates of 5 slices")
+    return rows
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------
+def oracle_sample(Xh, cores0, nupd=1):
+    """The FP64 oracle's STR update (Alg. 4, 5 sweeps) on the order4 workload:
+    initialisation stage on 40 slices (untimed), then `nupd` timed updates."""
+    from oracle import stream as ost
+    st = ost.str_init(Xh[..., :W2.t_init], cores0)
+    t = W2.t_init
+    t0 = time.perf_counter()
+    for _ in range(nupd):
+        ost.str_update(st, Xh[..., t:t + W2.t_new], sweeps=W2.sweeps)
+        t += W2.t_new
+    return time.perf_counter() - t0
+
+
+def cpu_threads():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
+def cpu_baseline(X, cores0, nupd=2):
+    Xh = X[..., :W2.t_init + nupd * W2.t_new].double().cpu().numpy()
+    secs = oracle_sample(Xh, cores0, nupd)
+    E = int(np.prod(W2.dims)) * W2.t_new
+    return {"value": nupd * E / secs, "unit": "entries/s", "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"{nupd} STR updates of 10 slices (5 sweeps) of the order4 workload, FP64 numpy oracle",
+            "seconds": secs}
+
+
+def main_reference(a):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    # inputs: same recipe on the host (oracle builds TR(G) itself)
+    from oracle import stream as ost
+    from oracle import tr as otr
+    nsl = a.warmup + a.steps
+    G = synth.gaussian_cores(tuple(W2.dims) + (W2.T,), W2.ranks, W2.seed)
+    tmax = W2.t_init + nsl * W2.t_new
+    Gt = G[:-1] + [G[-1][:, :tmax, :]]
+    Xt = otr.tr_full(Gt)
+    full = synth.gaussian_tensor(tuple(W2.dims) + (W2.T,), W2.seed + 100)[..., :tmax]
+    X = Xt + W2.noise * np.linalg.norm(Xt) * full / np.linalg.norm(full)
+    rng = np.random.default_rng(W2.seed + 200)
+    init = [g + 0.3 * rng.standard_normal(g.shape) for g in G]
+    init[-1] = init[-1][:, :W2.t_init, :]
+    st = ost.str_init(X[..., :W2.t_init], init)
+    t = W2.t_init
+    for _ in range(a.warmup):
+        ost.str_update(st, X[..., t:t + W2.t_new], sweeps=W2.sweeps)
+        t += W2.t_new
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        ost.str_update(st, X[..., t:t + W2.t_new], sweeps=W2.sweeps)
+        times.append(time.perf_counter() - t0)
+        t += W2.t_new
+    E = int(np.prod(W2.dims)) * W2.t_new
+    value = a.steps * E / sum(times)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / a.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "entries_per_update": E},
+           "cpu_baseline": {"value": value, "unit": "entries/s", "kind": "oracle", "cores": cpu_threads(),
+                            "sample": "each step = one STR update of 10 slices (5 sweeps) by the FP64 oracle"},
+           "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    args = args_parse()
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)

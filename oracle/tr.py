@@ -29,14 +29,21 @@ def tr_entry(cores: Sequence[np.ndarray], idx: Sequence[int]) -> float:
 def tr_full(cores: Sequence[np.ndarray]) -> np.ndarray:
     """The full tensor TR({G_n}) as an array indexed X[i_1, ..., i_N].
 
-    Same trace formula as tr_entry, evaluated for all indices at once by
-    multiplying the slices left to right (one library contraction per core).
+    Same trace formula as tr_entry, evaluated for all indices at once: the
+    slices of G_1..G_{N-1} are multiplied left to right (one library
+    contraction per core), then the last core's slice is multiplied in and the
+    trace taken in one contraction (R_{N+1} = R_1).
     """
     T = cores[0]                                   # (R_1, I_1, R_2)
-    for G in cores[1:]:
+    for G in cores[1:-1]:
         T = np.tensordot(T, G, axes=([T.ndim - 1], [0]))   # (R_1, I_1, .., I_k, R_{k+1})
-    # trace over the first and last rank index (R_{N+1} = R_1)
-    return np.trace(T, axis1=0, axis2=T.ndim - 1)
+    GN = cores[-1]                                 # (R_N, I_N, R_1)
+    R1 = T.shape[0]
+    RN = T.shape[-1]
+    lead = T.shape[1:-1]
+    A = np.moveaxis(T, 0, -1).reshape(int(np.prod(lead)), RN * R1)   # (i_1..i_{N-1}), (r_N, r_1)
+    B = GN.transpose(0, 2, 1).reshape(RN * R1, GN.shape[1])          # (r_N, r_1), i_N
+    return (A @ B).reshape(tuple(lead) + (GN.shape[1],))
 
 
 # ----------------------------------------------------------------------------
