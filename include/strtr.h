@@ -243,6 +243,26 @@ str_status tr_masked_loss_bwd(int N, const int64_t* dims, const int* ranks, str_
                               const uint32_t* mask_bits, double grad_scale,
                               void* const* grad_cores_dev, void* stream);
 
+/*
+ * tr_masked_loss_fwd_noalloc -- the paper has no counterpart; this is a service
+ * entry point of the library.  Same arguments and result as
+ * tr_masked_loss_fwd, but it allocates no device memory, for callers that
+ * cannot call cudaMalloc: code running while a CUDA graph is captured, code
+ * whose framework allocator owns all device memory, and latency-critical
+ * loops that cannot take cudaMalloc's device synchronisation.
+ * Its scratch is one fixed 32 MiB array in device global memory (held by every
+ * GPU that loads the library until the process exits).  A problem whose
+ * scratch does not fit returns STR_ERR_SHAPE before launching anything
+ * (str_last_error() gives the size).  All calls share that array: calls that
+ * overlap on the GPU (other streams or host threads) race.  The first call on
+ * each device looks up the array's address with that device current; make it
+ * before any stream capture.
+ */
+str_status tr_masked_loss_fwd_noalloc(int N, const int64_t* dims, const int* ranks,
+                                      str_dtype dtype, const void* const* cores_dev,
+                                      const void* X_dev, const uint32_t* mask_bits,
+                                      double* loss_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,8 @@ _SIGS = [
                                    c_void_p, c_void_p, c_void_p, c_void_p]),
     ("tr_masked_loss_bwd", c_int, [c_int, POINTER(c_int64), POINTER(c_int), c_int, POINTER(c_void_p),
                                    c_void_p, c_void_p, c_double, POINTER(c_void_p), c_void_p]),
+    ("tr_masked_loss_fwd_noalloc", c_int, [c_int, POINTER(c_int64), POINTER(c_int), c_int,
+                                           POINTER(c_void_p), c_void_p, c_void_p, c_void_p, c_void_p]),
 ]
 
 

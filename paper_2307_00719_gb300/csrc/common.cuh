@@ -79,5 +79,6 @@ __device__ __forceinline__ uint64_t draw_u64(uint64_t seed, uint64_t s, uint64_t
   } while (0)
 
 void str_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void str_set_last_error_text(const char* text);
 
 static inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

@@ -25,6 +25,8 @@ void str_set_last_cuda_error(cudaError_t e, const char* what, const char* file, 
                  std::to_string(line) + ")";
 }
 
+void str_set_last_error_text(const char* text) { g_last_error = text; }
+
 namespace {
 
 constexpr uint64_t kSaveMagic = 0x31565254534C4953ull;  // save-format tag
