@@ -142,8 +142,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def timed_updates(p, torch, ctx, slabs, steps, warmup, randomized=False, flush=None, profile=False):
     """Warm-up, then `steps` updates, each bracketed by CUDA events on the
-    launching stream with an L2 flush before it (outside the events)."""
-    stream = torch.cuda.current_stream()
+    launching stream with an L2 flush before it (outside the events).  Runs on
+    a dedicated (non-default) stream so STR updates replay captured graphs."""
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        return _timed_updates(p, torch, ctx, slabs, steps, warmup, randomized, flush, profile, stream)
+
+
+def _timed_updates(p, torch, ctx, slabs, steps, warmup, randomized, flush, profile, stream):
     upd = ctx.rupdate if randomized else ctx.update
     for j in range(warmup):
         upd(slabs(j))
@@ -214,21 +221,25 @@ def main_ours(a):
     ctxp.close()
     k_ms, k_n = pst["class_ms"], pst["class_launches"]
     mt_avg_ms = k_ms["mttkrp"] / max(1, k_n["mttkrp"])
-    RR = W2.ranks[0] * W2.ranks[1]
-    flop_per_launch = 2.0 * E * RR                     # 2 E R_n R_{n+1} per MTTKRP launch
-    achieved = flop_per_launch / (mt_avg_ms / 1e3) / 1e12
+    peak_hbm = measured_peak("hbm_gbs", 6685.5)
+    slab_bytes = E * 4                                  # one read of the FP32 slab per launch
+    achieved = slab_bytes / (mt_avg_ms / 1e3) / 1e9
     sm_clock = (clk.get("sm_mhz") or 1900.0)
-    peak = 152 * 128 * 2 * 2070e6 / 1e12               # FP32 FMA lanes x 2 flop x max SM clock
     tot = sum(k_ms.values())
-    roofline = {"kernel": "mttkrp_kernel (FP32 SIMT, on-the-fly subchain)", "bound": "alu",
-                "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "algorithmic_per_launch": {"flop": flop_per_launch, "bytes": E * 4},
-                "avg_launch_ms": round(mt_avg_ms, 5),
-                "hbm_equiv": {"achieved_gbs": round(E * 4 / (mt_avg_ms / 1e3) / 1e9, 1),
-                              "peak_gbs": measured_peak("hbm_gbs", 6685.5)},
-                "peak_note": "FP32 SIMT peak from 152 SMs x 128 FMA/clk x 2 x 2070 MHz; "
-                             f"median SM clock under load {sm_clock} MHz"}
+    c_avg_ms = k_ms["contract"] / max(1, k_n["contract"])
+    RRk = W2.ranks[0] * W2.ranks[1]
+    roofline = {"kernel": "stage1_tc_persist_kernel (tcgen05 kind::tf32, 3-term split, TMA-fed)",
+                "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_hbm, "unit": "GB/s",
+                "frac": round(achieved / peak_hbm, 4), "traffic": None,
+                "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured",
+                "algorithmic_per_launch": {"bytes": slab_bytes, "flop": 2.0 * E * RRk,
+                                           "note": "one read of the 64^3 x 10 FP32 slab; 2 E R_1 R_2 flop"},
+                "avg_launch_ms": round(mt_avg_ms, 5), "launches": int(k_n["mttkrp"]),
+                "tensor_tflops": round(2.0 * E * RRk / (mt_avg_ms / 1e3) / 1e12, 2),
+                "stage2": {"kernel": "stage2_kernel (SIMT contraction with chain tables)",
+                           "avg_launch_ms": round(c_avg_ms, 5), "launches": int(k_n["contract"]),
+                           "read_gbs": round(E // W2.dims[0] * RRk * 4 / max(c_avg_ms, 1e-9) / 1e6, 1)},
+                "sm_mhz_median": sm_clock}
     kernel_share = {k: round(v / tot, 4) for k, v in k_ms.items() if tot > 0 and v > 0}
 
     out = {"metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": a.steps,
@@ -251,15 +262,17 @@ def main_ours(a):
         h = torch.empty(list(d.shape)[::-1], dtype=d.dtype, pin_memory=True)
         h.copy_(d.permute(rev))
         host.append(h.permute(rev))
-    for j in range(a.warmup):
-        ctx_e.update(host[j % nsl])
-        ctx_e.core(1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for j in range(a.steps):
-        ctx_e.update(host[(a.warmup + j) % nsl])
-        ctx_e.core(1)
-    torch.cuda.synchronize()
+    st_e = torch.cuda.Stream()
+    with torch.cuda.stream(st_e):
+        for j in range(a.warmup):
+            ctx_e.update(host[j % nsl])
+            ctx_e.core(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(a.steps):
+            ctx_e.update(host[(a.warmup + j) % nsl])
+            ctx_e.core(1)
+        torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     ctx_e.close()
     out["e2e"] = {"value": world * a.steps * E / e2e_s, "unit": "entries/s",

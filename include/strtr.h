@@ -92,6 +92,13 @@ typedef struct {
                             *     call or str_sync() and then make the context sticky-failed */
   int profile;             /* 1 = time every kernel launch with CUDA events on the launch
                             *     stream (per-class totals in str_stats) */
+  int mttkrp_path;         /* dense FP32-compute MTTKRP: 0 = tensor cores (tcgen05) where the
+                            *     slab layout allows it, else SIMT; 1 = SIMT only */
+  int graphs;              /* 1 (default) = str_update replays a captured CUDA graph of its
+                            *     kernels once a slab shape has been seen; the slab is then
+                            *     first copied to a library-owned buffer.  Not used while
+                            *     profiling or on the legacy default stream (NULL).
+                            *     0 = plain stream launches */
 } str_options;
 
 /* Fills *opt with the defaults listed above (compute F64, sweeps 1, rescale 1,
@@ -190,7 +197,7 @@ str_status str_load(str_ctx** out, const void* buf, size_t len, void* stream);
 
 /* kernel classes of the per-class profile counters */
 enum {
-  STR_K_MTTKRP = 0,   /* slab / sampled MTTKRP with on-the-fly subchain */
+  STR_K_MTTKRP = 0,   /* slab MTTKRP: tensor-core stage 1, or the SIMT kernel (sampled, FP64) */
   STR_K_REDUCE = 1,   /* fixed-order split reduction into P_n */
   STR_K_GRAM = 2,     /* core Gram and ring contraction */
   STR_K_FACTOR = 3,   /* Cholesky factorisation */
@@ -198,7 +205,8 @@ enum {
   STR_K_SKETCH = 5,   /* draws, sign flips, weighted sampled Gram */
   STR_K_DFT = 6,      /* KSRFT mixing / unmixing */
   STR_K_OTHER = 7,    /* conversions, reconstruction, checks */
-  STR_K_CLASSES = 8
+  STR_K_CONTRACT = 8, /* tensor-core MTTKRP stage 2: contraction with the chain tables */
+  STR_K_CLASSES = 9
 };
 
 typedef struct {

@@ -39,7 +39,8 @@ class StrOptions(Structure):
     _fields_ = [("compute", c_int), ("sweeps", c_int), ("rescale", c_int), ("t_capacity", c_int64),
                 ("init_max_it", c_int), ("init_tol", c_double), ("sketch", c_int), ("m", c_int64),
                 ("seed", c_uint64), ("stream_id", c_uint32), ("check_finite", c_int),
-                ("async_status", c_int), ("profile", c_int)]
+                ("async_status", c_int), ("profile", c_int), ("mttkrp_path", c_int),
+                ("graphs", c_int)]
 
 
 class StrTensor(Structure):
@@ -50,10 +51,10 @@ class StrTensor(Structure):
 class StrStats(Structure):
     _fields_ = [("steps", c_int64), ("time_rows", c_int64), ("kernel_launches", c_int64),
                 ("device_bytes", c_int64), ("min_pivot_ratio", c_double),
-                ("class_launches", c_int64 * 8), ("class_ms", c_double * 8)]
+                ("class_launches", c_int64 * 9), ("class_ms", c_double * 9)]
 
 
-KERNEL_CLASSES = ("mttkrp", "reduce", "gram", "factor", "solve", "sketch", "dft", "other")
+KERNEL_CLASSES = ("mttkrp", "reduce", "gram", "factor", "solve", "sketch", "dft", "other", "contract")
 
 
 class _SaveHeader(Structure):

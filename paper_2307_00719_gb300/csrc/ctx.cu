@@ -67,6 +67,20 @@ struct str_ctx {
   // per-step scratch
   DevBuf partial, gnew64, gnew32, enew, mtmp, qtmp, lfac, invd, ring0, ring1, gs, ws, gram,
       xstage, xmix0, xmix1, gmix[STR_MAXN], sgn[STR_MAXN], tab0, tab1, bsum, sums;
+  // tensor-core MTTKRP scratch: split operand, stage-1 result, chain tables, partials,
+  // and the slab with its two fastest modes swapped (made once per slab)
+  DevBuf tc_bhi, tc_blo, tc_y2[2], tc_ta, tc_tb, tc_part, tc_xt, wg_part;
+  const void* tc_xt_src = nullptr;
+  // stage-1 reuse: Y_k = X x_k G_k is kept while the slab and core k are unchanged
+  const void* y_slab[2] = {nullptr, nullptr};
+  const double* y_core[2] = {nullptr, nullptr};
+  uint64_t y_ver[2] = {0, 0};
+  uint64_t core_ver[STR_MAXN] = {};   // bumped whenever a core is rewritten
+  // captured update graphs, keyed by buffer parity, slab shape and buffer generation
+  struct Graph { int parity; int64_t tn; int xtype; uint64_t gen; cudaGraphExec_t exec; int64_t launches; };
+  std::vector<Graph> graphs;
+  std::vector<std::pair<int64_t, int>> warm;   // slab shapes already run without capture
+  uint64_t gen = 0;                            // bumped whenever a scratch buffer is reallocated
   int* d_status = nullptr;
   int* h_status = nullptr;       // pinned
   double* d_pivot = nullptr;
@@ -152,6 +166,7 @@ str_status grow(str_ctx* c, DevBuf& b, size_t bytes) {
   size_t nb = std::max<size_t>(bytes, 256);
   TRY(dalloc(c, &b.p, nb));
   b.cap = nb;
+  c->gen++;
   return STR_OK;
 }
 
@@ -224,6 +239,12 @@ str_status solve_rows(str_ctx* c, const double* Qm, int n, const double* Pm, int
                       double* out64, float* out32, cudaStream_t s) {
   TRY(grow(c, c->lfac, (size_t)n * n * 8));
   TRY(grow(c, c->invd, (size_t)n * 8));
+  if (c->compute == 1) {
+    // FP32 slab arithmetic: FP32 inverse, one FP64-residual refinement step
+    LCHK(c, STR_K_FACTOR, launch_solve_mixed(Qm, n, Pm, rows, 1, (float*)c->lfac.p, (float*)c->invd.p, out64,
+                                             out32, c->d_status, c->d_pivot, s));
+    return STR_OK;
+  }
   LCHK(c, STR_K_FACTOR, launch_chol_factor(Qm, n, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, c->d_pivot, s));
   LCHK(c, STR_K_SOLVE, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, n, Pm, rows, out64, out32, nullptr, s));
   return STR_OK;
@@ -266,10 +287,19 @@ struct SlabView {
   int64_t dim[STR_MAXN];
 };
 
+str_status mttkrp_tc(str_ctx* c, const SlabView& v, int n, const void* const* cores, const double* G64k,
+                     const double* base, double* out, cudaStream_t s, bool* used);
+
 str_status mttkrp_into(str_ctx* c, const SlabView& v, int n, const void* const* cores, bool sampled,
                        const int32_t* idxs, bool lev, const double* const* pk, double wscale,
                        bool cplx, const double* base, double* out, void* gs, double* ws,
                        cudaStream_t s) {
+  if (!sampled && !cplx && c->compute == 1 && c->opt.mttkrp_path == 0) {
+    const int kc = (n == 0) ? 1 : 0;
+    bool used = false;
+    TRY(mttkrp_tc(c, v, n, cores, c->G64[kc][buf_of(c, kc)], base, out, s, &used));
+    if (used) return STR_OK;
+  }
   MttkrpArgs a;
   a.X = v.X;
   a.xtype = v.xtype;
@@ -305,6 +335,88 @@ str_status mttkrp_into(str_ctx* c, const SlabView& v, int n, const void* const* 
   return STR_OK;
 }
 
+
+// Dense FP32-compute MTTKRP on the tensor cores (two stages, see k_tc.cu).
+// cores: FP32 cores as seen in the step (temporal = the slab's rows);
+// G64k: FP64 master of the contracted core k.  Returns false (and does
+// nothing) when the slab layout does not allow the tensor-core path.
+str_status mttkrp_tc(str_ctx* c, const SlabView& v, int n, const void* const* cores, const double* G64k,
+                     const double* base, double* out, cudaStream_t s, bool* used) {
+  *used = false;
+  const int N = c->N;
+  const int k = (n == 0) ? 1 : 0;
+  int64_t E = 1;
+  for (int j = 0; j < N; ++j) E *= v.dim[j];
+  const int K = (int)v.dim[k];
+  const void* Xa = v.X;
+  if (v.xtype != XT_F32 && v.xtype != XT_BF16) return STR_OK;
+  if (k == 1) {
+    // stage 1 needs the contracted mode contiguous: swap the two fastest modes once per slab
+    const size_t es = v.xtype == XT_BF16 ? 2 : 4;
+    if ((K * es) % 16 != 0 || E / (v.dim[0] * v.dim[1]) > 65535) return STR_OK;
+    if (c->tc_xt_src != v.X) {
+      TRY(grow(c, c->tc_xt, (size_t)E * es));
+      LCHK(c, STR_K_OTHER, launch_transpose01(v.X, c->tc_xt.p, v.xtype, (int)v.dim[0], (int)v.dim[1],
+                                              E / (v.dim[0] * v.dim[1]), s));
+      c->tc_xt_src = v.X;
+    }
+    Xa = c->tc_xt.p;
+  }
+  if (!tc_supported(K, v.xtype, Xa)) return STR_OK;
+  const int Rk = c->R[k], Rk1 = c->R[k + 1], RRk = Rk * Rk1;
+  const int Npad = ((RRk + 15) / 16) * 16;
+  const int Kpad = ((K + 31) / 32) * 32;
+  const int64_t M = E / K;
+  DevBuf& ybuf = c->tc_y2[k];
+  if (!(c->y_slab[k] == v.X && c->y_core[k] == G64k && c->y_ver[k] == c->core_ver[k] && ybuf.p)) {
+    TRY(grow(c, c->tc_bhi, (size_t)Npad * Kpad * 4));
+    TRY(grow(c, c->tc_blo, (size_t)Npad * Kpad * 4));
+    TRY(grow(c, ybuf, (size_t)M * RRk * 4));
+    LCHK(c, STR_K_OTHER, launch_prep_b(G64k, K, RRk, Kpad, Npad, (float*)c->tc_bhi.p, (float*)c->tc_blo.p, s));
+    LCHK(c, STR_K_MTTKRP, launch_stage1_tc(Xa, v.xtype, M, K, (const float*)c->tc_bhi.p, (const float*)c->tc_blo.p,
+                                            Kpad, RRk, Npad, (float*)ybuf.p, c->d_status, s));
+    c->y_slab[k] = v.X;
+    c->y_core[k] = G64k;
+    c->y_ver[k] = c->core_ver[k];
+  }
+  // stage 2: groups of modes below / above n (mode k excluded), chain tables
+  Stage2Args a;
+  a.Y = (const float*)ybuf.p;
+  a.Rk = Rk; a.Rk1 = Rk1; a.Rn = c->R[n]; a.Rn1 = c->R[n + 1]; a.k = k;
+  a.dn = v.dim[n];
+  int lo0, lo1, hi0, hi1;   // inclusive mode ranges (lo1 < lo0 = empty)
+  if (k == 0) { lo0 = 1; lo1 = n - 1; hi0 = n + 1; hi1 = N - 1; }
+  else { lo0 = 1; lo1 = 0; hi0 = 2; hi1 = N - 1; }
+  a.Jlo = 1; a.Jhi = 1;
+  for (int j = lo0; j <= lo1; ++j) a.Jlo *= v.dim[j];
+  for (int j = hi0; j <= hi1; ++j) a.Jhi *= v.dim[j];
+  int64_t dims[STR_MAXN];
+  for (int j = 0; j < N; ++j) dims[j] = v.dim[j];
+  if (k == 0 && hi0 <= hi1) {   // A = G_{n+1} .. G_{N-1}
+    TRY(grow(c, c->tc_ta, (size_t)a.Jhi * a.Rn1 * Rk * 4));
+    LCHK(c, STR_K_GRAM, launch_chain_table(cores, 1, c->R, N, dims, hi0, hi1, 0, 0, c->tc_ta.p, s));
+    a.TA = (const float*)c->tc_ta.p;
+  }
+  const int b0 = (k == 0) ? lo0 : hi0, b1 = (k == 0) ? lo1 : hi1;
+  if (b0 <= b1) {               // B = G_{k+1} .. G_{n-1}
+    int64_t J = 1;
+    for (int j = b0; j <= b1; ++j) J *= v.dim[j];
+    TRY(grow(c, c->tc_tb, (size_t)J * Rk1 * a.Rn * 4));
+    LCHK(c, STR_K_GRAM, launch_chain_table(cores, 1, c->R, N, dims, b0, b1, 0, 0, c->tc_tb.p, s));
+    a.TB = (const float*)c->tc_tb.p;
+  }
+  int64_t per = 1;
+  a.splits = stage2_plan_splits(a.dn, a.Jlo * a.Jhi, &per);
+  a.per = per;
+  const int OUTP = a.Rn * a.Rn1;
+  TRY(grow(c, c->tc_part, (size_t)a.splits * a.dn * OUTP * 4));
+  a.partial = (float*)c->tc_part.p;
+  LCHK(c, STR_K_CONTRACT, launch_stage2(a, s));
+  LCHK(c, STR_K_REDUCE, launch_reduce_partials(a.partial, 1, 0, a.splits, a.dn * OUTP, base, 1.0, out, s));
+  *used = true;
+  return STR_OK;
+}
+
 // ---------------------------------------------------------------------------
 // slab intake
 // ---------------------------------------------------------------------------
@@ -320,6 +432,8 @@ str_status take_slab(str_ctx* c, const str_tensor* X, SlabView* v, cudaStream_t 
     count *= X->dims[k];
   }
   v->xtype = xtype_of(X->dtype);
+  c->tc_xt_src = nullptr;
+  c->y_slab[0] = c->y_slab[1] = nullptr;
   if (X->on_host) {
     TRY(grow(c, c->xstage, (size_t)count * dsize(X->dtype)));
     STR_CUDA_TRY(cudaMemcpyAsync(c->xstage.p, X->data, (size_t)count * dsize(X->dtype), cudaMemcpyHostToDevice, s));
@@ -452,6 +566,7 @@ str_status upload_cores(str_ctx* c, const double* const* cores, cudaStream_t s) 
       LCH(c, launch_convert(dst, XT_F64, d32, XT_F32, rows * RR, s));
     }
     if (k < N - 1) LCHK(c, STR_K_GRAM, launch_core_gram(dst, rows, c->R[k], c->R[k + 1], nullptr, c->E[k][c->cur[k]], s));
+    c->core_ver[k]++;
   }
   return STR_OK;
 }
@@ -508,6 +623,7 @@ str_status rstr_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
   int RRmax = 0;
   for (int k = 0; k < N; ++k) RRmax = std::max(RRmax, c->RR(k));
   TRY(grow(c, c->gs, (size_t)m * RRmax * celem(c)));
+  TRY(grow(c, c->wg_part, (size_t)64 * RRmax * RRmax * 8));
   TRY(grow(c, c->ws, (size_t)m * 8));
   int64_t Imax = 0;
   for (int k = 0; k < N; ++k) Imax = std::max(Imax, v.dim[k]);
@@ -532,7 +648,7 @@ str_status rstr_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
     } else {
       TRY(mttkrp_into(c, sv, n, cores, true, idx0, lev, pk, ws, false, nullptr, Pn, c->gs.p, (double*)c->ws.p, s));
     }
-    LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, nullptr, Qn, s));
+    LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, nullptr, Qn, (double*)c->wg_part.p, s));
   }
   return STR_OK;
 }
@@ -619,12 +735,71 @@ str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
                      c->compute == 1 ? c->G32[n][w] : nullptr, s));
       LCHK(c, STR_K_GRAM, launch_core_gram(c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][w], s));
       c->upd[n] = 1;
+      c->core_ver[n]++;
     }
   }
-  // append the new temporal rows
-  STR_CUDA_TRY(cudaMemcpyAsync(c->GT64 + c->t_rows * RRN, gn64, (size_t)tn * RRN * 8, cudaMemcpyDeviceToDevice, s));
+  return STR_OK;
+}
+
+// append the step's new temporal rows after the committed ones (Alg. 4 line 10)
+str_status append_rows(str_ctx* c, int64_t tn, cudaStream_t s) {
+  const int RRN = c->RR(c->N - 1);
+  STR_CUDA_TRY(cudaMemcpyAsync(c->GT64 + c->t_rows * RRN, c->gnew64.p, (size_t)tn * RRN * 8, cudaMemcpyDeviceToDevice, s));
   if (c->compute == 1)
     STR_CUDA_TRY(cudaMemcpyAsync(c->GT32 + c->t_rows * RRN, c->gnew32.p, (size_t)tn * RRN * 4, cudaMemcpyDeviceToDevice, s));
+  return STR_OK;
+}
+
+// str_step through a captured CUDA graph: the slab is staged at a fixed address
+// (c->xstage); the first run of a shape is plain, the next one per buffer parity
+// is captured, later ones replay.  Every launch of str_step is device work on
+// `s`, so the captured graph repeats exactly what a plain run would enqueue.
+str_status str_step_graph(str_ctx* c, SlabView& v, int64_t count, size_t es, cudaStream_t s) {
+  if (v.X != c->xstage.p) {
+    TRY(grow(c, c->xstage, (size_t)count * es));
+    STR_CUDA_TRY(cudaMemcpyAsync(c->xstage.p, v.X, (size_t)count * es, cudaMemcpyDeviceToDevice, s));
+    v.X = c->xstage.p;
+  }
+  const int64_t tn = v.dim[c->N - 1];
+  const int parity = c->cur[0];
+  for (auto& g : c->graphs) {
+    if (g.parity == parity && g.tn == tn && g.xtype == v.xtype && g.gen == c->gen) {
+      STR_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+      for (int k = 0; k < c->N - 1; ++k) { c->upd[k] = 1; c->core_ver[k]++; }
+      c->launches = g.launches;
+      return STR_OK;
+    }
+  }
+  const std::pair<int64_t, int> shape(tn, v.xtype);
+  const bool is_warm = std::find(c->warm.begin(), c->warm.end(), shape) != c->warm.end();
+  if (!is_warm) {
+    TRY(str_step(c, v, s));
+    c->warm.push_back(shape);
+    return STR_OK;
+  }
+  const uint64_t gen0 = c->gen;
+  STR_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  str_status st = str_step(c, v, s);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  if (st != STR_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+  if (ce != cudaSuccess || c->gen != gen0) {
+    // nothing recorded was executed: forget the capture's host-side bookkeeping
+    // and run the step directly
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    for (int k = 0; k < STR_MAXN; ++k) c->upd[k] = 0;
+    c->y_slab[0] = c->y_slab[1] = nullptr;
+    c->tc_xt_src = nullptr;
+    c->launches = 0;
+    return str_step(c, v, s);
+  }
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return from_cuda(ce, "cudaGraphInstantiate");
+  c->graphs.push_back({parity, tn, v.xtype, c->gen, exec, c->launches});
+  STR_CUDA_TRY(cudaGraphLaunch(exec, s));
   return STR_OK;
 }
 
@@ -649,6 +824,7 @@ str_status rstr_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
   TRY(grow(c, c->mtmp, (size_t)Imax * RRmax * 16));
   TRY(grow(c, c->qtmp, (size_t)RRN * RRN * 8));
   TRY(grow(c, c->gs, (size_t)m * RRmax * celem(c)));
+  TRY(grow(c, c->wg_part, (size_t)64 * RRmax * RRmax * 8));
   TRY(grow(c, c->ws, (size_t)m * 8));
   TRY(grow(c, c->sums, (size_t)N * m * 4));
   double* gn64 = (double*)c->gnew64.p;
@@ -686,7 +862,7 @@ str_status rstr_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
   } else {
     TRY(mttkrp_into(c, sv, N - 1, cores, true, idxcat, lev, pk, wsN, false, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
   }
-  LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RRN, nullptr, (double*)c->qtmp.p, s));
+  LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RRN, nullptr, (double*)c->qtmp.p, (double*)c->wg_part.p, s));
   TRY(solve_rows(c, (double*)c->qtmp.p, RRN, ks ? (double*)c->gram.p : (double*)c->mtmp.p, tn, gn64,
                  c->compute == 1 ? (float*)c->gnew32.p : nullptr, s));
   {
@@ -716,9 +892,10 @@ str_status rstr_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
     } else {
       TRY(mttkrp_into(c, sv, n, cores, true, idxcat, lev, pk, wsn, false, c->P[n][c->cur[n]], c->P[n][w], c->gs.p, (double*)c->ws.p, s));
     }
-    LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, c->Q[n][c->cur[n]], c->Q[n][w], s));
+    LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, c->Q[n][c->cur[n]], c->Q[n][w], (double*)c->wg_part.p, s));
     TRY(solve_rows(c, c->Q[n][w], RR, c->P[n][w], c->I[n], c->G64[n][w], c->compute == 1 ? c->G32[n][w] : nullptr, s));
     c->upd[n] = 1;
+    c->core_ver[n]++;
     if (levdraw) {
       TRY(ensure_p(c, n, c->I[n]));
       TRY(leverage(c, c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], c->p[n][w], s));
@@ -805,6 +982,9 @@ str_status str_default_options(str_options* o) {
   o->stream_id = 0;
   o->check_finite = 0;
   o->async_status = 0;
+  o->profile = 0;
+  o->mttkrp_path = 0;
+  o->graphs = 1;
   return STR_OK;
 }
 
@@ -874,6 +1054,7 @@ str_status str_init(str_ctx** out, const str_tensor* X0, const int* ranks, const
       double* o64 = (n == N - 1) ? c->GT64 : c->G64[n][c->cur[n]];
       float* o32 = (c->compute == 1) ? ((n == N - 1) ? c->GT32 : c->G32[n][c->cur[n]]) : nullptr;
       st = solve_rows(c, (double*)c->qtmp.p, RR, (double*)c->mtmp.p, v.dim[n], o64, o32, s);
+      c->core_ver[n]++;
       if (st == STR_OK && n < N - 1)
         st = from_cuda(launch_core_gram(o64, c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][c->cur[n]], s), "core_gram");
     }
@@ -908,7 +1089,16 @@ str_status str_update(str_ctx* c, const str_tensor* X, void* stream) {
   TRY(take_slab(c, X, &v, s));
   const int64_t tn = v.dim[c->N - 1];
   if (c->t_rows + tn > c->opt.t_capacity) return STR_ERR_CAPACITY;
-  str_status st = str_step(c, v, s);
+  str_status st;
+  // the legacy default stream cannot be captured: plain launches there
+  if (c->opt.graphs && !c->opt.profile && s != nullptr && s != cudaStreamLegacy) {
+    int64_t count = 1;
+    for (int k = 0; k < c->N; ++k) count *= v.dim[k];
+    st = str_step_graph(c, v, count, dsize(X->dtype), s);
+  } else {
+    st = str_step(c, v, s);
+  }
+  if (st == STR_OK) st = append_rows(c, tn, s);
   if (st != STR_OK) {
     for (int k = 0; k < STR_MAXN; ++k) c->upd[k] = 0;
     return st;
@@ -959,6 +1149,7 @@ str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, in
     tns[i] = v.dim[c->N - 1];
     if (c->t_rows + tns[i] > c->opt.t_capacity) { st = STR_ERR_CAPACITY; break; }
     st = randomized ? rstr_step(c, v, s) : str_step(c, v, s);
+    if (st == STR_OK && !randomized) st = append_rows(c, tns[i], s);
     done = i + 1;
   }
   bool any_fail = st != STR_OK;
@@ -1247,6 +1438,7 @@ void str_destroy(str_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   for (void* p : c->owned) cudaFree(p);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& e : c->pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : c->pool) cudaEventDestroy(e);
   if (c->h_status) cudaFreeHost(c->h_status);

@@ -70,7 +70,7 @@ struct SmemPlan {
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 __host__ __device__ inline void smem_offsets(int BK, int BM, int RR, int Rb, int Rmid, int esize,
-                                             int tsize, size_t* o) {
+                                             int tsize, int slice_elems, size_t* o) {
   size_t off = 0;
   o[0] = off; off = align16(off + (size_t)BK * STR_MAXN * 4);   // sIdx
   o[1] = off; off = align16(off + (size_t)BK * 8);              // sBase
@@ -79,7 +79,8 @@ __host__ __device__ inline void smem_offsets(int BK, int BM, int RR, int Rb, int
   o[4] = off; off = align16(off + (size_t)BK * RR * esize);     // sS
   o[5] = off; off = align16(off + (size_t)BK * Rb * Rmid * esize);  // sT0
   o[6] = off; off = align16(off + (size_t)BK * Rb * Rmid * esize);  // sT1
-  o[7] = off;
+  o[7] = off; off = align16(off + (size_t)BK * slice_elems * esize); // staged core slices
+  o[8] = off;
 }
 
 template <typename T, bool C, typename XS, int RPT, int CPT>
@@ -100,15 +101,18 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
   for (int t = 0; t < N - 1; ++t) order[t] = (n + 1 + t) % N;
   int Rmid = 1;
   for (int t = 1; t < N - 2; ++t) Rmid = max(Rmid, a.R[order[t] + 1]);
+  int slice_elems = 0;
+  for (int t = 0; t < N - 1; ++t) slice_elems += a.R[order[t]] * a.R[order[t] + 1];
 
-  size_t o[8];
-  smem_offsets(BK, BM, RR, Rb, Rmid, (int)sizeof(E), (int)sizeof(T), o);
+  size_t o[9];
+  smem_offsets(BK, BM, RR, Rb, Rmid, (int)sizeof(E), (int)sizeof(T), slice_elems, o);
   int32_t* sIdx = (int32_t*)(smem + o[0]);
   int64_t* sBase = (int64_t*)(smem + o[1]);
   T* sW = (T*)(smem + o[2]);
   E* sX = (E*)(smem + o[3]);
   E* sS = (E*)(smem + o[4]);
   E* sT[2] = {(E*)(smem + o[5]), (E*)(smem + o[6])};
+  E* sG = (E*)(smem + o[7]);   // slices of the chain cores: [t][jj][R_k R_{k+1}]
 
   const int64_t f_begin = (int64_t)blockIdx.y * a.fib_per_split;
   const int64_t f_end = min(a.nfib, f_begin + a.fib_per_split);
@@ -152,12 +156,30 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
     }
     __syncthreads();
 
-    // (2) subchain slices S_f = F_0 F_1 ... F_{N-2},  F_t = G_{order[t]}(i_{order[t]})
+    // (2a) stage the chain cores' slices G_k(i_k) of this chunk (each slice is
+    //      contiguous in global memory: coalesced copies)
+    {
+      int soff = 0;
+      for (int t = 0; t < N - 1; ++t) {
+        const int k = order[t];
+        const int sz = a.R[k] * a.R[k + 1];
+        const E* Gk = (const E*)a.core[k];
+        E* dst = sG + (size_t)BK * soff;
+        for (int e = tid; e < nf * sz; e += blockDim.x) {
+          const int jj = e / sz, x = e - jj * sz;
+          dst[e] = Gk[(int64_t)sIdx[jj * STR_MAXN + k] * sz + x];
+        }
+        soff += sz;
+      }
+    }
+    __syncthreads();
+    // (2b) subchain slices S_f = F_0 F_1 ... F_{N-2},  F_t = G_{order[t]}(i_{order[t]})
     {
       const int k0 = order[0], k1 = order[1];
       const int R0 = a.R[k0], R1 = a.R[k1], R2 = a.R[k1 + 1];
-      const E* G0 = (const E*)a.core[k0];
-      const E* G1 = (const E*)a.core[k1];
+      const int sz0 = R0 * R1, sz1 = R1 * R2;
+      const E* g0s = sG;
+      const E* g1s = sG + (size_t)BK * sz0;
       const bool last = (N == 3);
       E* dst = last ? sS : sT[0];
       const int cols = R2;
@@ -166,8 +188,8 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
         const int jj = e / (Rb * cols);
         const int rc = e - jj * Rb * cols;
         const int r = rc / cols, c = rc - r * cols;
-        const E* g0 = G0 + (int64_t)sIdx[jj * STR_MAXN + k0] * R0 * R1;
-        const E* g1 = G1 + (int64_t)sIdx[jj * STR_MAXN + k1] * R1 * R2;
+        const E* g0 = g0s + jj * sz0;
+        const E* g1 = g1s + jj * sz1;
         E v = ezero<E>();
         for (int x = 0; x < R1; ++x) mulacc(v, g0[r + R0 * x], g1[x + R1 * c]);
         if (last) dst[jj * RR + c + Ra * r] = v;      // S(b=r, a=c) -> column a + Ra b
@@ -175,11 +197,14 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
       }
       int cur = 0;
       int cur_cols = R2;
+      int soff = sz0 + sz1;
       for (int t = 2; t < N - 1; ++t) {
         __syncthreads();
         const int k = order[t];
         const int Rk = a.R[k], Rk1 = a.R[k + 1];
-        const E* Gk = (const E*)a.core[k];
+        const int szk = Rk * Rk1;
+        const E* gks = sG + (size_t)BK * soff;
+        soff += szk;
         const bool fin = (t == N - 2);
         E* src = sT[cur];
         E* out = fin ? sS : sT[cur ^ 1];
@@ -188,7 +213,7 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
           const int jj = e / (Rb * Rk1);
           const int rc = e - jj * Rb * Rk1;
           const int r = rc / Rk1, c = rc - r * Rk1;
-          const E* gk = Gk + (int64_t)sIdx[jj * STR_MAXN + k] * Rk * Rk1;
+          const E* gk = gks + jj * szk;
           const E* srow = src + jj * Rb * Rmid + r * Rmid;
           E v = ezero<E>();
           for (int x = 0; x < cur_cols; ++x) mulacc(v, srow[x], gk[x + Rk * c]);
@@ -253,9 +278,14 @@ int plan_rmid(const MttkrpArgs& a) {
 size_t smem_bytes(const MttkrpArgs& a, int BK, int BM) {
   const int esize = (a.compute == 2 ? 8 : 4) * (a.cplx ? 2 : 1);
   const int tsize = a.compute == 2 ? 8 : 4;
-  size_t o[8];
-  smem_offsets(BK, BM, a.R[a.n] * a.R[a.n + 1], a.R[a.n + 1], plan_rmid(a), esize, tsize, o);
-  return o[7];
+  int slice_elems = 0;
+  for (int t = 0; t < a.N - 1; ++t) {
+    const int k = (a.n + 1 + t) % a.N;
+    slice_elems += a.R[k] * a.R[k + 1];
+  }
+  size_t o[9];
+  smem_offsets(BK, BM, a.R[a.n] * a.R[a.n + 1], a.R[a.n + 1], plan_rmid(a), esize, tsize, slice_elems, o);
+  return o[8];
 }
 
 template <typename T, bool C, typename XS, int RPT, int CPT>
@@ -286,8 +316,8 @@ cudaError_t launch_rc(const MttkrpArgs& a, cudaStream_t s) {
 int mttkrp_plan_splits(const MttkrpArgs& a, int64_t* fib_per_split) {
   const int BM = a.dim[a.n] <= 16 ? 16 : 64;
   const int gx = ceil_div_i(a.dim[a.n], BM);
-  const int target = 4 * 152;
-  int64_t min_chunk = 128;
+  const int target = 2 * 152;
+  int64_t min_chunk = 256;
   int64_t splits = std::max<int64_t>(1, target / std::max(1, gx));
   splits = std::min<int64_t>(splits, std::max<int64_t>(1, (a.nfib + min_chunk - 1) / min_chunk));
   int64_t per = (a.nfib + splits - 1) / splits;
@@ -318,39 +348,38 @@ cudaError_t launch_mttkrp(const MttkrpArgs& a, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// fixed-order reduction of split partials
+// fixed-order reduction of split partials: a CTA owns 16 outputs; its 16 lane
+// groups each sum the splits g, g+16, g+32, ... and the 16 group sums are then
+// added in group order -- the same order on every run (no atomics).
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void reduce_real_kernel(const T* partial, int splits, int64_t count, const double* base,
-                                   double scale, double* out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < splits; ++k) s += (double)partial[(int64_t)k * count + i];
-    out[i] = (base ? base[i] : 0.0) + scale * s;
-  }
-}
-template <typename T>
-__global__ void reduce_cplx_kernel(const T* partial, int splits, int64_t count, double scale,
-                                   double* out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double re = 0.0, im = 0.0;
-    for (int k = 0; k < splits; ++k) {
-      re += (double)partial[2 * ((int64_t)k * count + i)];
-      im += (double)partial[2 * ((int64_t)k * count + i) + 1];
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(256) reduce_kernel(const T* __restrict__ partial, int splits,
+                                                     int64_t count, const double* __restrict__ base,
+                                                     double scale, double* __restrict__ out) {
+  constexpr int W = CPLX ? 2 : 1;
+  __shared__ double red[16][16 * W];
+  const int o = threadIdx.x & 15, g = threadIdx.x >> 4;
+  const int64_t i = (int64_t)blockIdx.x * 16 + o;
+  double acc[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc[w] = 0.0;
+  if (i < count) {
+    for (int k = g; k < splits; k += 16) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc[w] += (double)partial[((int64_t)k * count + i) * W + w];
     }
-    out[2 * i] = scale * re;
-    out[2 * i + 1] = scale * im;
   }
-}
-template <typename T, typename O>
-__global__ void reduce_to_kernel(const T* partial, int splits, int64_t count, double scale, O* out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < splits; ++k) s += (double)partial[(int64_t)k * count + i];
-    out[i] = (O)(scale * s);
+#pragma unroll
+  for (int w = 0; w < W; ++w) red[g][o * W + w] = acc[w];
+  __syncthreads();
+  if (g == 0 && i < count) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      double sum = 0.0;
+      for (int q = 0; q < 16; ++q) sum += red[q][o * W + w];
+      if (CPLX) out[2 * i + w] = scale * sum;
+      else out[i] = (base ? base[i] : 0.0) + scale * sum;
+    }
   }
 }
 
@@ -363,14 +392,25 @@ cudaError_t launch_reduce_partials(const void* partial, int compute, int cplx, i
                                    int64_t count, const double* base, double scale, double* out,
                                    cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((count + 15) / 16);
   if (cplx) {
-    if (compute == 2) reduce_cplx_kernel<double><<<grid_for(count), 256, 0, s>>>((const double*)partial, splits, count, scale, out);
-    else reduce_cplx_kernel<float><<<grid_for(count), 256, 0, s>>>((const float*)partial, splits, count, scale, out);
+    if (compute == 2) reduce_kernel<double, true><<<blocks, 256, 0, s>>>((const double*)partial, splits, count, nullptr, scale, out);
+    else reduce_kernel<float, true><<<blocks, 256, 0, s>>>((const float*)partial, splits, count, nullptr, scale, out);
   } else {
-    if (compute == 2) reduce_real_kernel<double><<<grid_for(count), 256, 0, s>>>((const double*)partial, splits, count, base, scale, out);
-    else reduce_real_kernel<float><<<grid_for(count), 256, 0, s>>>((const float*)partial, splits, count, base, scale, out);
+    if (compute == 2) reduce_kernel<double, false><<<blocks, 256, 0, s>>>((const double*)partial, splits, count, base, scale, out);
+    else reduce_kernel<float, false><<<blocks, 256, 0, s>>>((const float*)partial, splits, count, base, scale, out);
   }
   return cudaGetLastError();
+}
+
+template <typename T, typename O>
+__global__ void reduce_to_kernel(const T* partial, int splits, int64_t count, double scale, O* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < splits; ++k) s += (double)partial[(int64_t)k * count + i];
+    out[i] = (O)(scale * s);
+  }
 }
 
 cudaError_t launch_reduce_partials_to(const void* partial, int compute, int splits, int64_t count,

@@ -85,17 +85,17 @@ cudaError_t launch_signs(double* d, int64_t I, uint64_t seed, int k, uint64_t ta
 // ---------------------------------------------------------------------------
 template <typename T, bool C>
 __global__ void __launch_bounds__(256) wgram_kernel(const T* __restrict__ g, const double* __restrict__ w,
-                                                    int64_t m, int RR, const double* __restrict__ base,
-                                                    double* __restrict__ out) {
+                                                    int64_t m, int64_t per, int RR, double* __restrict__ part) {
   constexpr int CH = 32;
   constexpr int W = C ? 2 : 1;
   __shared__ double sa[CH][16 * W], sb[CH][16 * W];
   __shared__ double sw[CH];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+  const int64_t sbeg = (int64_t)blockIdx.z * per, send = min(m, sbeg + per);
   double acc = 0.0;
-  for (int64_t s0 = 0; s0 < m; s0 += CH) {
-    const int ns = (m - s0 < CH) ? (int)(m - s0) : CH;
+  for (int64_t s0 = sbeg; s0 < send; s0 += CH) {
+    const int ns = (send - s0 < CH) ? (int)(send - s0) : CH;
     for (int e = threadIdx.x; e < CH * 16 * W; e += 256) {
       const int ss = e / (16 * W), x = e % (16 * W);
       const int cc = x / W, part = x % W;
@@ -118,20 +118,29 @@ __global__ void __launch_bounds__(256) wgram_kernel(const T* __restrict__ g, con
     __syncthreads();
   }
   const int r = r0 + ty, c = c0 + tx;
-  if (r < RR && c < RR) out[(int64_t)r * RR + c] = (base ? base[(int64_t)r * RR + c] : 0.0) + acc;
+  if (r < RR && c < RR) part[((int64_t)blockIdx.z * RR + r) * RR + c] = acc;
 }
 
-cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const double* w, int64_t m,
-                                 int RR, const double* base, double* out, cudaStream_t s) {
-  dim3 grid((unsigned)ceil_div_i(RR, 16), (unsigned)ceil_div_i(RR, 16));
+// out = base + sum over sample splits (fixed order), FP64
+cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const double* w, int64_t m, int RR,
+                                 const double* base, double* out, double* part, cudaStream_t s) {
+  const int tiles = ceil_div_i(RR, 16) * ceil_div_i(RR, 16);
+  int64_t splits = std::max<int64_t>(1, (4 * 152 + tiles - 1) / tiles);
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, m / 64));
+  splits = std::min<int64_t>(splits, 64);
+  const int64_t per = (m + splits - 1) / splits;
+  splits = (m + per - 1) / per;
+  dim3 grid((unsigned)ceil_div_i(RR, 16), (unsigned)ceil_div_i(RR, 16), (unsigned)splits);
   if (compute == 2) {
-    if (cplx) wgram_kernel<double, true><<<grid, 256, 0, s>>>((const double*)gs, w, m, RR, base, out);
-    else wgram_kernel<double, false><<<grid, 256, 0, s>>>((const double*)gs, w, m, RR, base, out);
+    if (cplx) wgram_kernel<double, true><<<grid, 256, 0, s>>>((const double*)gs, w, m, per, RR, part);
+    else wgram_kernel<double, false><<<grid, 256, 0, s>>>((const double*)gs, w, m, per, RR, part);
   } else {
-    if (cplx) wgram_kernel<float, true><<<grid, 256, 0, s>>>((const float*)gs, w, m, RR, base, out);
-    else wgram_kernel<float, false><<<grid, 256, 0, s>>>((const float*)gs, w, m, RR, base, out);
+    if (cplx) wgram_kernel<float, true><<<grid, 256, 0, s>>>((const float*)gs, w, m, per, RR, part);
+    else wgram_kernel<float, false><<<grid, 256, 0, s>>>((const float*)gs, w, m, per, RR, part);
   }
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_partials(part, 2, 0, (int)splits, (int64_t)RR * RR, base, 1.0, out, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -222,6 +231,107 @@ static const double* twiddles(int64_t L) {
   return dptr;
 }
 
+// ---------------------------------------------------------------------------
+// radix-2 FFT along one mode (power-of-two length L <= 4096), in shared memory:
+// bit-reversed load (with the sign pre-multiply), log2(L) in-place butterfly
+// stages (decimation in time), then either the unitary transform written as
+// complex values, or (inverse, unmixing) base + d_k * Re(result) as FP64.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void fft_mode_kernel(const void* __restrict__ in, int in_type, void* __restrict__ out,
+                                int out_real, const double* __restrict__ base, int64_t L, int logL,
+                                int64_t inner, int64_t nfib, const double* __restrict__ dpre,
+                                const double* __restrict__ dpost, int inverse,
+                                const double* __restrict__ tw, int FB) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sre = (T*)smraw;                 // L * FB
+  T* sim = sre + L * FB;              // L * FB
+  T* cs = sim + L * FB;               // L
+  T* sn = cs + L;                     // L
+  for (int64_t j = threadIdx.x; j < L; j += blockDim.x) { cs[j] = (T)tw[2 * j]; sn[j] = (T)tw[2 * j + 1]; }
+  const T scale = (T)(1.0 / sqrt((double)L));
+  const T sgn = inverse ? (T)1 : (T)-1;   // exp(sgn * 2 pi i t / L) = cos + sgn * i sin
+  for (int64_t fb0 = (int64_t)blockIdx.x * FB; fb0 < nfib; fb0 += (int64_t)gridDim.x * FB) {
+    for (int64_t e = threadIdx.x; e < L * FB; e += blockDim.x) {
+      const int ff = (int)(e % FB);
+      const int64_t i = e / FB;
+      const int64_t f = fb0 + ff;
+      T re = 0, im = 0;
+      if (f < nfib) {
+        const int64_t o = (f / inner) * L * inner + i * inner + (f % inner);
+        switch (in_type) {
+          case XT_BF16: re = (T)__bfloat162float(((const __nv_bfloat16*)in)[o]); break;
+          case XT_F32: re = (T)((const float*)in)[o]; break;
+          case XT_F64: re = (T)((const double*)in)[o]; break;
+          case XT_C32: re = (T)((const float*)in)[2 * o]; im = (T)((const float*)in)[2 * o + 1]; break;
+          default: re = (T)((const double*)in)[2 * o]; im = (T)((const double*)in)[2 * o + 1]; break;
+        }
+        if (dpre) { re *= (T)dpre[i]; im *= (T)dpre[i]; }
+      }
+      const int64_t br = (int64_t)(__brev((unsigned)i) >> (32 - logL));
+      sre[br * FB + ff] = re;
+      sim[br * FB + ff] = im;
+    }
+    __syncthreads();
+    for (int st = 0; st < logL; ++st) {
+      const int64_t half = (int64_t)1 << st;
+      const int64_t tstep = L >> (st + 1);     // twiddle index stride = L / len
+      for (int64_t e = threadIdx.x; e < (L / 2) * FB; e += blockDim.x) {
+        const int ff = (int)(e % FB);
+        const int64_t b = e / FB;
+        const int64_t g = b >> st, j = b & (half - 1);
+        const int64_t i0 = g * 2 * half + j, i1 = i0 + half;
+        const int64_t t = j * tstep;
+        const T wr = cs[t], wi = sgn * sn[t];
+        const T xr = sre[i1 * FB + ff], xi = sim[i1 * FB + ff];
+        const T vr = xr * wr - xi * wi, vi = xr * wi + xi * wr;
+        const T ur = sre[i0 * FB + ff], ui = sim[i0 * FB + ff];
+        sre[i0 * FB + ff] = ur + vr;
+        sim[i0 * FB + ff] = ui + vi;
+        sre[i1 * FB + ff] = ur - vr;
+        sim[i1 * FB + ff] = ui - vi;
+      }
+      __syncthreads();
+    }
+    for (int64_t e = threadIdx.x; e < L * FB; e += blockDim.x) {
+      const int ff = (int)(e % FB);
+      const int64_t kk = e / FB;
+      const int64_t f = fb0 + ff;
+      if (f < nfib) {
+        const int64_t o = (f / inner) * L * inner + kk * inner + (f % inner);
+        T yr = sre[kk * FB + ff] * scale, yi = sim[kk * FB + ff] * scale;
+        if (dpost) { yr *= (T)dpost[kk]; yi *= (T)dpost[kk]; }
+        if (out_real) ((double*)out)[o] = (base ? base[o] : 0.0) + (double)yr;
+        else { ((T*)out)[2 * o] = yr; ((T*)out)[2 * o + 1] = yi; }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static int log2_exact(int64_t L) {
+  if (L < 2 || L > 4096 || (L & (L - 1))) return -1;
+  int lg = 0;
+  while (((int64_t)1 << lg) < L) ++lg;
+  return lg;
+}
+
+template <typename T>
+static cudaError_t launch_fft(const void* in, int in_type, void* out, int out_real, const double* base,
+                              int64_t L, int logL, int64_t inner, int64_t nfib, const double* dpre,
+                              const double* dpost, int inverse, const double* tw, cudaStream_t s) {
+  const int tsize = sizeof(T);
+  int FB = 16;
+  while (FB > 1 && (size_t)(2 * L * FB + 2 * L) * tsize > 96 * 1024) FB /= 2;
+  const size_t sm = (size_t)(2 * L * FB + 2 * L) * tsize;
+  cudaError_t e = cudaFuncSetAttribute(fft_mode_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nfib + FB - 1) / FB, 152 * 8));
+  fft_mode_kernel<T><<<(unsigned)blocks, 256, sm, s>>>(in, in_type, out, out_real, base, L, logL, inner, nfib,
+                                                       dpre, dpost, inverse, tw, FB);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dft_mode(const void* in, int in_type, void* out, int out_cplx_compute, int N,
                             const int64_t* dims, int mode, const double* d, cudaStream_t s) {
   const int64_t L = dims[mode];
@@ -230,6 +340,11 @@ cudaError_t launch_dft_mode(const void* in, int in_type, void* out, int out_cplx
   const int64_t nfib = total / L;
   const double* tw = twiddles(L);
   if (!tw) return cudaErrorMemoryAllocation;
+  const int logL = log2_exact(L);
+  if (logL > 0) {
+    if (out_cplx_compute == 2) return launch_fft<double>(in, in_type, out, 0, nullptr, L, logL, inner, nfib, d, nullptr, 0, tw, s);
+    return launch_fft<float>(in, in_type, out, 0, nullptr, L, logL, inner, nfib, d, nullptr, 0, tw, s);
+  }
   const int tsize = out_cplx_compute == 2 ? 8 : 4;
   int FB = 16;
   while (FB > 1 && (size_t)(2 * L * FB + 2 * L) * tsize > 96 * 1024) FB /= 2;
@@ -271,6 +386,9 @@ cudaError_t launch_unmix_rows(const double* Y, int64_t L, int RR, const double* 
                               const double* base, double* out, cudaStream_t s) {
   const double* tw = twiddles(L);
   if (!tw) return cudaErrorMemoryAllocation;
+  const int logL = log2_exact(L);
+  if (logL > 0)   // Y as a (RR, L) tensor, inverse transform along L
+    return launch_fft<double>(Y, XT_C64, out, 1, base, L, logL, RR, RR, nullptr, d, 1, tw, s);
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((L * RR + 255) / 256, 2048));
   unmix_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y, L, RR, d, tw, base, out);
   return cudaGetLastError();

@@ -3,8 +3,9 @@
 //   core Gram        M = G_{(2)}^T G_{(2)},   transfer form E = sum_i G(i) (x) G(i)
 //                    (the Gram tensor Z of Alg. 2 line 2, with its indices permuted)
 //   ring             W = E_{n+1} E_{n+2} ... E_{n-1}  gives  (H^{!=n})_<2>   (Prop. subchain_gram)
-//   solve            G_{n(2)} = P_n Q_n^{-1} by Cholesky (Alg. 4 line 17)
-//   leverage         l_i = ||L^{-1} g_i||^2 with M = L L^T (Lemma lev_est)
+//   solve            G_{n(2)} = P_n Q_n^{-1} (Alg. 4 line 17): FP64 LDL^T + substitution, or
+//                    (FP32 path) Q_n^{-1} from an FP32 symmetric sweep + FP64-residual refinement
+//   leverage         l_i = g_i M^{-1} g_i^T with M = G_{(2)}^T G_{(2)} = L D L^T (Lemma lev_est)
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -12,27 +13,36 @@
 // ---------------------------------------------------------------------------
 // core Gram: one thread per (c, c') pair with c <= c'; writes both halves
 // ---------------------------------------------------------------------------
-__global__ void core_gram_kernel(const double* __restrict__ G, int64_t I, int Ra, int Rb,
-                                 double* __restrict__ M, double* __restrict__ E) {
+__global__ void __launch_bounds__(256) core_gram_kernel(const double* __restrict__ G, int64_t I, int Ra,
+                                                        int Rb, double* __restrict__ M,
+                                                        double* __restrict__ E) {
+  // 64 pairs per CTA, 4 threads per pair each summing every 4th row; the four
+  // partial sums are added in a fixed order
+  __shared__ double red[4][64];
   const int RR = Ra * Rb;
   const int64_t npairs = (int64_t)RR * (RR + 1) / 2;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npairs;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  const int p = threadIdx.x & 63, q = threadIdx.x >> 6;
+  const int64_t t = (int64_t)blockIdx.x * 64 + p;
+  int c = 0, cp = 0;
+  double s = 0.0;
+  if (t < npairs) {
     // decode t -> (c, c') with c <= c'  (row-wise over the upper triangle)
-    int c = 0;
     int64_t rem = t;
     while (rem >= RR - c) { rem -= RR - c; ++c; }
-    const int cp = c + (int)rem;
-    double s = 0.0;
-    for (int64_t i = 0; i < I; ++i) s = fma(G[i * RR + c], G[i * RR + cp], s);
-    if (M) { M[(int64_t)c * RR + cp] = s; M[(int64_t)cp * RR + c] = s; }
-    if (E) {
-      // c = a + Ra b, c' = a' + Ra b'  ->  E[(a + Ra a'), (b + Rb b')]
-      const int a = c % Ra, b = c / Ra, ap = cp % Ra, bp = cp / Ra;
-      const int64_t RR2 = (int64_t)Rb * Rb;
-      E[(int64_t)(a + Ra * ap) * RR2 + (b + Rb * bp)] = s;
-      E[(int64_t)(ap + Ra * a) * RR2 + (bp + Rb * b)] = s;
-    }
+    cp = c + (int)rem;
+    for (int64_t i = q; i < I; i += 4) s = fma(G[i * RR + c], G[i * RR + cp], s);
+  }
+  red[q][p] = s;
+  __syncthreads();
+  if (q != 0 || t >= npairs) return;
+  s = (red[0][p] + red[1][p]) + (red[2][p] + red[3][p]);
+  if (M) { M[(int64_t)c * RR + cp] = s; M[(int64_t)cp * RR + c] = s; }
+  if (E) {
+    // c = a + Ra b, c' = a' + Ra b'  ->  E[(a + Ra a'), (b + Rb b')]
+    const int a = c % Ra, b = c / Ra, ap = cp % Ra, bp = cp / Ra;
+    const int64_t RR2 = (int64_t)Rb * Rb;
+    E[(int64_t)(a + Ra * ap) * RR2 + (b + Rb * bp)] = s;
+    E[(int64_t)(ap + Ra * a) * RR2 + (bp + Rb * b)] = s;
   }
 }
 
@@ -40,86 +50,249 @@ cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double*
                              cudaStream_t s) {
   const int RR = Ra * Rb;
   const int64_t npairs = (int64_t)RR * (RR + 1) / 2;
-  const int threads = 128;
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((npairs + threads - 1) / threads, 2048));
-  core_gram_kernel<<<(unsigned)blocks, threads, 0, s>>>(G, I, Ra, Rb, M, E);
+  const int64_t blocks = std::max<int64_t>(1, (npairs + 63) / 64);
+  core_gram_kernel<<<(unsigned)blocks, 256, 0, s>>>(G, I, Ra, Rb, M, E);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// small FP64 GEMM, one output per thread; optional ring-permute epilogue
+// small FP64 GEMM: 8x8 output tile per 64-thread CTA, A rows and B columns of
+// the tile staged in shared memory (K <= 256); optional ring-permute epilogue
 // ---------------------------------------------------------------------------
-__global__ void gemm64_kernel(const double* __restrict__ A, const double* __restrict__ B,
-                              double* __restrict__ C, int M, int K, int N, int pRa, int pRb,
-                              const double* __restrict__ base) {
-  const int col = blockIdx.x * 8 + (threadIdx.x & 7);
-  const int row = blockIdx.y * 8 + (threadIdx.x >> 3);
+__global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ A,
+                                                     const double* __restrict__ B,
+                                                     double* __restrict__ C, int M, int K, int N,
+                                                     int pRa, int pRb, const double* __restrict__ base) {
+  extern __shared__ double gsm[];
+  double* sA = gsm;            // 8 x K
+  double* sB = gsm + 8 * K;    // K x 8
+  __shared__ double red[4][64];
+  const int r0 = blockIdx.y * 8, c0 = blockIdx.x * 8;
+  for (int e = threadIdx.x; e < 8 * K; e += 256) {
+    const int r = e / K, k = e % K;
+    sA[e] = (r0 + r < M) ? A[(int64_t)(r0 + r) * K + k] : 0.0;
+    const int kk = e / 8, c = e % 8;
+    sB[e] = (c0 + c < N) ? B[(int64_t)kk * N + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  // 64 outputs x 4 slices of K; slices summed in a fixed order
+  const int o = threadIdx.x & 63, q = threadIdx.x >> 6;
+  const double* a = sA + (o >> 3) * K;
+  const double* b = sB + (o & 7);
+  double s0 = 0.0;
+  for (int k = q; k < K; k += 4) s0 = fma(a[k], b[k * 8], s0);
+  red[q][o] = s0;
+  __syncthreads();
+  if (q != 0) return;
+  const int col = c0 + (o & 7);
+  const int row = r0 + (o >> 3);
   if (row >= M || col >= N) return;
-  double s = 0.0;
-  for (int k = 0; k < K; ++k) s = fma(A[(int64_t)row * K + k], B[(int64_t)k * N + col], s);
+  const double s = (red[0][o] + red[1][o]) + (red[2][o] + red[3][o]);
   if (pRa <= 0) {
     C[(int64_t)row * N + col] = s;
   } else {
     // row = b + Rb b', col = a + Ra a'  ->  Q[a + Ra b][a' + Ra b']
-    const int b = row % pRb, bp = row / pRb, a = col % pRa, ap = col / pRa;
+    const int bb = row % pRb, bp = row / pRb, aa = col % pRa, ap = col / pRa;
     const int RR = pRa * pRb;
-    const int64_t q = (int64_t)(a + pRa * b) * RR + (ap + pRa * bp);
-    C[q] = (base ? base[q] : 0.0) + s;
+    const int64_t qi = (int64_t)(aa + pRa * bb) * RR + (ap + pRa * bp);
+    C[qi] = (base ? base[qi] : 0.0) + s;
   }
 }
 
 cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, int K, int N,
                           int perm_Ra, int perm_Rb, const double* base, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div_i(N, 8), (unsigned)ceil_div_i(M, 8));
-  gemm64_kernel<<<grid, 64, 0, s>>>(A, B, C, M, K, N, perm_Ra, perm_Rb, base);
+  const size_t sm = (size_t)16 * K * sizeof(double);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gemm64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  gemm64_kernel<<<grid, 256, sm, s>>>(A, B, C, M, K, N, perm_Ra, perm_Rb, base);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky factorisation in shared memory (right-looking, one CTA)
+// Inverse of an SPD matrix by the symmetric sweep (in-place Gauss-Jordan without
+// pivoting; its pivots are the Schur-complement pivots of the LDL^T / Cholesky
+// factorisation).  256 threads as a 16 x 16 grid; thread (ty, tx) keeps the
+// entries (ty + 16a, tx + 16b), a, b < B, in registers.  Per pivot k the owners
+// of column k publish it to shared memory (double-buffered), then every thread
+// updates its entries: one barrier per pivot.  After n sweeps the matrix holds
+// -Q^{-1}.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restrict__ Q, int n,
-                                                          double* __restrict__ L,
-                                                          double* __restrict__ invdiag,
-                                                          int* status, double* pivot_ratio) {
-  extern __shared__ double A[];   // n x n, row-major, lower triangle used
-  __shared__ double s_tol, s_ratio;
+template <typename T, int B>
+__global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __restrict__ Q, int n,
+                                                            T* __restrict__ W, int* status,
+                                                            double* pivot_ratio) {
+  __shared__ T col[2][16 * B];
+  __shared__ T qd[16 * B];
   __shared__ int s_bad;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < n * n; e += blockDim.x) A[e] = Q[e];
+  __shared__ T s_ratio;
+  __shared__ T s_tol;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T a[B][B];
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      a[i][j] = (r < n && c < n) ? (T)Q[(int64_t)r * n + c] : (T)0;
+    }
+  for (int k = tid; k < n; k += 256) qd[k] = (T)Q[(int64_t)k * n + k];
+  __syncthreads();
   if (tid == 0) {
-    double mx = 0.0;
-    for (int k = 0; k < n; ++k) mx = fmax(mx, Q[(int64_t)k * n + k]);
-    s_tol = (double)n * 2.220446049250313e-16 * mx;
-    s_ratio = 1.0;
+    T mx = 0;
+    for (int k = 0; k < n; ++k) mx = mx > qd[k] ? mx : qd[k];
+    s_tol = (T)n * (T)(sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07) * mx;
     s_bad = 0;
+    s_ratio = (T)1;
   }
   __syncthreads();
-  const int tx = tid & 31, ty = tid >> 5, nty = blockDim.x >> 5;
+  const T tol = s_tol;
   for (int k = 0; k < n; ++k) {
+    const int par = k & 1, kb = k >> 4, kr = k & 15;
+    if (tx == kr) {
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        const int r = ty + 16 * i;
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+          if (j == kb && r < n) col[par][r] = a[i][j];
+      }
+    }
+    __syncthreads();
+    T piv = col[par][k];
+    const bool bad = !(piv > tol);
+    if (bad) piv = (T)1;
+    const T rcp = (T)1 / piv;
     if (tid == 0) {
-      double d = A[k * n + k];
-      const double q = Q[(int64_t)k * n + k];
-      if (!(d > s_tol)) { s_bad = 1; d = 1.0; }
-      else if (q > 0) s_ratio = fmin(s_ratio, d / q);
-      const double r = sqrt(d);
-      A[k * n + k] = r;
-      invdiag[k] = 1.0 / r;
+      if (bad) s_bad = 1;
+      else if (qd[k] > (T)0 && piv * rcp * rcp * qd[k] > (T)0) {
+        const T ratio = piv / qd[k];
+        s_ratio = ratio < s_ratio ? ratio : s_ratio;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int r = ty + 16 * i;
+      if (r >= n) continue;
+      const T ci = col[par][r];
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        const int c = tx + 16 * j;
+        if (c >= n) continue;
+        const T cj = col[par][c];
+        if (r == k && c == k) a[i][j] = -rcp;
+        else if (r == k) a[i][j] = cj * rcp;
+        else if (c == k) a[i][j] = ci * rcp;
+        else a[i][j] -= ci * cj * rcp;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      if (r < n && c < n) W[(int64_t)r * n + c] = -a[i][j];
+    }
+  if (tid == 0) {
+    if (s_bad && status) atomicOr(status, DEV_ERR_SINGULAR);
+    if (pivot_ratio) *pivot_ratio = (double)s_ratio;
+  }
+}
+
+template <typename T>
+static cudaError_t launch_sweep(const double* Q, int n, T* W, int* status, double* pivot_ratio, cudaStream_t s) {
+  if (n <= 16) sweep_inverse_kernel<T, 1><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
+  else if (n <= 32) sweep_inverse_kernel<T, 2><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
+  else if (n <= 64) sweep_inverse_kernel<T, 4><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
+  else if (n <= 112) sweep_inverse_kernel<T, 7><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
+  else if (n <= 160) sweep_inverse_kernel<T, 10><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 LDL^T, register-blocked like the sweep: thread (ty, tx) keeps entries
+// (ty + 16a, tx + 16b).  Per pivot k the owners of column k publish it (double
+// buffered) and the owner of (k, k) publishes 1/d_k: one barrier per pivot and
+// one FP64 division per pivot.  Only the lower triangle is updated (n^3/6 FMA).
+// Output: unit lower L (row-major) and invdiag = 1/d.
+// ---------------------------------------------------------------------------
+template <int B>
+__global__ void __launch_bounds__(256) ldlt64_kernel(const double* __restrict__ Q, int n,
+                                                     double* __restrict__ L, double* __restrict__ invdiag,
+                                                     int* status, double* pivot_ratio) {
+  __shared__ double col[2][16 * B];
+  __shared__ double rb[2];
+  __shared__ double sinv[16 * B];
+  __shared__ double qd[16 * B];
+  __shared__ double s_tol, s_ratio;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double a[B][B];
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      a[i][j] = (r < n && c < n && c <= r) ? Q[(int64_t)r * n + c] : 0.0;
+    }
+  for (int k = tid; k < n; k += 256) qd[k] = Q[(int64_t)k * n + k];
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < n; ++k) mx = fmax(mx, qd[k]);
+    s_tol = (double)n * 2.220446049250313e-16 * mx;
+    s_bad = 0;
+    s_ratio = 1.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const int par = k & 1, kb = k >> 4, kr = k & 15;
+    if (tx == kr) {
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        const int r = ty + 16 * i;
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+          if (j == kb && r < n && r >= k) {
+            col[par][r] = a[i][j];
+            if (r == k) {   // pivot owner
+              double d = a[i][j];
+              if (!(d > s_tol)) { s_bad = 1; d = 1.0; }
+              else if (qd[k] > 0) s_ratio = fmin(s_ratio, d / qd[k]);
+              const double rc = 1.0 / d;
+              rb[par] = rc;
+              sinv[k] = rc;
+            }
+          }
+      }
     }
     __syncthreads();
-    const double inv = 1.0 / A[k * n + k];
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) A[i * n + k] *= inv;
-    __syncthreads();
-    for (int i = k + 1 + ty; i < n; i += nty) {
-      const double lik = A[i * n + k];
-      for (int j = k + 1 + tx; j <= i; j += 32) A[i * n + j] = fma(-lik, A[j * n + k], A[i * n + j]);
+    const double rc = rb[par];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int r = ty + 16 * i;
+      if (r <= k || r >= n) continue;
+      const double li = col[par][r] * rc;
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        const int c = tx + 16 * j;
+        if (c > k && c <= r) a[i][j] = fma(-li, col[par][c], a[i][j]);
+      }
     }
-    __syncthreads();
   }
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    L[e] = (j <= i) ? A[e] : 0.0;
-  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      if (r < n && c < n) L[(int64_t)r * n + c] = (c < r) ? a[i][j] * sinv[c] : (c == r ? 1.0 : 0.0);
+    }
+  for (int k = tid; k < n; k += 256) invdiag[k] = sinv[k];
   if (tid == 0) {
     if (s_bad && status) atomicOr(status, DEV_ERR_SINGULAR);
     if (pivot_ratio) *pivot_ratio = s_ratio;
@@ -128,54 +301,55 @@ __global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restri
 
 cudaError_t launch_chol_factor(const double* Q, int n, double* L, double* invdiag, int* status,
                                double* pivot_ratio, cudaStream_t s) {
-  const size_t sm = (size_t)n * n * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(chol_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  chol_factor_kernel<<<1, 256, sm, s>>>(Q, n, L, invdiag, status, pivot_ratio);
+  if (n <= 16) ldlt64_kernel<1><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
+  else if (n <= 32) ldlt64_kernel<2><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
+  else if (n <= 64) ldlt64_kernel<4><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
+  else if (n <= 112) ldlt64_kernel<7><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
+  else if (n <= 160) ldlt64_kernel<10><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// row solves with L in shared memory; one warp per right-hand side row
+// row solves x = p Q^{-1} = p L^{-T} D^{-1} L^{-1} with L (unit) in shared
+// memory (padded rows); one warp per right-hand side row, 4 warps per CTA.
+// leverage mode: lev[r] = ||D^{-1/2} L^{-1} p||^2 / n.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) chol_solve_kernel(const double* __restrict__ Lg,
+__global__ void __launch_bounds__(128) chol_solve_kernel(const double* __restrict__ Lg,
                                                          const double* __restrict__ invdiag, int n,
                                                          const double* __restrict__ P, int64_t rows,
                                                          double* out64, float* out32, double* lev) {
   extern __shared__ double sm[];
-  double* L = sm;                       // n x n
-  double* inv = L + n * n;              // n
-  double* ys = inv + n;                 // 8 warps x n
+  const int ld = n + 1;
+  double* L = sm;                       // n x ld
+  double* inv = L + n * ld;             // n
+  double* ys = inv + n;                 // 4 warps x n
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < n * n; e += blockDim.x) L[e] = Lg[e];
+  for (int e = tid; e < n * n; e += blockDim.x) L[(e / n) * ld + (e % n)] = Lg[e];
   for (int e = tid; e < n; e += blockDim.x) inv[e] = invdiag[e];
   __syncthreads();
   double* y = ys + warp * n;
-  for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < rows; r += (int64_t)gridDim.x * 8) {
+  for (int64_t r = (int64_t)blockIdx.x * 4 + warp; r < rows; r += (int64_t)gridDim.x * 4) {
     for (int j = lane; j < n; j += 32) y[j] = P[r * n + j];
     __syncwarp();
-    // forward: L y = p
-    for (int k = 0; k < n; ++k) {
-      const double yk = y[k] * inv[k];
-      __syncwarp();
-      if (lane == 0) y[k] = yk;
-      for (int j = k + 1 + lane; j < n; j += 32) y[j] = fma(-L[j * n + k], yk, y[j]);
+    for (int k = 0; k < n - 1; ++k) {
+      const double yk = y[k];
+      for (int j = k + 1 + lane; j < n; j += 32) y[j] = fma(-L[j * ld + k], yk, y[j]);
       __syncwarp();
     }
     if (lev) {
-      double s = 0.0;
-      for (int j = lane; j < n; j += 32) s = fma(y[j], y[j], s);
-      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) lev[r] = s / n;
+      double sum = 0.0;
+      for (int j = lane; j < n; j += 32) sum = fma(y[j] * inv[j], y[j], sum);
+      for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) lev[r] = sum / n;
       __syncwarp();
       continue;
     }
-    // backward: L^T x = y
-    for (int k = n - 1; k >= 0; --k) {
-      const double xk = y[k] * inv[k];
-      __syncwarp();
-      if (lane == 0) y[k] = xk;
-      for (int j = lane; j < k; j += 32) y[j] = fma(-L[k * n + j], xk, y[j]);
+    for (int j = lane; j < n; j += 32) y[j] *= inv[j];
+    __syncwarp();
+    for (int k = n - 1; k > 0; --k) {
+      const double xk = y[k];
+      for (int j = lane; j < k; j += 32) y[j] = fma(-L[k * ld + j], xk, y[j]);
       __syncwarp();
     }
     for (int j = lane; j < n; j += 32) {
@@ -190,11 +364,82 @@ cudaError_t launch_chol_solve(const double* L, const double* invdiag, int n, con
                               int64_t rows, double* out64, float* out32, double* lev,
                               cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
-  const size_t sm = ((size_t)n * n + n + 8 * (size_t)n) * sizeof(double);
+  const size_t sm = ((size_t)n * (n + 1) + n + 4 * (size_t)n) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, 152 * 2));
-  chol_solve_kernel<<<(unsigned)blocks, 256, sm, s>>>(L, invdiag, n, P, rows, out64, out32, lev);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((rows + 3) / 4, 152 * 2));
+  chol_solve_kernel<<<(unsigned)blocks, 128, sm, s>>>(L, invdiag, n, P, rows, out64, out32, lev);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision (FP32 slab arithmetic): W32 = Q^{-1} by the FP32 sweep, then
+// per row g = p W32 followed by `iters` refinement steps
+// r = p - g Q (FP64, Q symmetric), g += r W32.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(64) solve_refine_kernel(const float* __restrict__ Wg,
+                                                          const double* __restrict__ Q, int n,
+                                                          const double* __restrict__ P, int64_t rows,
+                                                          int iters, double* out64, float* out32) {
+  extern __shared__ unsigned char smr[];
+  float* Wm = (float*)smr;                                                    // n x n
+  double* vs = (double*)(((uintptr_t)(Wm + n * n) + 7) & ~(uintptr_t)7);     // 2 warps x 2 x n
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < n * n; e += blockDim.x) Wm[e] = Wg[e];
+  __syncthreads();
+  double* v = vs + warp * 2 * n;      // right-hand side of the current product
+  double* g = v + n;                  // solution
+  for (int64_t r = (int64_t)blockIdx.x * 2 + warp; r < rows; r += (int64_t)gridDim.x * 2) {
+    const double* p = P + r * n;
+    for (int j = lane; j < n; j += 32) { v[j] = p[j]; g[j] = 0.0; }
+    __syncwarp();
+    for (int it = 0; it <= iters; ++it) {
+      // g += v W32   (v = p on the first pass, then the FP64 residual)
+      for (int c = lane; c < n; c += 32) {
+        float a0 = 0.f, a1 = 0.f;
+        int cp = 0;
+        for (; cp + 1 < n; cp += 2) {
+          a0 = fmaf((float)v[cp], Wm[cp * n + c], a0);
+          a1 = fmaf((float)v[cp + 1], Wm[(cp + 1) * n + c], a1);
+        }
+        if (cp < n) a0 = fmaf((float)v[cp], Wm[cp * n + c], a0);
+        g[c] += (double)(a0 + a1);
+      }
+      __syncwarp();
+      if (it == iters) break;
+      // v = p - g Q in FP64
+      for (int c = lane; c < n; c += 32) {
+        double acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+        int cp = 0;
+        for (; cp + 8 <= n; cp += 8) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u] = fma(-g[cp + u], Q[(int64_t)(cp + u) * n + c], acc[u]);
+        }
+        for (; cp < n; ++cp) acc[0] = fma(-g[cp], Q[(int64_t)cp * n + c], acc[0]);
+        v[c] = p[c] + (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
+      }
+      __syncwarp();
+    }
+    for (int j = lane; j < n; j += 32) {
+      if (out64) out64[r * n + j] = g[j];
+      if (out32) out32[r * n + j] = (float)g[j];
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_solve_mixed(const double* Q, int n, const double* P, int64_t rows, int iters,
+                               float* W32, float* /*unused*/, double* out64, float* out32, int* status,
+                               double* pivot_ratio, cudaStream_t s) {
+  cudaError_t e = launch_sweep<float>(Q, n, W32, status, pivot_ratio, s);
+  if (e != cudaSuccess || rows <= 0) return e;
+  const size_t sms = (size_t)n * n * sizeof(float) + 8 + 4 * (size_t)n * sizeof(double);
+  e = cudaFuncSetAttribute(solve_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((rows + 1) / 2, 152 * 4));
+  solve_refine_kernel<<<(unsigned)blocks, 64, sms, s>>>(W32, Q, n, P, rows, iters, out64, out32);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,653 @@
+// Dense slab MTTKRP on the 5th-generation tensor cores (tcgen05), FP32 results.
+//
+// The subchain of mode n is split at one contracted mode k (k = 1 when n = 1,
+// else k = 1's neighbour 0; both 0-based here as k = 0 / k = 1):
+//     G^{!=n}(j) = A(i_A) G_k(i_k) B(i_B),
+// A = G_{n+1} ... G_{k-1},  B = G_{k+1} ... G_{n-1}  (cyclic, either may be empty).
+// Then  X_[n] G^{!=n}_[2]  (Eq. partial)  is computed in two stages:
+//   stage 1  Y = X x_k G_k : a GEMM  [M = E / I_k] x [K = I_k] x [N = R_k R_{k+1}]
+//            on tcgen05.mma (kind::tf32) with A tiles fed by TMA, accumulator in
+//            TMEM.  FP32 accuracy comes from a 3-term split: X = X_hi + X_lo and
+//            G = G_hi + G_lo, both terms rounded to nearest TF32 before the MMA
+//            (so the hardware's TF32 conversion is exact and unbiased), products
+//            X_hi G_hi + X_hi G_lo + X_lo G_hi.  A BF16 slab is exact in TF32
+//            (X_lo = 0), so it needs two products.
+//   stage 2  P(i_n, a + R_n b) = sum_{i_A, i_B, c, d} A(b,c) Y(.., c + R_k d) B(d,a)
+//            with A and B read from precomputed chain tables (SIMT, FP32).
+#include <cuda.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on an mbarrier phase: false after `ns` nanoseconds
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t ns) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (gtimer() - t0 > ns) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld_x8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                 "=r"(v[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes in 8-row atoms of 1024 bytes (stride between atoms = 1024 B).
+__device__ __forceinline__ uint64_t desc_sw128(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;          // start address (16-byte units)
+  d |= (uint64_t)1 << 16;                // leading-dimension offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;      // stride-dimension offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                // 128-byte swizzle
+  return d;
+}
+
+// byte offset of the 16-byte chunk j of row r in a 128B-swizzled K-major tile
+__device__ __forceinline__ int sw128_off(int r, int j) {
+  return (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4);
+}
+
+// round to the nearest TF32 value (ties away from zero); the result is exact in TF32,
+// so the tensor core's own conversion of it is the identity
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: far above any legitimate wait
+
+// ---------------------------------------------------------------------------
+// stage 1: one CTA per 128-row tile of Y, K in chunks of 32
+// ---------------------------------------------------------------------------
+template <bool SRC_BF16>
+__global__ void __launch_bounds__(128, 1) stage1_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                           const float* __restrict__ Bhi,
+                                                           const float* __restrict__ Blo, int M,
+                                                           int Kpad, int N, int Npad, uint32_t tmem_cols,
+                                                           float* __restrict__ Y, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sAhi = smem;                              // 128 x 128 B
+  unsigned char* sAlo = smem + 16384;                      // 128 x 128 B
+  unsigned char* sBhi = smem + 32768;                      // Npad x 128 B
+  unsigned char* sBlo = sBhi + (size_t)Npad * 128;         // Npad x 128 B
+  unsigned char* sAraw = sBlo + (size_t)Npad * 128;        // 128 x 32 source elements
+  uint64_t* bars = (uint64_t*)(sAraw + 16384);
+  uint32_t* tslot = (uint32_t*)(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * 128;
+
+  if (warp == 0) tmem_alloc(tslot, tmem_cols);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Npad >> 3) << 17) |
+                         ((uint32_t)(128 >> 4) << 24);
+  const uint32_t box_bytes = SRC_BF16 ? 128 * 32 * 2 : 128 * 32 * 4;
+  uint32_t ph_tma = 0, ph_mma = 0;
+  bool failed = false;
+  const int nchunks = Kpad / 32;
+  for (int c = 0; c < nchunks && !failed; ++c) {
+    if (tid == 0) {
+      mbar_expect_tx(&bars[0], box_bytes);
+      tma_load_2d(sAraw, &tmA, &bars[0], c * 32, m0);
+    }
+    // B chunk: rows n < Npad, columns 32c .. 32c+31 of the pre-split operand
+    for (int r = tid >> 3; r < Npad; r += 16) {
+      const int j = tid & 7;
+      const float4 h = *(const float4*)(Bhi + (size_t)r * Kpad + c * 32 + j * 4);
+      const float4 l = *(const float4*)(Blo + (size_t)r * Kpad + c * 32 + j * 4);
+      *(float4*)(sBhi + sw128_off(r, j)) = h;
+      *(float4*)(sBlo + sw128_off(r, j)) = l;
+    }
+    const bool ok = mbar_wait(&bars[0], ph_tma, kWaitNs);
+    ph_tma ^= 1;
+    if (__syncthreads_or(!ok)) { failed = true; break; }
+    // A chunk: split into hi / lo and write the swizzled operand tiles
+    for (int p = 0; p < 8; ++p) {
+      const int r = p * 16 + (tid >> 3);
+      const int j = tid & 7;
+      float4 v;
+      if (SRC_BF16) {
+        const __nv_bfloat162* q = (const __nv_bfloat162*)(sAraw + r * 64 + j * 8);
+        const float2 a = __bfloat1622float2(q[0]), b = __bfloat1622float2(q[1]);
+        v = make_float4(a.x, a.y, b.x, b.y);
+      } else {
+        v = *(const float4*)(sAraw + r * 128 + j * 16);
+      }
+      const float4 hi = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+      *(float4*)(sAhi + sw128_off(r, j)) = hi;
+      if (!SRC_BF16) {
+        const float4 lo = make_float4(tf32_rn(v.x - hi.x), tf32_rn(v.y - hi.y), tf32_rn(v.z - hi.z),
+                                      tf32_rn(v.w - hi.w));
+        *(float4*)(sAlo + sw128_off(r, j)) = lo;
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint64_t ah = desc_sw128(sAhi), al = desc_sw128(sAlo);
+      const uint64_t bh = desc_sw128(sBhi), bl = desc_sw128(sBlo);
+      // three accumulators: hi*hi products alternate between columns [0, Npad) and
+      // [Npad, 2 Npad); the small cross terms go to [2 Npad, 3 Npad).  Shorter
+      // accumulation chains keep the accumulator's rounding error down.
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t adv = (uint64_t)(kk * 32) >> 4;   // 8 TF32 = 32 bytes along K
+        const int step = c * 4 + kk;
+        const uint32_t dhi = tmem + (uint32_t)((step & 1) * Npad);
+        const uint32_t dx = tmem + (uint32_t)(2 * Npad);
+        mma_tf32(dhi, ah + adv, bh + adv, idesc, step >= 2 ? 1u : 0u);
+        mma_tf32(dx, ah + adv, bl + adv, idesc, step >= 1 ? 1u : 0u);
+        if (!SRC_BF16) mma_tf32(dx, al + adv, bh + adv, idesc, 1u);
+      }
+      mma_commit(&bars[1]);
+    }
+    const bool ok2 = mbar_wait(&bars[1], ph_mma, kWaitNs);
+    ph_mma ^= 1;
+    if (__syncthreads_or(!ok2)) { failed = true; break; }
+  }
+  tc_fence_after();
+  if (!failed) {
+    const int row = m0 + 32 * warp + lane;
+    const bool two = nchunks * 4 >= 2;   // the second hi*hi accumulator was written
+    for (int col = 0; col < Npad; col += 8) {
+      const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col;
+      uint32_t v0[8], v1[8], vx[8];
+      tmem_ld_x8(base, v0);
+      tmem_ld_x8(base + (uint32_t)Npad, v1);
+      tmem_ld_x8(base + (uint32_t)(2 * Npad), vx);
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float y = __uint_as_float(v0[j]) + __uint_as_float(vx[j]);
+          if (two) y += __uint_as_float(v1[j]);
+          if (col + j < N) Y[(size_t)row * N + col + j] = y;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(status, DEV_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, tmem_cols);
+}
+
+// ---------------------------------------------------------------------------
+// stage 1, persistent form: one CTA per SM loops over 128-row tiles.  The split
+// B operand (all K chunks) is loaded once into shared memory; the next tile's
+// A chunks are prefetched by TMA into a second raw buffer while the current
+// tile is converted, multiplied and written out.
+// ---------------------------------------------------------------------------
+template <bool SRC_BF16>
+__global__ void __launch_bounds__(128, 1) stage1_tc_persist_kernel(
+    const __grid_constant__ CUtensorMap tmA, const float* __restrict__ Bhi, const float* __restrict__ Blo,
+    int M, int Kpad, int N, int Npad, uint32_t tmem_cols, float* __restrict__ Y, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int nch = Kpad / 32;
+  const size_t bchunk = (size_t)Npad * 128;
+  unsigned char* sBhi = smem;                                   // nch x (Npad x 128 B)
+  unsigned char* sBlo = sBhi + nch * bchunk;
+  unsigned char* sAhi = sBlo + nch * bchunk;                    // nch x 16 KB
+  unsigned char* sAlo = sAhi + (size_t)nch * 16384;
+  unsigned char* sRaw = sAlo + (size_t)nch * 16384;             // 2 x nch x 16 KB
+  uint64_t* bars = (uint64_t*)(sRaw + (size_t)2 * nch * 16384); // tma[0], tma[1], mma
+  uint32_t* tslot = (uint32_t*)(bars + 3);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = (M + 127) / 128;
+  const uint32_t chunk_bytes = SRC_BF16 ? 128 * 32 * 2 : 128 * 32 * 4;
+
+  if (warp == 0) tmem_alloc(tslot, tmem_cols);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  if (tid == 0 && (int)blockIdx.x < ntiles) {
+    mbar_expect_tx(&bars[0], chunk_bytes * nch);
+    for (int c = 0; c < nch; ++c) tma_load_2d(sRaw + (size_t)c * 16384, &tmA, &bars[0], c * 32, blockIdx.x * 128);
+  }
+  // the whole split B operand, swizzled, once per CTA
+  for (int c = 0; c < nch; ++c)
+    for (int r = tid >> 3; r < Npad; r += 16) {
+      const int j = tid & 7;
+      *(float4*)(sBhi + c * bchunk + sw128_off(r, j)) = *(const float4*)(Bhi + (size_t)r * Kpad + c * 32 + j * 4);
+      *(float4*)(sBlo + c * bchunk + sw128_off(r, j)) = *(const float4*)(Blo + (size_t)r * Kpad + c * 32 + j * 4);
+    }
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Npad >> 3) << 17) |
+                         ((uint32_t)(128 >> 4) << 24);
+  uint32_t ph_tma[2] = {0, 0}, ph_mma = 0;
+  bool failed = false;
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int buf = it & 1;
+    const int tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) {   // prefetch the next tile into the other raw buffer
+      mbar_expect_tx(&bars[buf ^ 1], chunk_bytes * nch);
+      for (int c = 0; c < nch; ++c)
+        tma_load_2d(sRaw + ((size_t)(buf ^ 1) * nch + c) * 16384, &tmA, &bars[buf ^ 1], c * 32, tn * 128);
+    }
+    const bool ok = mbar_wait(&bars[buf], ph_tma[buf], kWaitNs);
+    ph_tma[buf] ^= 1;
+    if (__syncthreads_or(!ok)) { failed = true; break; }
+    for (int c = 0; c < nch; ++c) {
+      const unsigned char* raw = sRaw + ((size_t)buf * nch + c) * 16384;
+      unsigned char* ah = sAhi + (size_t)c * 16384;
+      unsigned char* al = sAlo + (size_t)c * 16384;
+      for (int p = 0; p < 8; ++p) {
+        const int r = p * 16 + (tid >> 3);
+        const int j = tid & 7;
+        float4 v;
+        if (SRC_BF16) {
+          const __nv_bfloat162* q = (const __nv_bfloat162*)(raw + r * 64 + j * 8);
+          const float2 x0 = __bfloat1622float2(q[0]), x1 = __bfloat1622float2(q[1]);
+          v = make_float4(x0.x, x0.y, x1.x, x1.y);
+        } else {
+          v = *(const float4*)(raw + r * 128 + j * 16);
+        }
+        const float4 hi = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+        *(float4*)(ah + sw128_off(r, j)) = hi;
+        if (!SRC_BF16)
+          *(float4*)(al + sw128_off(r, j)) = make_float4(tf32_rn(v.x - hi.x), tf32_rn(v.y - hi.y),
+                                                         tf32_rn(v.z - hi.z), tf32_rn(v.w - hi.w));
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int c = 0; c < nch; ++c) {
+        const uint64_t ah = desc_sw128(sAhi + (size_t)c * 16384), al = desc_sw128(sAlo + (size_t)c * 16384);
+        const uint64_t bh = desc_sw128(sBhi + c * bchunk), bl = desc_sw128(sBlo + c * bchunk);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+          const int step = c * 4 + kk;
+          const uint32_t dhi = tmem + (uint32_t)((step & 1) * Npad);
+          const uint32_t dx = tmem + (uint32_t)(2 * Npad);
+          mma_tf32(dhi, ah + adv, bh + adv, idesc, step >= 2 ? 1u : 0u);
+          mma_tf32(dx, ah + adv, bl + adv, idesc, step >= 1 ? 1u : 0u);
+          if (!SRC_BF16) mma_tf32(dx, al + adv, bh + adv, idesc, 1u);
+        }
+      }
+      mma_commit(&bars[2]);
+    }
+    const bool ok2 = mbar_wait(&bars[2], ph_mma, kWaitNs);
+    ph_mma ^= 1;
+    if (__syncthreads_or(!ok2)) { failed = true; break; }
+    tc_fence_after();
+    const int row = t * 128 + 32 * warp + lane;
+    for (int col = 0; col < Npad; col += 16) {
+      const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col;
+      uint32_t v0[16], v1[16], vx[16];
+      tmem_ld_x16(base, v0);
+      tmem_ld_x16(base + (uint32_t)Npad, v1);
+      tmem_ld_x16(base + (uint32_t)(2 * Npad), vx);
+      if (row < M) {
+        float* yrow = Y + (size_t)row * N + col;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (col + j < N) yrow[j] = (__uint_as_float(v0[j]) + __uint_as_float(vx[j])) + __uint_as_float(v1[j]);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (failed && tid == 0) atomicOr(status, DEV_ERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, tmem_cols);
+}
+
+// ---------------------------------------------------------------------------
+// operand prep: B^T split, [Npad][Kpad], zero padded
+// ---------------------------------------------------------------------------
+__global__ void prep_b_kernel(const double* __restrict__ G, int K, int N, int Kpad, int Npad,
+                              float* __restrict__ Bhi, float* __restrict__ Blo) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)Kpad * Npad;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e / Kpad), k = (int)(e % Kpad);
+    float h = 0.f, l = 0.f;
+    if (n < N && k < K) {
+      const double g = G[(int64_t)k * N + n];
+      h = tf32_rn((float)g);
+      l = tf32_rn((float)(g - (double)h));
+    }
+    Bhi[e] = h;
+    Blo[e] = l;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// swap the two fastest modes of a slab: out[i1 + d1 (i0 + d0 r)] = in[i0 + d0 (i1 + d1 r)]
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void transpose01_kernel(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int64_t rest) {
+  __shared__ T tile[32][33];
+  const int64_t r = blockIdx.z;
+  const int i0b = blockIdx.x * 32, i1b = blockIdx.y * 32;
+  const T* src = in + r * (int64_t)d0 * d1;
+  T* dst = out + r * (int64_t)d0 * d1;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int i1 = i1b + y, i0 = i0b + threadIdx.x;
+    if (i0 < d0 && i1 < d1) tile[y][threadIdx.x] = src[(int64_t)i1 * d0 + i0];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int i0 = i0b + y, i1 = i1b + threadIdx.x;
+    if (i0 < d0 && i1 < d1) dst[(int64_t)i0 * d1 + i1] = tile[threadIdx.x][y];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage 2 (SIMT): per (i_n, split) CTA, chunks of 32 combinations (i_lo, i_hi)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) stage2_kernel(Stage2Args a) {
+  // one warp per combination (i_lo, i_hi) at a time, warp-private staging in
+  // shared memory, outputs accumulated per lane; warps combined at the end in a
+  // fixed order (deterministic)
+  extern __shared__ float s2[];
+  const int Rk = a.Rk, Rk1 = a.Rk1, Rn = a.Rn, Rn1 = a.Rn1;
+  const int RRk = Rk * Rk1;
+  const int szA = Rn1 * Rk, szB = Rk1 * Rn, szT = Rk * Rn;
+  const int OUTP = Rn * Rn1;
+  const int per_warp = RRk + szA + szB + szT;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* sY = s2 + warp * per_warp;
+  float* sA = sY + RRk;
+  float* sB = sA + szA;
+  float* sT = sB + szB;
+  float* red = s2 + 8 * per_warp;       // 8 x OUTP
+  const uint32_t Jlo = (uint32_t)a.Jlo;
+  const int64_t in = blockIdx.x;
+  const int64_t ncomb = a.Jlo * a.Jhi;
+  const int64_t q0 = (int64_t)blockIdx.y * a.per, q1 = min(ncomb, q0 + a.per);
+  constexpr int MAXU = 8;               // OUTP <= 256 outputs: 8 per lane
+  float acc[MAXU];
+#pragma unroll
+  for (int u = 0; u < MAXU; ++u) acc[u] = 0.f;
+  for (int64_t q = q0 + warp; q < q1; q += 8) {
+    const uint32_t qq = (uint32_t)q;
+    const uint32_t ilo = qq % Jlo, ihi = qq / Jlo;
+    const int64_t m = (int64_t)ilo + a.Jlo * (in + a.dn * (int64_t)ihi);
+    const float* yrow = a.Y + m * RRk;
+    for (int x = lane; x < RRk; x += 32) sY[x] = yrow[x];
+    if (a.TA) {
+      const float* t = a.TA + (int64_t)ihi * szA;
+      for (int x = lane; x < szA; x += 32) sA[x] = t[x];
+    }
+    if (a.TB) {
+      const float* t = a.TB + (int64_t)(a.k == 0 ? ilo : ihi) * szB;
+      for (int x = lane; x < szB; x += 32) sB[x] = t[x];
+    }
+    __syncwarp();
+    const float* T1 = sY;      // T1[c][aa] = Y[c + Rk aa] when B is the identity
+    int t1_ld_c = 1, t1_ld_a = Rk;
+    if (a.TB) {
+      for (int x = lane; x < szT; x += 32) {
+        const int c = x / Rn, aa = x - c * Rn;
+        float v = 0.f;
+        for (int d = 0; d < Rk1; ++d) v = fmaf(sY[c + Rk * d], sB[d + Rk1 * aa], v);
+        sT[x] = v;
+      }
+      __syncwarp();
+      T1 = sT;
+      t1_ld_c = Rn;
+      t1_ld_a = 1;
+    }
+#pragma unroll
+    for (int u = 0; u < MAXU; ++u) {
+      const int o = lane + 32 * u;
+      if (o >= OUTP) break;
+      const int ob = o / Rn, oa = o - ob * Rn;
+      if (a.TA) {
+        float v = acc[u];
+        for (int c = 0; c < Rk; ++c) v = fmaf(sA[ob + Rn1 * c], T1[c * t1_ld_c + oa * t1_ld_a], v);
+        acc[u] = v;
+      } else {
+        acc[u] += T1[ob * t1_ld_c + oa * t1_ld_a];
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int u = 0; u < MAXU; ++u) {
+    const int o = lane + 32 * u;
+    if (o < OUTP) red[warp * OUTP + o] = acc[u];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < OUTP; o += blockDim.x) {
+    float sum = 0.f;
+    for (int w = 0; w < 8; ++w) sum += red[w * OUTP + o];
+    a.partial[((int64_t)blockIdx.y * a.dn + in) * OUTP + o] = sum;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tensor maps (driver entry point resolved once through the runtime)
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool tc_supported(int K, int xtype, const void* base) {
+  const int es = xtype == XT_BF16 ? 2 : 4;
+  if (xtype != XT_BF16 && xtype != XT_F32) return false;
+  if (((uintptr_t)base & 15) != 0) return false;
+  if (((int64_t)K * es) % 16 != 0) return false;
+  return encode_fn() != nullptr;
+}
+
+size_t stage1_smem_bytes(int Npad) { return 1024 + 32768 + 2 * (size_t)Npad * 128 + 16384 + 64; }
+
+cudaError_t launch_prep_b(const double* G, int K, int N, int Kpad, int Npad, float* Bhi, float* Blo,
+                          cudaStream_t s) {
+  const int64_t total = (int64_t)Kpad * Npad;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 1024));
+  prep_b_kernel<<<blocks, 256, 0, s>>>(G, K, N, Kpad, Npad, Bhi, Blo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose01(const void* in, void* out, int xtype, int d0, int d1, int64_t rest,
+                               cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div_i(d0, 32), (unsigned)ceil_div_i(d1, 32), (unsigned)rest);
+  dim3 block(32, 8);
+  if (rest > 65535) return cudaErrorInvalidValue;
+  if (xtype == XT_BF16)
+    transpose01_kernel<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, d0, d1, rest);
+  else
+    transpose01_kernel<float><<<grid, block, 0, s>>>((const float*)in, (float*)out, d0, d1, rest);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage1_tc(const void* Xa, int xtype, int64_t M, int K, const float* Bhi, const float* Blo,
+                             int Kpad, int N, int Npad, float* Y, int* status, cudaStream_t s) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tm;
+  const int es = xtype == XT_BF16 ? 2 : 4;
+  cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)M};
+  cuuint64_t gstride[1] = {(cuuint64_t)K * es};
+  cuuint32_t box[2] = {32, 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&tm, xtype == XT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<void*>(Xa), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  uint32_t cols = 32;
+  while ((int)cols < 3 * Npad) cols <<= 1;
+  if (cols > 512) return cudaErrorInvalidValue;
+  const int nch = Kpad / 32;
+  const size_t smp = 1024 + (size_t)2 * nch * Npad * 128 + (size_t)4 * nch * 16384 + 64;
+  if (smp <= 200 * 1024) {
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (M + 127) / 128;
+    const unsigned gridp = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, sms));
+    if (xtype == XT_BF16) {
+      cudaError_t e = cudaFuncSetAttribute(stage1_tc_persist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+      if (e != cudaSuccess) return e;
+      stage1_tc_persist_kernel<true><<<gridp, 128, smp, s>>>(tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+    } else {
+      cudaError_t e = cudaFuncSetAttribute(stage1_tc_persist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+      if (e != cudaSuccess) return e;
+      stage1_tc_persist_kernel<false><<<gridp, 128, smp, s>>>(tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+    }
+    return cudaGetLastError();
+  }
+  const size_t sm = stage1_smem_bytes(Npad);
+  const unsigned grid = (unsigned)((M + 127) / 128);
+  if (xtype == XT_BF16) {
+    cudaError_t e = cudaFuncSetAttribute(stage1_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    stage1_tc_kernel<true><<<grid, 128, sm, s>>>(tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(stage1_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    stage1_tc_kernel<false><<<grid, 128, sm, s>>>(tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+  }
+  return cudaGetLastError();
+}
+
+int stage2_plan_splits(int64_t dn, int64_t ncomb, int64_t* per) {
+  int64_t splits = std::max<int64_t>(1, (2 * 152 + dn - 1) / dn);
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, ncomb / 128));
+  int64_t p = (ncomb + splits - 1) / splits;
+  *per = std::max<int64_t>(1, p);
+  return (int)((ncomb + *per - 1) / *per);
+}
+
+cudaError_t launch_stage2(const Stage2Args& a, cudaStream_t s) {
+  const int RRk = a.Rk * a.Rk1;
+  const int OUTP = a.Rn * a.Rn1;
+  if (OUTP > 256 || a.Jlo * a.Jhi >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  const size_t sm = sizeof(float) * ((size_t)8 * (RRk + a.Rn1 * a.Rk + a.Rk1 * a.Rn + a.Rk * a.Rn) + (size_t)8 * OUTP);
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(stage2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)a.dn, (unsigned)a.splits);
+  stage2_kernel<<<grid, 256, sm, s>>>(a);
+  return cudaGetLastError();
+}

@@ -57,8 +57,8 @@ cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, in
                           int perm_Ra, int perm_Rb, const double* base, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
-// Cholesky: Q = L L^T (one CTA, FP64, shared memory), pivot check -> status.
-// Solve rows: out_row = p_row Q^{-1}; leverage mode: lev[r] = ||L^{-1} p_row||^2 / n.
+// FP64 LDL^T of an SPD matrix (one CTA, register-blocked): unit lower L and 1/d, pivot check ->
+// status.  Rows: out_row = p_row Q^{-1} by substitution; leverage mode: lev[r] = p Q^{-1} p^T / n.
 // ---------------------------------------------------------------------------
 cudaError_t launch_chol_factor(const double* Q, int n, double* L, double* invdiag, int* status,
                                double* pivot_ratio, cudaStream_t s);
@@ -66,6 +66,11 @@ cudaError_t launch_chol_solve(const double* L, const double* invdiag, int n, con
                               int64_t rows, double* out64, float* out32, double* lev,
                               cudaStream_t s);
 cudaError_t launch_fill(double* p, int64_t count, double v, cudaStream_t s);
+// FP32 LDL^T factor of Q + FP32 row solves refined `iters` times with FP64 residuals
+// (two launches; L32 n x n, invd32 n)
+cudaError_t launch_solve_mixed(const double* Q, int n, const double* P, int64_t rows, int iters,
+                               float* L32, float* invd32, double* out64, float* out32, int* status,
+                               double* pivot_ratio, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // sketches
@@ -74,9 +79,10 @@ cudaError_t launch_draw_indices(int32_t* out, int64_t m, int64_t I, uint64_t see
                                 uint64_t tau, uint32_t stream_id, const double* p, cudaStream_t s);
 cudaError_t launch_signs(double* d, int64_t I, uint64_t seed, int k, uint64_t tau,
                          uint32_t stream_id, cudaStream_t s);
-// out[c][c'] = base + sum_s w_s Re(g_s[c] conj(g_s[c']))  (FP64 accumulate)
+// out[c][c'] = base + sum_s w_s Re(g_s[c] conj(g_s[c']))  (FP64 accumulate; sample splits
+// reduced in a fixed order; `part` holds 64 x RR x RR doubles)
 cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const double* w,
-                                 int64_t m, int RR, const double* base, double* out,
+                                 int64_t m, int RR, const double* base, double* out, double* part,
                                  cudaStream_t s);
 // unitary DFT with sign pre-multiply along mode `mode` of a tensor with dims[N]:
 // out(.., k, ..) = sum_i F(k, i) d_i in(.., i, ..),  F(k,i) = exp(-2 pi i k i / L) / sqrt(L)
@@ -112,3 +118,30 @@ cudaError_t launch_recon(const void* Lm, const void* Rm, int compute, int64_t ro
 cudaError_t launch_sum_blocks(const double* block_sums, int64_t nblocks, int width, double* out,
                               double scale, cudaStream_t s);
 int recon_blocks(int64_t rows, int64_t cols);
+
+// ---------------------------------------------------------------------------
+// tensor-core dense MTTKRP (k_tc.cu): stage 1 Y = X x_k G_k on tcgen05,
+// stage 2 contraction of Y with the chain tables of the other cores
+// ---------------------------------------------------------------------------
+struct Stage2Args {
+  const float* Y = nullptr;    // M x (R_k R_{k+1}), row m = i_lo + Jlo (i_n + dn i_hi)
+  const float* TA = nullptr;   // [i_hi][R_{n+1} x R_k]  (nullptr = identity)
+  const float* TB = nullptr;   // [i_lo (k = 0) or i_hi (k = 1)][R_{k+1} x R_n]  (nullptr = identity)
+  int Rk = 0, Rk1 = 0, Rn = 0, Rn1 = 0;
+  int k = 0;
+  int64_t dn = 0, Jlo = 1, Jhi = 1;
+  float* partial = nullptr;    // [splits][dn][R_n R_{n+1}]
+  int splits = 1;
+  int64_t per = 1;             // combinations per split
+};
+bool tc_supported(int K, int xtype, const void* base);
+size_t stage1_smem_bytes(int Npad);
+cudaError_t launch_prep_b(const double* G, int K, int N, int Kpad, int Npad, float* Bhi, float* Blo,
+                          cudaStream_t s);
+cudaError_t launch_transpose01(const void* in, void* out, int xtype, int d0, int d1, int64_t rest,
+                               cudaStream_t s);
+cudaError_t launch_stage1_tc(const void* Xa, int xtype, int64_t M, int K, const float* Bhi,
+                             const float* Blo, int Kpad, int N, int Npad, float* Y, int* status,
+                             cudaStream_t s);
+int stage2_plan_splits(int64_t dn, int64_t ncomb, int64_t* per);
+cudaError_t launch_stage2(const Stage2Args& a, cudaStream_t s);

@@ -64,7 +64,7 @@ def test_struct_layouts_match_c(built_lib, tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(str_options), offsetof(str_options, t_capacity),
          offsetof(str_options, init_tol), offsetof(str_options, m), offsetof(str_options, stream_id),
-         offsetof(str_options, profile));
+         offsetof(str_options, graphs));
   printf("%zu %zu %zu\n", sizeof(str_tensor), offsetof(str_tensor, dims), offsetof(str_tensor, on_host));
   printf("%zu %zu %zu\n", sizeof(str_stats), offsetof(str_stats, min_pivot_ratio), offsetof(str_stats, class_ms));
   return 0;
@@ -76,7 +76,7 @@ int main(void) {
                                                                       text=True).stdout.splitlines()]
     O, T, S = built_lib.StrOptions, built_lib.StrTensor, built_lib.StrStats
     assert vals[0] == [ctypes.sizeof(O), O.t_capacity.offset, O.init_tol.offset, O.m.offset,
-                       O.stream_id.offset, O.profile.offset]
+                       O.stream_id.offset, O.graphs.offset]
     assert vals[1] == [ctypes.sizeof(T), T.dims.offset, T.on_host.offset]
     assert vals[2] == [ctypes.sizeof(S), S.min_pivot_ratio.offset, S.class_ms.offset]
 

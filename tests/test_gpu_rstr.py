@@ -57,6 +57,13 @@ def test_rstr_fp64_order4_no_rescale(sketch):
     _run(sketch, (6, 5, 7), 12, (2, 2, 3, 2), 4, 4, m=70, rescale=0, stream_id=5)
 
 
+@pytest.mark.parametrize("compute,tol", [("f64", 1e-10), ("f32", 1e-5)])
+def test_ksrft_power_of_two_lengths(compute, tol):
+    """Every mode length a power of two: mixing, core mixing and unmixing all
+    take the radix-2 FFT route (the other KSRFT tests use the direct DFT)."""
+    _run("ksrft", (16, 32), 16, (2, 3, 2), 8, 4, m=120, compute=compute, tol=tol)
+
+
 @pytest.mark.parametrize("sketch", ["uniform", "leverage", "ksrft"])
 def test_rstr_bf16_slab_fp32(sketch):
     _run(sketch, (48, 40), 20, (3, 3, 3), 10, 5, m=200, compute="f32", slab="bf16", tol=1e-5)

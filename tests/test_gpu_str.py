@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _run(dims, T, ranks, t_init, t_new, compute="f64", sweeps=1, slab="f64", seed=0, tol=1e-10,
-         init=None, check_every=True):
+         init=None, check_every=True, path=0):
     import torch
     p = lib()
     G, X = problem(dims, T, ranks, seed)
@@ -19,7 +19,8 @@ def _run(dims, T, ranks, t_init, t_new, compute="f64", sweeps=1, slab="f64", see
         X = synth.to_bf16_values(X)
     tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[slab]
     init = init or perturbed_init(G, t_init, seed + 7)
-    ctx = p.str_init_cores(init, X0=dev(X[..., :t_init], tdt), compute=compute, sweeps=sweeps)
+    ctx = p.str_init_cores(init, X0=dev(X[..., :t_init], tdt), compute=compute, sweeps=sweeps,
+                           mttkrp_path=path)
     ref = ost.str_init(X[..., :t_init], init)
     worst = 0.0
     t = t_init
@@ -63,12 +64,23 @@ def test_tile_tails_and_single_slice_fp64():
     _run((70, 9), 14, (3, 4, 2), 8, 1, seed=3, check_every=False)
 
 
-def test_fp32_compute():
-    _run((12, 10, 9), 16, (3, 3, 3, 3), 6, 5, compute="f32", slab="f32", sweeps=2, seed=4, tol=1e-5)
+@pytest.mark.parametrize("path", [0, 1])
+def test_fp32_compute(path):
+    _run((12, 10, 9), 16, (3, 3, 3, 3), 6, 5, compute="f32", slab="f32", sweeps=2, seed=4, tol=1e-5, path=path)
 
 
-def test_bf16_slab_fp32_compute():
-    _run((40, 36), 30, (4, 4, 4), 10, 5, compute="f32", slab="bf16", seed=5, tol=1e-5)
+@pytest.mark.parametrize("path", [0, 1])
+def test_bf16_slab_fp32_compute(path):
+    _run((40, 36), 30, (4, 4, 4), 10, 5, compute="f32", slab="bf16", seed=5, tol=1e-5, path=path)
+
+
+@pytest.mark.parametrize("slab", ["f32", "bf16"])
+def test_tensor_core_path_every_mode(slab):
+    """Dims that are multiples of 8 send every mode through the tcgen05 stage
+    (mode 1 via the slab with its two fastest modes swapped); 128-row tiles end
+    ragged; unequal ranks give padded N."""
+    _run((16, 24, 8), 20, (3, 2, 4, 3), 8, 6, compute="f32", slab=slab, sweeps=2, seed=9, tol=1e-5)
+    _run((64, 40), 23, (5, 4, 6), 7, 8, compute="f32", slab=slab, seed=10, tol=1e-5)
 
 
 def test_host_slab_matches_device_slab():
