@@ -120,6 +120,11 @@ cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, in
 // updates its entries: one barrier per pivot.  After n sweeps the matrix holds
 // -Q^{-1}.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 template <typename T, int B>
 __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __restrict__ Q, int n,
                                                             T* __restrict__ W, int* status,
@@ -149,43 +154,53 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
   }
   __syncthreads();
   const T tol = s_tol;
-  for (int k = 0; k < n; ++k) {
-    const int par = k & 1, kb = k >> 4, kr = k & 15;
-    if (tx == kr) {
+  // the pivot loop is unrolled so that the block index kb and the lane index kr
+  // of every pivot are compile-time constants: the owners' selections become
+  // predicated moves instead of runtime-indexed register accesses
 #pragma unroll
-      for (int i = 0; i < B; ++i) {
-        const int r = ty + 16 * i;
+  for (int kb = 0; kb < B; ++kb) {
 #pragma unroll
-        for (int j = 0; j < B; ++j)
-          if (j == kb && r < n) col[par][r] = a[i][j];
+    for (int kr = 0; kr < 16; ++kr) {
+      const int k = kb * 16 + kr;
+      if (k >= n) break;
+      const int par = k & 1;
+      // padded rows hold zeros, so the owners publish every row of the column
+      if (tx == kr) {
+#pragma unroll
+        for (int i = 0; i < B; ++i) col[par][ty + 16 * i] = a[i][kb];
       }
-    }
-    __syncthreads();
-    T piv = col[par][k];
-    const bool bad = !(piv > tol);
-    if (bad) piv = (T)1;
-    const T rcp = (T)1 / piv;
-    if (tid == 0) {
-      if (bad) s_bad = 1;
-      else if (qd[k] > (T)0 && piv * rcp * rcp * qd[k] > (T)0) {
-        const T ratio = piv / qd[k];
-        s_ratio = ratio < s_ratio ? ratio : s_ratio;
+      __syncthreads();
+      T piv = col[par][k];
+      const bool bad = !(piv > tol);
+      if (bad) piv = (T)1;
+      const T rcp = recip(piv);
+      if (tid == 0) {
+        if (bad) s_bad = 1;
+        else if (qd[k] > (T)0) {
+          const T ratio = piv / qd[k];
+          s_ratio = ratio < s_ratio ? ratio : s_ratio;
+        }
       }
-    }
+      // generic update a_ij -= a_ik a_kj / a_kk for every owned entry, then the
+      // owners of row k / column k overwrite theirs (row k and column k scale
+      // by 1/a_kk, the pivot becomes -1/a_kk)
+      T cir[B], cj[B];
 #pragma unroll
-    for (int i = 0; i < B; ++i) {
-      const int r = ty + 16 * i;
-      if (r >= n) continue;
-      const T ci = col[par][r];
+      for (int i = 0; i < B; ++i) cir[i] = col[par][ty + 16 * i] * rcp;
 #pragma unroll
-      for (int j = 0; j < B; ++j) {
-        const int c = tx + 16 * j;
-        if (c >= n) continue;
-        const T cj = col[par][c];
-        if (r == k && c == k) a[i][j] = -rcp;
-        else if (r == k) a[i][j] = cj * rcp;
-        else if (c == k) a[i][j] = ci * rcp;
-        else a[i][j] -= ci * cj * rcp;
+      for (int j = 0; j < B; ++j) cj[j] = col[par][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int j = 0; j < B; ++j) a[i][j] = fma_t(-cir[i], cj[j], a[i][j]);
+      if (ty == kr) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) a[kb][j] = cj[j] * rcp;
+      }
+      if (tx == kr) {
+#pragma unroll
+        for (int i = 0; i < B; ++i) a[i][kb] = cir[i];
+        if (ty == kr) a[kb][kb] = -rcp;
       }
     }
   }
@@ -325,8 +340,9 @@ __global__ void __launch_bounds__(128) chol_solve_kernel(const double* __restric
   double* inv = L + n * ld;             // n
   double* ys = inv + n;                 // 4 warps x n
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < n * n; e += blockDim.x) L[(e / n) * ld + (e % n)] = Lg[e];
-  for (int e = tid; e < n; e += blockDim.x) inv[e] = invdiag[e];
+  for (int e = tid; e < n * n; e += blockDim.x) cp_async8(&L[(e / n) * ld + (e % n)], &Lg[e]);
+  for (int e = tid; e < n; e += blockDim.x) cp_async8(&inv[e], &invdiag[e]);
+  cp_async_wait_all();
   __syncthreads();
   double* y = ys + warp * n;
   for (int64_t r = (int64_t)blockIdx.x * 4 + warp; r < rows; r += (int64_t)gridDim.x * 4) {
@@ -377,56 +393,66 @@ cudaError_t launch_chol_solve(const double* L, const double* invdiag, int n, con
 // per row g = p W32 followed by `iters` refinement steps
 // r = p - g Q (FP64, Q symmetric), g += r W32.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(64) solve_refine_kernel(const float* __restrict__ Wg,
-                                                          const double* __restrict__ Q, int n,
-                                                          const double* __restrict__ P, int64_t rows,
-                                                          int iters, double* out64, float* out32) {
+__global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restrict__ Wg,
+                                                           const double* __restrict__ Qg, int n,
+                                                           const double* __restrict__ P, int64_t rows,
+                                                           int iters, int q_in_smem, double* out64,
+                                                           float* out32) {
+  // one row of P per CTA at a time, one thread per column of the solution
   extern __shared__ unsigned char smr[];
   float* Wm = (float*)smr;                                                    // n x n
-  double* vs = (double*)(((uintptr_t)(Wm + n * n) + 7) & ~(uintptr_t)7);     // 2 warps x 2 x n
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < n * n; e += blockDim.x) Wm[e] = Wg[e];
+  double* Qs = (double*)(((uintptr_t)(Wm + n * n) + 15) & ~(uintptr_t)15);    // n x n (optional)
+  double* gs = Qs + (q_in_smem ? n * n : 0);                                  // n: current solution
+  float* vf = (float*)(gs + n);                                               // n: right-hand side (FP32)
+  const int tid = threadIdx.x;
+  for (int e = tid; e < n * n; e += blockDim.x) cp_async4(&Wm[e], &Wg[e]);
+  if (q_in_smem)
+    for (int e = tid; e < n * n; e += blockDim.x) cp_async8(&Qs[e], &Qg[e]);
+  cp_async_wait_all();
   __syncthreads();
-  double* v = vs + warp * 2 * n;      // right-hand side of the current product
-  double* g = v + n;                  // solution
-  for (int64_t r = (int64_t)blockIdx.x * 2 + warp; r < rows; r += (int64_t)gridDim.x * 2) {
-    const double* p = P + r * n;
-    for (int j = lane; j < n; j += 32) { v[j] = p[j]; g[j] = 0.0; }
-    __syncwarp();
+  const double* Q = q_in_smem ? Qs : Qg;
+  const int c = tid;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double pc = c < n ? P[r * n + c] : 0.0;
+    if (c < n) vf[c] = (float)pc;
+    double g = 0.0;
+    __syncthreads();
     for (int it = 0; it <= iters; ++it) {
       // g += v W32   (v = p on the first pass, then the FP64 residual)
-      for (int c = lane; c < n; c += 32) {
-        float a0 = 0.f, a1 = 0.f;
-        int cp = 0;
-        for (; cp + 1 < n; cp += 2) {
-          a0 = fmaf((float)v[cp], Wm[cp * n + c], a0);
-          a1 = fmaf((float)v[cp + 1], Wm[(cp + 1) * n + c], a1);
+      if (c < n) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int k = 0;
+        for (; k + 3 < n; k += 4) {
+          a0 = fmaf(vf[k], Wm[k * n + c], a0);
+          a1 = fmaf(vf[k + 1], Wm[(k + 1) * n + c], a1);
+          a2 = fmaf(vf[k + 2], Wm[(k + 2) * n + c], a2);
+          a3 = fmaf(vf[k + 3], Wm[(k + 3) * n + c], a3);
         }
-        if (cp < n) a0 = fmaf((float)v[cp], Wm[cp * n + c], a0);
-        g[c] += (double)(a0 + a1);
+        for (; k < n; ++k) a0 = fmaf(vf[k], Wm[k * n + c], a0);
+        g += (double)((a0 + a1) + (a2 + a3));
+        gs[c] = g;
       }
-      __syncwarp();
+      __syncthreads();
       if (it == iters) break;
-      // v = p - g Q in FP64
-      for (int c = lane; c < n; c += 32) {
-        double acc[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = 0.0;
-        int cp = 0;
-        for (; cp + 8 <= n; cp += 8) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) acc[u] = fma(-g[cp + u], Q[(int64_t)(cp + u) * n + c], acc[u]);
+      // v = p - g Q in FP64 (Q symmetric)
+      if (c < n) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int k = 0;
+        for (; k + 3 < n; k += 4) {
+          a0 = fma(-gs[k], Q[(int64_t)k * n + c], a0);
+          a1 = fma(-gs[k + 1], Q[(int64_t)(k + 1) * n + c], a1);
+          a2 = fma(-gs[k + 2], Q[(int64_t)(k + 2) * n + c], a2);
+          a3 = fma(-gs[k + 3], Q[(int64_t)(k + 3) * n + c], a3);
         }
-        for (; cp < n; ++cp) acc[0] = fma(-g[cp], Q[(int64_t)cp * n + c], acc[0]);
-        v[c] = p[c] + (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
+        for (; k < n; ++k) a0 = fma(-gs[k], Q[(int64_t)k * n + c], a0);
+        vf[c] = (float)(pc + ((a0 + a1) + (a2 + a3)));
       }
-      __syncwarp();
+      __syncthreads();
     }
-    for (int j = lane; j < n; j += 32) {
-      if (out64) out64[r * n + j] = g[j];
-      if (out32) out32[r * n + j] = (float)g[j];
+    if (c < n) {
+      if (out64) out64[r * n + c] = g;
+      if (out32) out32[r * n + c] = (float)g;
     }
-    __syncwarp();
   }
 }
 
@@ -435,11 +461,14 @@ cudaError_t launch_solve_mixed(const double* Q, int n, const double* P, int64_t 
                                double* pivot_ratio, cudaStream_t s) {
   cudaError_t e = launch_sweep<float>(Q, n, W32, status, pivot_ratio, s);
   if (e != cudaSuccess || rows <= 0) return e;
-  const size_t sms = (size_t)n * n * sizeof(float) + 8 + 4 * (size_t)n * sizeof(double);
+  const size_t base = (size_t)n * n * sizeof(float) + 16 + (size_t)n * (sizeof(double) + sizeof(float));
+  const int q_in_smem = base + (size_t)n * n * sizeof(double) <= 200 * 1024 ? 1 : 0;
+  const size_t sms = base + (q_in_smem ? (size_t)n * n * sizeof(double) : 0);
   e = cudaFuncSetAttribute(solve_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((rows + 1) / 2, 152 * 4));
-  solve_refine_kernel<<<(unsigned)blocks, 64, sms, s>>>(W32, Q, n, P, rows, iters, out64, out32);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 4));
+  const int threads = ((n + 31) / 32) * 32;
+  solve_refine_kernel<<<(unsigned)blocks, threads, sms, s>>>(W32, Q, n, P, rows, iters, q_in_smem, out64, out32);
   return cudaGetLastError();
 }
 

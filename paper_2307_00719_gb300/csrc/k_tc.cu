@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_persist_kernel(
     }
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Npad >> 3) << 17) |
                          ((uint32_t)(128 >> 4) << 24);
-  uint32_t ph_tma[2] = {0, 0}, ph_mma = 0;
+  uint32_t ph_tma = 0, ph_mma = 0;   // ph_tma bit b: phase of raw buffer b
   bool failed = false;
   int it = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
@@ -328,8 +328,8 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_persist_kernel(
       for (int c = 0; c < nch; ++c)
         tma_load_2d(sRaw + ((size_t)(buf ^ 1) * nch + c) * 16384, &tmA, &bars[buf ^ 1], c * 32, tn * 128);
     }
-    const bool ok = mbar_wait(&bars[buf], ph_tma[buf], kWaitNs);
-    ph_tma[buf] ^= 1;
+    const bool ok = mbar_wait(&bars[buf], (ph_tma >> buf) & 1u, kWaitNs);
+    ph_tma ^= 1u << buf;
     if (__syncthreads_or(!ok)) { failed = true; break; }
     for (int c = 0; c < nch; ++c) {
       const unsigned char* raw = sRaw + ((size_t)buf * nch + c) * 16384;
@@ -441,87 +441,171 @@ __global__ void transpose01_kernel(const T* __restrict__ in, T* __restrict__ out
 }
 
 // ---------------------------------------------------------------------------
-// stage 2 (SIMT): per (i_n, split) CTA, chunks of 32 combinations (i_lo, i_hi)
+// stage 2 (SIMT).  Per combination q = i_lo + Jlo i_hi the work is one small
+// product:
+//   B present:          Z = Y_q (R_k x R_{k+1}) . B (R_{k+1} x R_n)      [form YB]
+//   A present, B empty: Z = A(i_hi) (R_{n+1} x R_k) . Y_q (R_k x R_n)    [form AY]
+//   neither:            Z = Y_q                                           [form Y]
+// When A and B are both present (k = 0, Jlo > 1) A depends on i_hi only, so the
+// YB products are summed over each run of equal i_hi first and multiplied by
+// A(i_hi) once per run.
+// CTA per (i_n, split); the split's combinations are staged in chunks of CH
+// (Y rows + the per-combination table), double-buffered with cp.async; thread
+// (g, o) owns output o of the product and every G-th combination of a chunk.
+// Groups are combined in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) stage2_kernel(Stage2Args a) {
-  // one warp per combination (i_lo, i_hi) at a time, warp-private staging in
-  // shared memory, outputs accumulated per lane; warps combined at the end in a
-  // fixed order (deterministic)
-  extern __shared__ float s2[];
+constexpr int S2_CH = 32;       // combinations per chunk
+constexpr int S2_THREADS = 256;
+
+__device__ __forceinline__ void s2_issue(const Stage2Args& a, int form, int64_t in, int64_t qa, int nq,
+                                         int ystr, int tstr, int tsz, float* sY, float* sT, bool vec) {
+  // 8 threads per combination
+  const int t = threadIdx.x, j = t >> 3, sub = t & 7;
+  if (j >= nq) return;
+  const uint32_t q = (uint32_t)(qa + j);
+  const uint32_t Jlo = (uint32_t)a.Jlo;
+  const uint32_t ilo = q % Jlo, ihi = q / Jlo;
+  const int64_t m = (int64_t)ilo + a.Jlo * (in + a.dn * (int64_t)ihi);
+  const int RRk = a.Rk * a.Rk1;
+  const float* ysrc = a.Y + m * RRk;
+  float* ydst = sY + j * ystr;
+  const float* tsrc = nullptr;
+  if (form == 0) tsrc = a.TB + (int64_t)(a.k == 0 ? ilo : ihi) * tsz;
+  else if (form == 1) tsrc = a.TA + (int64_t)ihi * tsz;
+  float* tdst = sT + j * tstr;
+  if (vec) {
+    for (int x = sub * 4; x < RRk; x += 32) cp_async16(ydst + x, ysrc + x);
+    if (tsrc)
+      for (int x = sub * 4; x < tsz; x += 32) cp_async16(tdst + x, tsrc + x);
+  } else {
+    for (int x = sub; x < RRk; x += 8) cp_async4(ydst + x, ysrc + x);
+    if (tsrc)
+      for (int x = sub; x < tsz; x += 8) cp_async4(tdst + x, tsrc + x);
+  }
+}
+
+__global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
+  extern __shared__ __align__(16) float s2[];
   const int Rk = a.Rk, Rk1 = a.Rk1, Rn = a.Rn, Rn1 = a.Rn1;
   const int RRk = Rk * Rk1;
-  const int szA = Rn1 * Rk, szB = Rk1 * Rn, szT = Rk * Rn;
   const int OUTP = Rn * Rn1;
-  const int per_warp = RRk + szA + szB + szT;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* sY = s2 + warp * per_warp;
-  float* sA = sY + RRk;
-  float* sB = sA + szA;
-  float* sT = sB + szB;
-  float* red = s2 + 8 * per_warp;       // 8 x OUTP
-  const uint32_t Jlo = (uint32_t)a.Jlo;
+  // form and product shape: out index of product entry (x, y) = y + Rn x
+  const int form = a.TB ? 0 : (a.TA ? 1 : 2);
+  const bool segA = a.TA && a.TB;          // YB runs multiplied by A(i_hi)
+  int X, Yd, inner, tsz;
+  if (form == 0) { X = Rk; Yd = Rn; inner = Rk1; tsz = Rk1 * Rn; }
+  else if (form == 1) { X = Rn1; Yd = Rn; inner = Rk; tsz = Rn1 * Rk; }
+  else { X = Rk; Yd = Rn; inner = 1; tsz = 0; }
+  const int PO = X * Yd;                   // outputs of one product
+  const int G = max(1, S2_THREADS / PO);   // combination groups
+  const int ystr = (RRk + 3) & ~3, tstr = (tsz + 3) & ~3;
+  // buffer b: Y rows at s2 + b * S2_CH * ystr, tables at s2 + 2 S2_CH ystr + b S2_CH tstr
+  float* const sY0 = s2;
+  float* const sT0 = s2 + 2 * S2_CH * ystr;
+  float* sRed = s2 + 2 * S2_CH * (ystr + tstr);   // G x PO, then PO (segment sums)
+  const bool vec = (RRk % 4 == 0) && (tsz % 4 == 0) && ((((uintptr_t)a.Y) & 15) == 0) &&
+                   (form == 2 || ((((uintptr_t)(form == 0 ? a.TB : a.TA)) & 15) == 0));
+  const int tid = threadIdx.x;
+  const int g = tid / PO, o = tid - g * PO;
+  const bool act = g < G;
+  const int x = act ? o % X : 0, y = act ? o / X : 0;
   const int64_t in = blockIdx.x;
   const int64_t ncomb = a.Jlo * a.Jhi;
   const int64_t q0 = (int64_t)blockIdx.y * a.per, q1 = min(ncomb, q0 + a.per);
-  constexpr int MAXU = 8;               // OUTP <= 256 outputs: 8 per lane
-  float acc[MAXU];
-#pragma unroll
-  for (int u = 0; u < MAXU; ++u) acc[u] = 0.f;
-  for (int64_t q = q0 + warp; q < q1; q += 8) {
-    const uint32_t qq = (uint32_t)q;
-    const uint32_t ilo = qq % Jlo, ihi = qq / Jlo;
-    const int64_t m = (int64_t)ilo + a.Jlo * (in + a.dn * (int64_t)ihi);
-    const float* yrow = a.Y + m * RRk;
-    for (int x = lane; x < RRk; x += 32) sY[x] = yrow[x];
-    if (a.TA) {
-      const float* t = a.TA + (int64_t)ihi * szA;
-      for (int x = lane; x < szA; x += 32) sA[x] = t[x];
+  float acc = 0.f;      // product sums (per group)
+  float outv = 0.f;     // A-multiplied segment sums (threads tid < OUTP)
+  // chunk boundaries: never cross an i_hi run when segA
+  auto chunk_end = [&](int64_t qa) {
+    int64_t e = min(q1, qa + S2_CH);
+    if (segA) e = min(e, (qa / a.Jlo + 1) * a.Jlo);
+    return e;
+  };
+  int64_t qa = q0;
+  if (qa < q1) {
+    s2_issue(a, form, in, qa, (int)(chunk_end(qa) - qa), ystr, tstr, tsz, sY0, sT0, vec);
+  }
+  cp_async_commit();
+  int buf = 0;
+  while (qa < q1) {
+    const int64_t qe = chunk_end(qa);
+    const int nq = (int)(qe - qa);
+    const int64_t qn = qe;
+    if (qn < q1) {
+      s2_issue(a, form, in, qn, (int)(chunk_end(qn) - qn), ystr, tstr, tsz, sY0 + (buf ^ 1) * S2_CH * ystr,
+               sT0 + (buf ^ 1) * S2_CH * tstr, vec);
     }
-    if (a.TB) {
-      const float* t = a.TB + (int64_t)(a.k == 0 ? ilo : ihi) * szB;
-      for (int x = lane; x < szB; x += 32) sB[x] = t[x];
-    }
-    __syncwarp();
-    const float* T1 = sY;      // T1[c][aa] = Y[c + Rk aa] when B is the identity
-    int t1_ld_c = 1, t1_ld_a = Rk;
-    if (a.TB) {
-      for (int x = lane; x < szT; x += 32) {
-        const int c = x / Rn, aa = x - c * Rn;
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+    if (act) {
+      const float* Yb = sY0 + buf * S2_CH * ystr;
+      const float* Tb = sT0 + buf * S2_CH * tstr;
+      for (int j = g; j < nq; j += G) {
+        const float* yq = Yb + j * ystr;
+        const float* tq = Tb + j * tstr;
         float v = 0.f;
-        for (int d = 0; d < Rk1; ++d) v = fmaf(sY[c + Rk * d], sB[d + Rk1 * aa], v);
-        sT[x] = v;
-      }
-      __syncwarp();
-      T1 = sT;
-      t1_ld_c = Rn;
-      t1_ld_a = 1;
-    }
-#pragma unroll
-    for (int u = 0; u < MAXU; ++u) {
-      const int o = lane + 32 * u;
-      if (o >= OUTP) break;
-      const int ob = o / Rn, oa = o - ob * Rn;
-      if (a.TA) {
-        float v = acc[u];
-        for (int c = 0; c < Rk; ++c) v = fmaf(sA[ob + Rn1 * c], T1[c * t1_ld_c + oa * t1_ld_a], v);
-        acc[u] = v;
-      } else {
-        acc[u] += T1[ob * t1_ld_c + oa * t1_ld_a];
+        if (form == 0) {
+          for (int e = 0; e < inner; ++e) v = fmaf(yq[x + Rk * e], tq[e + Rk1 * y], v);
+        } else if (form == 1) {
+          for (int e = 0; e < inner; ++e) v = fmaf(tq[x + Rn1 * e], yq[e + Rk * y], v);
+        } else {
+          v = yq[x + Rk * y];
+        }
+        acc += v;
       }
     }
-    __syncwarp();
+    __syncthreads();   // buffer `buf` is refilled by the next iteration's issue
+    buf ^= 1;
+    qa = qe;
+    const bool seg_end = segA && (qa >= q1 || (qa % a.Jlo) == 0);
+    if (seg_end) {
+      // S = sum over groups (fixed order), then out += A(i_hi) S
+      if (act) sRed[g * PO + o] = acc;
+      acc = 0.f;
+      __syncthreads();
+      float* sS = sRed + G * PO;
+      for (int e = tid; e < PO; e += S2_THREADS) {
+        float v = 0.f;
+        for (int gg = 0; gg < G; ++gg) v += sRed[gg * PO + e];
+        sS[e] = v;
+      }
+      __syncthreads();
+      const int64_t ihi = (qa - 1) / a.Jlo;
+      const float* A = a.TA + ihi * (int64_t)(Rn1 * Rk);
+      for (int e = tid; e < OUTP; e += S2_THREADS) {
+        const int ob = e / Rn, oa = e - ob * Rn;
+        float v = 0.f;
+        for (int c = 0; c < Rk; ++c) v = fmaf(A[ob + Rn1 * c], sS[c + Rk * oa], v);
+        outv += v;
+      }
+      __syncthreads();
+    }
   }
-#pragma unroll
-  for (int u = 0; u < MAXU; ++u) {
-    const int o = lane + 32 * u;
-    if (o < OUTP) red[warp * OUTP + o] = acc[u];
+  cp_async_wait_0();
+  float* dst = a.partial + ((int64_t)blockIdx.y * a.dn + in) * OUTP;
+  if (segA) {
+    for (int e = tid; e < OUTP; e += S2_THREADS) dst[e] = outv;   // tid < OUTP <= 256: one each
+    return;
   }
+  if (act) sRed[g * PO + o] = acc;
   __syncthreads();
-  for (int o = threadIdx.x; o < OUTP; o += blockDim.x) {
-    float sum = 0.f;
-    for (int w = 0; w < 8; ++w) sum += red[w * OUTP + o];
-    a.partial[((int64_t)blockIdx.y * a.dn + in) * OUTP + o] = sum;
+  for (int e = tid; e < PO; e += S2_THREADS) {
+    float v = 0.f;
+    for (int gg = 0; gg < G; ++gg) v += sRed[gg * PO + e];
+    const int xx = e % X, yy = e / X;
+    dst[yy + Rn * xx] = v;
   }
+}
+
+size_t stage2_smem_bytes(const Stage2Args& a) {
+  const int RRk = a.Rk * a.Rk1;
+  int tsz = 0, PO = 0;
+  if (a.TB) { tsz = a.Rk1 * a.Rn; PO = a.Rk * a.Rn; }
+  else if (a.TA) { tsz = a.Rn1 * a.Rk; PO = a.Rn1 * a.Rn; }
+  else { PO = a.Rk * a.Rn; }
+  const int G = std::max(1, S2_THREADS / PO);
+  const int ystr = (RRk + 3) & ~3, tstr = (tsz + 3) & ~3;
+  return sizeof(float) * ((size_t)2 * S2_CH * (ystr + tstr) + (size_t)G * PO + PO);
 }
 
 // ---------------------------------------------------------------------------
@@ -638,16 +722,17 @@ int stage2_plan_splits(int64_t dn, int64_t ncomb, int64_t* per) {
 }
 
 cudaError_t launch_stage2(const Stage2Args& a, cudaStream_t s) {
-  const int RRk = a.Rk * a.Rk1;
   const int OUTP = a.Rn * a.Rn1;
-  if (OUTP > 256 || a.Jlo * a.Jhi >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  const size_t sm = sizeof(float) * ((size_t)8 * (RRk + a.Rn1 * a.Rk + a.Rk1 * a.Rn + a.Rk * a.Rn) + (size_t)8 * OUTP);
+  if (OUTP > S2_THREADS || a.Rk * a.Rn > S2_THREADS || a.Rn1 * a.Rn > S2_THREADS ||
+      a.Jlo * a.Jhi >= ((int64_t)1 << 31))
+    return cudaErrorInvalidValue;
+  const size_t sm = stage2_smem_bytes(a);
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(stage2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)a.dn, (unsigned)a.splits);
-  stage2_kernel<<<grid, 256, sm, s>>>(a);
+  stage2_kernel<<<grid, S2_THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
