@@ -76,6 +76,9 @@ struct str_ctx {
   const double* y_core[2] = {nullptr, nullptr};
   uint64_t y_ver[2] = {0, 0};
   uint64_t core_ver[STR_MAXN] = {};   // bumped whenever a core is rewritten
+  // chain tables of several cores kept within a step (stage 2 of the MTTKRP)
+  struct Chain { int k0 = 0, k1 = -1; bool valid = false; uint64_t ver[STR_MAXN] = {}; const void* cores[STR_MAXN] = {}; DevBuf buf; };
+  Chain chains[4];
   // captured update graphs, keyed by buffer parity, slab shape and buffer generation
   struct Graph { int parity; int64_t tn; int xtype; uint64_t gen; cudaGraphExec_t exec; int64_t launches; };
   std::vector<Graph> graphs;
@@ -93,6 +96,14 @@ struct str_ctx {
   std::vector<cudaEvent_t> pool;
   int64_t prof_launch[STR_K_CLASSES] = {};
   double prof_ms[STR_K_CLASSES] = {};
+  // second stream for the Q-side branch of an update (created on first use)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // third stream: the ring prefix M of the next mode
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
+  bool side2_used = false;
+  DevBuf mbuf[2];
 
   int RR(int n) const { return R[n] * R[n + 1]; }
   int64_t m() const { return opt.m; }
@@ -134,6 +145,12 @@ cudaEvent_t ev_get(str_ctx* c) {
     if (_e != cudaSuccess) return from_cuda(_e, #expr);                \
   } while (0)
 #define LCH(ctx, expr) LCHK(ctx, STR_K_OTHER, expr)
+// LCHK on an explicitly named stream
+#define LCHKS(ctx, cls, strm, expr) \
+  do {                              \
+    cudaStream_t s = (strm);        \
+    LCHK(ctx, cls, expr);           \
+  } while (0)
 
 str_status dalloc(str_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
@@ -234,19 +251,113 @@ str_status ring_Q(str_ctx* c, int n, const double* ENew, const double* base, dou
   return STR_OK;
 }
 
-// solve out = P Q^{-1} (rows x n) by Cholesky; writes FP64 (and FP32 shadow)
-str_status solve_rows(str_ctx* c, const double* Qm, int n, const double* Pm, int64_t rows,
-                      double* out64, float* out32, cudaStream_t s) {
+// Q_n split as M_n E_{n-1}: M_n = E_{n+1} ... E_{n-2} (the N-2 factors before the
+// last, cyclic) does not involve the core updated just before mode n in a
+// sweep, so it can be formed ahead of time.  ring_prefix writes M_n into `out`
+// (N >= 4; for N = 3, M_n is E_{n+1} itself and *M points there).
+str_status ring_prefix(str_ctx* c, int n, const double* ENew, double* out, const double** M, cudaStream_t s) {
+  const int N = c->N;
+  auto Eptr = [&](int k) -> const double* { return k == N - 1 ? ENew : E_of(c, k); };
+  const int f0 = (n + 1) % N;
+  if (N == 3) { *M = Eptr(f0); return STR_OK; }
+  TRY(grow(c, c->ring0, (size_t)STR_MAXRR * STR_MAXRR * 8));
+  TRY(grow(c, c->ring1, (size_t)STR_MAXRR * STR_MAXRR * 8));
+  const double* A = Eptr(f0);
+  const int Mrows = c->R[f0] * c->R[f0];
+  int Kc = c->R[f0 + 1] * c->R[f0 + 1];
+  double* bufs[2] = {(double*)c->ring0.p, (double*)c->ring1.p};
+  int bi = 0;
+  for (int t = 1; t < N - 2; ++t) {
+    const int k = (n + 1 + t) % N;
+    const int Ncols = c->R[k + 1] * c->R[k + 1];
+    double* dst = (t == N - 3) ? out : bufs[bi];
+    LCHK(c, STR_K_GRAM, launch_gemm64(A, Eptr(k), dst, Mrows, Kc, Ncols, 0, 0, nullptr, s));
+    A = dst;
+    bi ^= 1;
+    Kc = Ncols;
+  }
+  *M = out;
+  return STR_OK;
+}
+
+// Q_n = base + perm(M_n E_{n-1})
+str_status ring_last(str_ctx* c, int n, const double* M, const double* ENew, const double* base, double* Qout,
+                     cudaStream_t s) {
+  const int N = c->N;
+  const int f0 = (n + 1) % N, kl = (n + N - 1) % N;
+  const double* El = kl == N - 1 ? ENew : E_of(c, kl);
+  LCHK(c, STR_K_GRAM, launch_gemm64(M, El, Qout, c->R[f0] * c->R[f0], c->R[kl] * c->R[kl],
+                                    c->R[kl + 1] * c->R[kl + 1], c->R[n], c->R[n + 1], base, s));
+  return STR_OK;
+}
+
+// solve out = P Q^{-1} (rows x n) in two parts: factor_q depends on Q only,
+// apply_q on the factor and P.  FP32 slab arithmetic: FP32 sweep inverse, then
+// one FP64-residual refinement step; FP64: LDL^T and substitution.  Writes FP64
+// (and the FP32 shadow).
+str_status factor_q(str_ctx* c, const double* Qm, int n, cudaStream_t s) {
   TRY(grow(c, c->lfac, (size_t)n * n * 8));
   TRY(grow(c, c->invd, (size_t)n * 8));
   if (c->compute == 1) {
-    // FP32 slab arithmetic: FP32 inverse, one FP64-residual refinement step
-    LCHK(c, STR_K_FACTOR, launch_solve_mixed(Qm, n, Pm, rows, 1, (float*)c->lfac.p, (float*)c->invd.p, out64,
-                                             out32, c->d_status, c->d_pivot, s));
-    return STR_OK;
+    LCHK(c, STR_K_FACTOR, launch_factor_mixed(Qm, n, (float*)c->lfac.p, c->d_status, c->d_pivot, s));
+  } else {
+    LCHK(c, STR_K_FACTOR, launch_chol_factor(Qm, n, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, c->d_pivot, s));
   }
-  LCHK(c, STR_K_FACTOR, launch_chol_factor(Qm, n, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, c->d_pivot, s));
-  LCHK(c, STR_K_SOLVE, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, n, Pm, rows, out64, out32, nullptr, s));
+  return STR_OK;
+}
+
+str_status apply_q(str_ctx* c, const double* Qm, int n, const double* Pm, int64_t rows, double* out64,
+                   float* out32, cudaStream_t s, const PartialSum* ps = nullptr) {
+  if (c->compute == 1) {
+    LCHK(c, STR_K_SOLVE, launch_apply_mixed((const float*)c->lfac.p, Qm, n, Pm, rows, 1, out64, out32,
+                                            ps && ps->part ? ps : nullptr, s));
+  } else {
+    LCHK(c, STR_K_SOLVE, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, n, Pm, rows, out64, out32, nullptr, s));
+  }
+  return STR_OK;
+}
+
+str_status solve_rows(str_ctx* c, const double* Qm, int n, const double* Pm, int64_t rows,
+                      double* out64, float* out32, cudaStream_t s) {
+  TRY(factor_q(c, Qm, n, s));
+  return apply_q(c, Qm, n, Pm, rows, out64, out32, s);
+}
+
+// second stream of the update: the Q-side chain (Gram of the last updated core,
+// ring product, factorisation) runs beside the MTTKRP; ordered by events, so a
+// captured update becomes a graph with two branches per mode
+str_status fork_side(str_ctx* c, cudaStream_t s) {
+  if (!c->side) {
+    STR_CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
+  STR_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+  STR_CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  return STR_OK;
+}
+
+str_status join_side(str_ctx* c, cudaStream_t s) {
+  STR_CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
+  STR_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
+  if (c->side2_used) {
+    STR_CUDA_TRY(cudaEventRecord(c->ev_join2, c->side2));
+    STR_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join2, 0));
+    c->side2_used = false;
+  }
+  return STR_OK;
+}
+
+// third stream: forms M for the next mode from the side stream's current point
+str_status fork_side2(str_ctx* c) {
+  if (!c->side2) {
+    STR_CUDA_TRY(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+    STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming));
+    STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
+  }
+  STR_CUDA_TRY(cudaEventRecord(c->ev_fork2, c->side));
+  STR_CUDA_TRY(cudaStreamWaitEvent(c->side2, c->ev_fork2, 0));
+  c->side2_used = true;
   return STR_OK;
 }
 
@@ -288,16 +399,17 @@ struct SlabView {
 };
 
 str_status mttkrp_tc(str_ctx* c, const SlabView& v, int n, const void* const* cores, const double* G64k,
-                     const double* base, double* out, cudaStream_t s, bool* used);
+                     const double* base, double* out, cudaStream_t s, bool* used, PartialSum* defer);
 
 str_status mttkrp_into(str_ctx* c, const SlabView& v, int n, const void* const* cores, bool sampled,
                        const int32_t* idxs, bool lev, const double* const* pk, double wscale,
                        bool cplx, const double* base, double* out, void* gs, double* ws,
-                       cudaStream_t s) {
+                       cudaStream_t s, PartialSum* defer = nullptr) {
+  if (defer) *defer = PartialSum();
   if (!sampled && !cplx && c->compute == 1 && c->opt.mttkrp_path == 0) {
     const int kc = (n == 0) ? 1 : 0;
     bool used = false;
-    TRY(mttkrp_tc(c, v, n, cores, c->G64[kc][buf_of(c, kc)], base, out, s, &used));
+    TRY(mttkrp_tc(c, v, n, cores, c->G64[kc][buf_of(c, kc)], base, out, s, &used, defer));
     if (used) return STR_OK;
   }
   MttkrpArgs a;
@@ -336,12 +448,47 @@ str_status mttkrp_into(str_ctx* c, const SlabView& v, int n, const void* const* 
 }
 
 
+// FP32 chain table of cores k0..k1 ([j][R_{k0} x R_{k1+1}], j over i_{k0}.. fastest
+// first).  One core is its own table (same layout).  Products of several cores
+// are kept for the rest of the step while none of their cores changes.
+str_status chain_table_c(str_ctx* c, const void* const* cores, const int64_t* dims, int k0, int k1,
+                         const float** out, cudaStream_t s) {
+  if (k0 == k1) { *out = (const float*)cores[k0]; return STR_OK; }
+  uint64_t ver[STR_MAXN] = {};
+  for (int k = k0; k <= k1; ++k) ver[k] = c->core_ver[k];
+  for (auto& e : c->chains) {
+    if (e.k0 == k0 && e.k1 == k1 && e.valid && std::equal(ver + k0, ver + k1 + 1, e.ver + k0) &&
+        std::equal(cores + k0, cores + k1 + 1, e.cores + k0)) {
+      *out = (const float*)e.buf.p;
+      return STR_OK;
+    }
+  }
+  str_ctx::Chain* slot = nullptr;
+  for (auto& e : c->chains) if (!e.valid) { slot = &e; break; }
+  if (!slot) slot = &c->chains[0];
+  int64_t J = 1;
+  for (int j = k0; j <= k1; ++j) J *= dims[j];
+  TRY(grow(c, slot->buf, (size_t)J * c->R[k0] * c->R[k1 + 1] * 4));
+  LCHK(c, STR_K_GRAM, launch_chain_table(cores, 1, c->R, c->N, dims, k0, k1, 0, 0, slot->buf.p, s));
+  slot->k0 = k0;
+  slot->k1 = k1;
+  slot->valid = true;
+  std::copy(ver, ver + STR_MAXN, slot->ver);
+  std::copy(cores, cores + c->N, slot->cores);
+  *out = (const float*)slot->buf.p;
+  return STR_OK;
+}
+
+void reset_chains(str_ctx* c) {
+  for (auto& e : c->chains) e.valid = false;
+}
+
 // Dense FP32-compute MTTKRP on the tensor cores (two stages, see k_tc.cu).
 // cores: FP32 cores as seen in the step (temporal = the slab's rows);
 // G64k: FP64 master of the contracted core k.  Returns false (and does
 // nothing) when the slab layout does not allow the tensor-core path.
 str_status mttkrp_tc(str_ctx* c, const SlabView& v, int n, const void* const* cores, const double* G64k,
-                     const double* base, double* out, cudaStream_t s, bool* used) {
+                     const double* base, double* out, cudaStream_t s, bool* used, PartialSum* defer) {
   *used = false;
   const int N = c->N;
   const int k = (n == 0) ? 1 : 0;
@@ -393,17 +540,11 @@ str_status mttkrp_tc(str_ctx* c, const SlabView& v, int n, const void* const* co
   int64_t dims[STR_MAXN];
   for (int j = 0; j < N; ++j) dims[j] = v.dim[j];
   if (k == 0 && hi0 <= hi1) {   // A = G_{n+1} .. G_{N-1}
-    TRY(grow(c, c->tc_ta, (size_t)a.Jhi * a.Rn1 * Rk * 4));
-    LCHK(c, STR_K_GRAM, launch_chain_table(cores, 1, c->R, N, dims, hi0, hi1, 0, 0, c->tc_ta.p, s));
-    a.TA = (const float*)c->tc_ta.p;
+    TRY(chain_table_c(c, cores, dims, hi0, hi1, &a.TA, s));
   }
   const int b0 = (k == 0) ? lo0 : hi0, b1 = (k == 0) ? lo1 : hi1;
   if (b0 <= b1) {               // B = G_{k+1} .. G_{n-1}
-    int64_t J = 1;
-    for (int j = b0; j <= b1; ++j) J *= v.dim[j];
-    TRY(grow(c, c->tc_tb, (size_t)J * Rk1 * a.Rn * 4));
-    LCHK(c, STR_K_GRAM, launch_chain_table(cores, 1, c->R, N, dims, b0, b1, 0, 0, c->tc_tb.p, s));
-    a.TB = (const float*)c->tc_tb.p;
+    TRY(chain_table_c(c, cores, dims, b0, b1, &a.TB, s));
   }
   int64_t per = 1;
   a.splits = stage2_plan_splits(a.dn, a.Jlo * a.Jhi, &per);
@@ -412,7 +553,14 @@ str_status mttkrp_tc(str_ctx* c, const SlabView& v, int n, const void* const* co
   TRY(grow(c, c->tc_part, (size_t)a.splits * a.dn * OUTP * 4));
   a.partial = (float*)c->tc_part.p;
   LCHK(c, STR_K_CONTRACT, launch_stage2(a, s));
-  LCHK(c, STR_K_REDUCE, launch_reduce_partials(a.partial, 1, 0, a.splits, a.dn * OUTP, base, 1.0, out, s));
+  if (defer) {
+    defer->part = a.partial;
+    defer->splits = a.splits;
+    defer->base = base;
+    defer->pout = out;
+  } else {
+    LCHK(c, STR_K_REDUCE, launch_reduce_partials(a.partial, 1, 0, a.splits, a.dn * OUTP, base, 1.0, out, s));
+  }
   *used = true;
   return STR_OK;
 }
@@ -662,6 +810,7 @@ str_status str_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
   const void* cores[STR_MAXN];
   for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
   cores[N - 1] = temporal_rows_c(c, 0);
+  reset_chains(c);
   for (int n = 0; n < N - 1; ++n) {
     TRY(mttkrp_into(c, v, n, cores, false, nullptr, false, nullptr, 1.0, false, nullptr, c->P[n][c->cur[n]], nullptr, nullptr, s));
     TRY(ring_Q(c, n, (double*)c->enew.p, nullptr, c->Q[n][c->cur[n]], s));
@@ -713,31 +862,92 @@ str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
   TRY(grow(c, c->qtmp, (size_t)RRN * RRN * 8));
   double* gn64 = (double*)c->gnew64.p;
   const void* gn_c = c->compute == 2 ? (const void*)gn64 : c->gnew32.p;
+  // Per mode the update is two branches joined before the solve:
+  //   main: MTTKRP  P_n = X_[n] G^{!=n}_[2]  (+ the committed P_n)
+  //   side: Gram E of the core updated just before, ring product Q_n, factor of Q_n
+  // then G_n = P_n Q_n^{-1} on the main stream.
+  int last = -1;   // core whose Gram matrix is still to be formed (-1: none, N-1: temporal)
+  reset_chains(c);
+  // ring prefixes M (Q_n = M_n E_{n-1}): M of the next mode is formed on a third
+  // stream while the current mode factors; slot = mode parity
+  const int RRmax = STR_MAXRR;
+  if (N >= 4) {
+    TRY(grow(c, c->mbuf[0], (size_t)RRmax * RRmax * 8));
+    TRY(grow(c, c->mbuf[1], (size_t)RRmax * RRmax * 8));
+  }
+  bool have_M = false;           // M of the mode about to run is already formed
+  const int nmodes = c->opt.sweeps * N;
+  int step_i = 0;                // position in the mode sequence T, 0, 1, .., N-2, T, ..
+  auto mode_at = [&](int i) { return (i % N) == 0 ? N - 1 : (i % N) - 1; };
+  // side branch of mode n: Gram of the core updated last, M_n (unless formed
+  // ahead), Q_n = base + perm(M_n E_{n-1}), its factor; then M of the next mode
+  auto side_branch = [&](int n, const double* base, double* Qout, int RRn) -> str_status {
+    cudaStream_t s2 = c->side;
+    if (last == N - 1)
+      LCHKS(c, STR_K_GRAM, s2, launch_core_gram(gn64, tn, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s2));
+    else if (last >= 0)
+      LCHKS(c, STR_K_GRAM, s2, launch_core_gram(c->G64[last][1 - c->cur[last]], c->I[last], c->R[last],
+                                                c->R[last + 1], nullptr, c->E[last][1 - c->cur[last]], s2));
+    const double* enew = (const double*)c->enew.p;
+    const double* ENew = (n == N - 1) ? nullptr : enew;
+    if (N == 3 || (n == N - 1 && last < 0)) {
+      // first temporal mode of the step (E_new of this step not formed yet) or N = 3
+      TRY(ring_Q(c, n, ENew, base, Qout, s2));
+    } else {
+      const double* M = nullptr;
+      if (!have_M) TRY(ring_prefix(c, n, ENew, (double*)c->mbuf[n & 1].p, &M, s2));
+      else M = (const double*)c->mbuf[n & 1].p;
+      TRY(ring_last(c, n, M, enew, base, Qout, s2));
+    }
+    have_M = false;
+    if (N >= 4 && step_i + 1 < nmodes) {
+      // M of the next mode: needs every E but the one of the core updated now
+      const int nx = mode_at(step_i + 1);
+      TRY(fork_side2(c));
+      const double* Mx = nullptr;
+      TRY(ring_prefix(c, nx, enew, (double*)c->mbuf[nx & 1].p, &Mx, c->side2));
+      have_M = true;
+    }
+    TRY(factor_q(c, Qout, RRn, s2));
+    return STR_OK;
+  };
   for (int sw = 0; sw < c->opt.sweeps; ++sw) {
     // temporal mode: H^{!=N} ring, M_N = X_[N] G^{!=N}_[2], G_N^new = M_N H^{-1}
     const void* cores[STR_MAXN];
     for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
     cores[N - 1] = nullptr;
-    TRY(ring_Q(c, N - 1, nullptr, nullptr, (double*)c->qtmp.p, s));
-    TRY(mttkrp_into(c, v, N - 1, cores, false, nullptr, false, nullptr, 1.0, false, nullptr, (double*)c->mtmp.p, nullptr, nullptr, s));
-    TRY(solve_rows(c, (double*)c->qtmp.p, RRN, (double*)c->mtmp.p, tn, gn64,
-                   c->compute == 1 ? (float*)c->gnew32.p : nullptr, s));
-    LCHK(c, STR_K_GRAM, launch_core_gram(gn64, tn, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s));
+    TRY(fork_side(c, s));
+    TRY(side_branch(N - 1, nullptr, (double*)c->qtmp.p, RRN));
+    PartialSum ps;
+    TRY(mttkrp_into(c, v, N - 1, cores, false, nullptr, false, nullptr, 1.0, false, nullptr, (double*)c->mtmp.p, nullptr, nullptr, s, &ps));
+    TRY(join_side(c, s));
+    TRY(apply_q(c, (double*)c->qtmp.p, RRN, (double*)c->mtmp.p, tn, gn64,
+                c->compute == 1 ? (float*)c->gnew32.p : nullptr, s, &ps));
+    c->core_ver[N - 1]++;
+    last = N - 1;
+    ++step_i;
     // spatial modes in order (Gauss-Seidel)
     for (int n = 0; n < N - 1; ++n) {
       const int RR = c->RR(n);
       const int w = 1 - c->cur[n];
       for (int k = 0; k < N - 1; ++k) cores[k] = core_c(c, k);
       cores[N - 1] = gn_c;
-      TRY(mttkrp_into(c, v, n, cores, false, nullptr, false, nullptr, 1.0, false, c->P[n][c->cur[n]], c->P[n][w], nullptr, nullptr, s));
-      TRY(ring_Q(c, n, (double*)c->enew.p, c->Q[n][c->cur[n]], c->Q[n][w], s));
-      TRY(solve_rows(c, c->Q[n][w], RR, c->P[n][w], c->I[n], c->G64[n][w],
-                     c->compute == 1 ? c->G32[n][w] : nullptr, s));
-      LCHK(c, STR_K_GRAM, launch_core_gram(c->G64[n][w], c->I[n], c->R[n], c->R[n + 1], nullptr, c->E[n][w], s));
+      TRY(fork_side(c, s));
+      TRY(side_branch(n, c->Q[n][c->cur[n]], c->Q[n][w], RR));
+      TRY(mttkrp_into(c, v, n, cores, false, nullptr, false, nullptr, 1.0, false, c->P[n][c->cur[n]], c->P[n][w], nullptr, nullptr, s, &ps));
+      TRY(join_side(c, s));
+      TRY(apply_q(c, c->Q[n][w], RR, c->P[n][w], c->I[n], c->G64[n][w],
+                  c->compute == 1 ? c->G32[n][w] : nullptr, s, &ps));
       c->upd[n] = 1;
       c->core_ver[n]++;
+      last = n;
+      ++step_i;
     }
   }
+  // Gram matrix of the last core updated (kept with the committed state)
+  if (last >= 0 && last < N - 1)
+    LCHK(c, STR_K_GRAM, launch_core_gram(c->G64[last][1 - c->cur[last]], c->I[last], c->R[last], c->R[last + 1],
+                                         nullptr, c->E[last][1 - c->cur[last]], s));
   return STR_OK;
 }
 
@@ -1441,6 +1651,12 @@ void str_destroy(str_ctx* c) {
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& e : c->pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork2) cudaEventDestroy(c->ev_fork2);
+  if (c->ev_join2) cudaEventDestroy(c->ev_join2);
+  if (c->side2) cudaStreamDestroy(c->side2);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_sums) cudaFreeHost(c->h_sums);
   delete c;

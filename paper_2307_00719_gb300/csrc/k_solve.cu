@@ -131,8 +131,7 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
                                                             double* pivot_ratio) {
   __shared__ T col[2][16 * B];
   __shared__ T qd[16 * B];
-  __shared__ int s_bad;
-  __shared__ T s_ratio;
+  __shared__ T pivs[16 * B];   // pivot k as met (before any replacement)
   __shared__ T s_tol;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   T a[B][B];
@@ -145,21 +144,25 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
     }
   for (int k = tid; k < n; k += 256) qd[k] = (T)Q[(int64_t)k * n + k];
   __syncthreads();
-  if (tid == 0) {
+  if (tid < 32) {
     T mx = 0;
-    for (int k = 0; k < n; ++k) mx = mx > qd[k] ? mx : qd[k];
-    s_tol = (T)n * (T)(sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07) * mx;
-    s_bad = 0;
-    s_ratio = (T)1;
+    for (int k = tid; k < n; k += 32) mx = mx > qd[k] ? mx : qd[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const T o = __shfl_xor_sync(0xffffffffu, mx, off);
+      mx = mx > o ? mx : o;
+    }
+    if (tid == 0) s_tol = (T)n * (T)(sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07) * mx;
   }
   __syncthreads();
   const T tol = s_tol;
-  // the pivot loop is unrolled so that the block index kb and the lane index kr
-  // of every pivot are compile-time constants: the owners' selections become
-  // predicated moves instead of runtime-indexed register accesses
+  // the pivot loop is unrolled over the register block index kb only, so that
+  // the owners' selections a[.][kb] are static register accesses; the 16
+  // pivots inside a block stay a loop (the fully unrolled form does not fit the
+  // instruction cache and stalls on instruction fetch)
 #pragma unroll
   for (int kb = 0; kb < B; ++kb) {
-#pragma unroll
+#pragma unroll 1
     for (int kr = 0; kr < 16; ++kr) {
       const int k = kb * 16 + kr;
       if (k >= n) break;
@@ -171,16 +174,9 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
       }
       __syncthreads();
       T piv = col[par][k];
-      const bool bad = !(piv > tol);
-      if (bad) piv = (T)1;
+      if (tid == 0) pivs[k] = piv;
+      if (!(piv > tol)) piv = (T)1;   // recorded as singular after the loop
       const T rcp = recip(piv);
-      if (tid == 0) {
-        if (bad) s_bad = 1;
-        else if (qd[k] > (T)0) {
-          const T ratio = piv / qd[k];
-          s_ratio = ratio < s_ratio ? ratio : s_ratio;
-        }
-      }
       // generic update a_ij -= a_ik a_kj / a_kk for every owned entry, then the
       // owners of row k / column k overwrite theirs (row k and column k scale
       // by 1/a_kk, the pivot becomes -1/a_kk)
@@ -211,9 +207,29 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
       const int r = ty + 16 * i, c = tx + 16 * j;
       if (r < n && c < n) W[(int64_t)r * n + c] = -a[i][j];
     }
-  if (tid == 0) {
-    if (s_bad && status) atomicOr(status, DEV_ERR_SINGULAR);
-    if (pivot_ratio) *pivot_ratio = (double)s_ratio;
+  // singular pivots and the smallest pivot / diagonal ratio
+  __syncthreads();
+  if (tid < 32) {
+    int bad = 0;
+    T ratio = (T)1;
+    for (int k = tid; k < n; k += 32) {
+      const T p = pivs[k];
+      if (!(p > tol)) bad = 1;
+      else if (qd[k] > (T)0) {
+        const T r = p / qd[k];
+        ratio = r < ratio ? r : ratio;
+      }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const T o = __shfl_xor_sync(0xffffffffu, ratio, off);
+      ratio = o < ratio ? o : ratio;
+    }
+    if (tid == 0) {
+      if (bad && status) atomicOr(status, DEV_ERR_SINGULAR);
+      if (pivot_ratio) *pivot_ratio = (double)ratio;
+    }
   }
 }
 
@@ -397,7 +413,7 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
                                                            const double* __restrict__ Qg, int n,
                                                            const double* __restrict__ P, int64_t rows,
                                                            int iters, int q_in_smem, double* out64,
-                                                           float* out32) {
+                                                           float* out32, PartialSum ps) {
   // one row of P per CTA at a time, one thread per column of the solution
   extern __shared__ unsigned char smr[];
   float* Wm = (float*)smr;                                                    // n x n
@@ -413,7 +429,19 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
   const double* Q = q_in_smem ? Qs : Qg;
   const int c = tid;
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-    const double pc = c < n ? P[r * n + c] : 0.0;
+    double pc = 0.0;
+    if (c < n) {
+      if (ps.part) {
+        // P = base + sum of the split partials, in split order; stored, then solved
+        pc = ps.base ? ps.base[r * n + c] : 0.0;
+        double acc = 0.0;
+        for (int k = 0; k < ps.splits; ++k) acc += (double)ps.part[(int64_t)k * rows * n + r * n + c];
+        pc += acc;
+        ps.pout[r * n + c] = pc;
+      } else {
+        pc = P[r * n + c];
+      }
+    }
     if (c < n) vf[c] = (float)pc;
     double g = 0.0;
     __syncthreads();
@@ -456,20 +484,34 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
   }
 }
 
-cudaError_t launch_solve_mixed(const double* Q, int n, const double* P, int64_t rows, int iters,
-                               float* W32, float* /*unused*/, double* out64, float* out32, int* status,
-                               double* pivot_ratio, cudaStream_t s) {
-  cudaError_t e = launch_sweep<float>(Q, n, W32, status, pivot_ratio, s);
-  if (e != cudaSuccess || rows <= 0) return e;
+cudaError_t launch_factor_mixed(const double* Q, int n, float* W32, int* status, double* pivot_ratio,
+                                cudaStream_t s) {
+  return launch_sweep<float>(Q, n, W32, status, pivot_ratio, s);
+}
+
+cudaError_t launch_apply_mixed(const float* W32, const double* Q, int n, const double* P, int64_t rows,
+                               int iters, double* out64, float* out32, const PartialSum* ps, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (n < 1 || n > 160) return cudaErrorInvalidValue;
   const size_t base = (size_t)n * n * sizeof(float) + 16 + (size_t)n * (sizeof(double) + sizeof(float));
   const int q_in_smem = base + (size_t)n * n * sizeof(double) <= 200 * 1024 ? 1 : 0;
   const size_t sms = base + (q_in_smem ? (size_t)n * n * sizeof(double) : 0);
-  e = cudaFuncSetAttribute(solve_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+  cudaError_t e = cudaFuncSetAttribute(solve_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 4));
   const int threads = ((n + 31) / 32) * 32;
-  solve_refine_kernel<<<(unsigned)blocks, threads, sms, s>>>(W32, Q, n, P, rows, iters, q_in_smem, out64, out32);
+  PartialSum none;
+  solve_refine_kernel<<<(unsigned)blocks, threads, sms, s>>>(W32, Q, n, P, rows, iters, q_in_smem, out64, out32,
+                                                            ps ? *ps : none);
   return cudaGetLastError();
+}
+
+cudaError_t launch_solve_mixed(const double* Q, int n, const double* P, int64_t rows, int iters,
+                               float* W32, float* /*unused*/, double* out64, float* out32, int* status,
+                               double* pivot_ratio, cudaStream_t s) {
+  cudaError_t e = launch_factor_mixed(Q, n, W32, status, pivot_ratio, s);
+  if (e != cudaSuccess) return e;
+  return launch_apply_mixed(W32, Q, n, P, rows, iters, out64, out32, nullptr, s);
 }
 
 __global__ void fill_kernel(double* p, int64_t count, double v) {

@@ -484,6 +484,23 @@ __device__ __forceinline__ void s2_issue(const Stage2Args& a, int form, int64_t 
   }
 }
 
+// sum_e L[R e] M[e] for a compile-time R (multiple of 4); M is 16-byte aligned
+template <int R>
+__device__ __forceinline__ float s2_dot(const float* L, const float* M) {
+  float v = 0.f;
+#pragma unroll
+  for (int e = 0; e < R; e += 4) {
+    const float4 m = *(const float4*)(M + e);
+    v = fmaf(L[R * e], m.x, v);
+    v = fmaf(L[R * (e + 1)], m.y, v);
+    v = fmaf(L[R * (e + 2)], m.z, v);
+    v = fmaf(L[R * (e + 3)], m.w, v);
+  }
+  return v;
+}
+
+// RT > 0: all four ranks equal RT (compile-time strides); RT = 0: any ranks
+template <int RT>
 __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
   extern __shared__ __align__(16) float s2[];
   const int Rk = a.Rk, Rk1 = a.Rk1, Rn = a.Rn, Rn1 = a.Rn1;
@@ -540,18 +557,32 @@ __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
     if (act) {
       const float* Yb = sY0 + buf * S2_CH * ystr;
       const float* Tb = sT0 + buf * S2_CH * tstr;
-      for (int j = g; j < nq; j += G) {
-        const float* yq = Yb + j * ystr;
-        const float* tq = Tb + j * tstr;
-        float v = 0.f;
-        if (form == 0) {
-          for (int e = 0; e < inner; ++e) v = fmaf(yq[x + Rk * e], tq[e + Rk1 * y], v);
-        } else if (form == 1) {
-          for (int e = 0; e < inner; ++e) v = fmaf(tq[x + Rn1 * e], yq[e + Rk * y], v);
+      if (form == 2) {
+        for (int j = g; j < nq; j += G) acc += Yb[j * ystr + x + Rk * y];
+      } else {
+        // product entry (x, y) = sum_e L[x + X e] M[e + inner y]:
+        // form YB: L = Y_q, M = B;  form AY: L = A, M = Y_q
+        const int lstr = form == 0 ? ystr : tstr, mstr = form == 0 ? tstr : ystr;
+        const float* Lb = (form == 0 ? Yb : Tb) + x;
+        const float* Mb = (form == 0 ? Tb : Yb) + inner * y;
+        if constexpr (RT > 0) {
+          int j = g;
+          for (; j + G < nq; j += 2 * G) {
+            const float v0 = s2_dot<RT>(Lb + j * lstr, Mb + j * mstr);
+            const float v1 = s2_dot<RT>(Lb + (j + G) * lstr, Mb + (j + G) * mstr);
+            acc += v0;
+            acc += v1;
+          }
+          if (j < nq) acc += s2_dot<RT>(Lb + j * lstr, Mb + j * mstr);
         } else {
-          v = yq[x + Rk * y];
+          for (int j = g; j < nq; j += G) {
+            const float* lq = Lb + j * lstr;
+            const float* mq = Mb + j * mstr;
+            float v = 0.f;
+            for (int e = 0; e < inner; ++e) v = fmaf(lq[X * e], mq[e], v);
+            acc += v;
+          }
         }
-        acc += v;
       }
     }
     __syncthreads();   // buffer `buf` is refilled by the next iteration's issue
@@ -728,11 +759,14 @@ cudaError_t launch_stage2(const Stage2Args& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
   const size_t sm = stage2_smem_bytes(a);
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  const bool eq = a.Rk == a.Rk1 && a.Rk == a.Rn && a.Rk == a.Rn1;
+  const int rt = eq && (a.Rk == 4 || a.Rk == 8) ? a.Rk : 0;
+  auto kern = rt == 4 ? stage2_kernel<4> : rt == 8 ? stage2_kernel<8> : stage2_kernel<0>;
   if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(stage2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)a.dn, (unsigned)a.splits);
-  stage2_kernel<<<grid, S2_THREADS, sm, s>>>(a);
+  kern<<<grid, S2_THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }

@@ -68,6 +68,19 @@ cudaError_t launch_chol_solve(const double* L, const double* invdiag, int n, con
 cudaError_t launch_fill(double* p, int64_t count, double v, cudaStream_t s);
 // FP32 LDL^T factor of Q + FP32 row solves refined `iters` times with FP64 residuals
 // (two launches; L32 n x n, invd32 n)
+// right-hand side still in split partials: P = base + sum_k part[k] (part: splits x rows x n)
+struct PartialSum {
+  const float* part = nullptr;
+  int splits = 0;
+  const double* base = nullptr;   // may be null
+  double* pout = nullptr;         // where P is stored
+};
+// FP32 sweep inverse W32 = Q^{-1} (factor) and the refined solve out = P Q^{-1} (apply);
+// with ps, P is formed from the partials inside the apply kernel (and stored to ps->pout)
+cudaError_t launch_factor_mixed(const double* Q, int n, float* W32, int* status, double* pivot_ratio,
+                                cudaStream_t s);
+cudaError_t launch_apply_mixed(const float* W32, const double* Q, int n, const double* P, int64_t rows,
+                               int iters, double* out64, float* out32, const PartialSum* ps, cudaStream_t s);
 cudaError_t launch_solve_mixed(const double* Q, int n, const double* P, int64_t rows, int iters,
                                float* L32, float* invd32, double* out64, float* out32, int* status,
                                double* pivot_ratio, cudaStream_t s);

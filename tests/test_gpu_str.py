@@ -83,6 +83,13 @@ def test_tensor_core_path_every_mode(slab):
     _run((64, 40), 23, (5, 4, 6), 7, 8, compute="f32", slab=slab, seed=10, tol=1e-5)
 
 
+@pytest.mark.parametrize("R", [4, 8])
+def test_tensor_core_path_equal_ranks(R):
+    """Equal TR-ranks 4 and 8 take the stage-2 kernel specialised on the rank;
+    the temporal mode's combinations span several chunks and splits."""
+    _run((16, 24, 8), 21, (R, R, R, R), 9, 6, compute="f32", slab="f32", sweeps=2, seed=11, tol=1e-5)
+
+
 def test_host_slab_matches_device_slab():
     import torch
     p = lib()
