@@ -96,6 +96,37 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // ---------------------------------------------------------------------------
+// programmatic dependent launch.  Every kernel of the library is launched with
+// programmatic stream serialisation allowed, so it can be scheduled while the
+// previous kernel of its stream is still running, and starts with PDL_ENTRY:
+// wait until every prerequisite grid has completed and its writes are visible,
+// then allow the next kernel of the stream to be scheduled.  No kernel touches
+// global memory before the wait, so the ordering is the stream's own.
+// ---------------------------------------------------------------------------
+#define PDL_ENTRY()                                          \
+  do {                                                       \
+    asm volatile("griddepcontrol.wait;" ::: "memory");       \
+    asm volatile("griddepcontrol.launch_dependents;" :::);   \
+  } while (0)
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                   Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  // the legacy default stream keeps its plain serialisation
+  cfg.numAttrs = (s == nullptr || s == cudaStreamLegacy) ? 0 : 1;
+  return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
+// ---------------------------------------------------------------------------
 // host-side launch checking
 // ---------------------------------------------------------------------------
 #define STR_CUDA_TRY(expr)                                                   \

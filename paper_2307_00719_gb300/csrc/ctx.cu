@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -91,7 +93,7 @@ struct str_ctx {
   std::vector<void*> owned;
   size_t bytes = 0;
   // profiling: pending (class, start, end) event triples and the event pool
-  struct Ev { int cls; cudaEvent_t a, b; };
+  struct Ev { int cls; cudaEvent_t a, b; int strm; };
   std::vector<Ev> pending;
   std::vector<cudaEvent_t> pool;
   int64_t prof_launch[STR_K_CLASSES] = {};
@@ -140,7 +142,7 @@ cudaEvent_t ev_get(str_ctx* c) {
     if (_c->opt.profile) {                                             \
       _b = ev_get(_c);                                                 \
       cudaEventRecord(_b, s);                                          \
-      _c->pending.push_back({(cls), _a, _b});                          \
+      _c->pending.push_back({(cls), _a, _b, s == _c->side ? 1 : s == _c->side2 ? 2 : 0}); \
     }                                                                  \
     if (_e != cudaSuccess) return from_cuda(_e, #expr);                \
   } while (0)
@@ -1591,15 +1593,28 @@ str_status str_get_stats(const str_ctx* c, str_stats* stats) {
   if (cudaMemcpy(&piv, c->d_pivot, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return STR_ERR_CUDA;
   stats->min_pivot_ratio = piv;
   str_ctx* m = const_cast<str_ctx*>(c);
+  // optional launch timeline (profiling mode): STRTR_TIMELINE names a file that
+  // receives one line per timed launch: class, stream (0 caller, 1-2 side
+  // streams), start and end in ms from the first timed launch
+  const char* tl_path = std::getenv("STRTR_TIMELINE");
+  FILE* tl = (tl_path && !m->pending.empty()) ? std::fopen(tl_path, "a") : nullptr;
   for (auto& e : m->pending) {
     float ms = 0.f;
-    if (cudaEventSynchronize(e.b) != cudaSuccess || cudaEventElapsedTime(&ms, e.a, e.b) != cudaSuccess)
+    if (cudaEventSynchronize(e.b) != cudaSuccess || cudaEventElapsedTime(&ms, e.a, e.b) != cudaSuccess) {
+      if (tl) std::fclose(tl);
       return STR_ERR_CUDA;
+    }
+    if (tl) {
+      float t0 = 0.f;
+      cudaEventElapsedTime(&t0, m->pending.front().a, e.a);
+      std::fprintf(tl, "%d %d %.4f %.4f\n", e.cls, e.strm, t0, t0 + ms);
+    }
     m->prof_ms[e.cls] += ms;
     m->prof_launch[e.cls] += 1;
     m->pool.push_back(e.a);
     m->pool.push_back(e.b);
   }
+  if (tl) { std::fprintf(tl, "--\n"); std::fclose(tl); }
   m->pending.clear();
   for (int k = 0; k < STR_K_CLASSES; ++k) {
     stats->class_launches[k] = m->prof_launch[k];

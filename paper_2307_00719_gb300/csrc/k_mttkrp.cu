@@ -85,6 +85,7 @@ __host__ __device__ inline void smem_offsets(int BK, int BM, int RR, int Rb, int
 
 template <typename T, bool C, typename XS, int RPT, int CPT>
 __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
+  PDL_ENTRY();
   typedef typename ElemT<T, C>::type E;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
@@ -298,7 +299,7 @@ cudaError_t launch_t(const MttkrpArgs& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)ceil_div_i(a.dim[a.n], BM), (unsigned)a.splits);
-  kern<<<grid, 256, sm, s>>>(a, BK);
+  launch_k(kern, grid, 256, sm, s, a, BK);
   return cudaGetLastError();
 }
 
@@ -356,6 +357,7 @@ template <typename T, bool CPLX>
 __global__ void __launch_bounds__(256) reduce_kernel(const T* __restrict__ partial, int splits,
                                                      int64_t count, const double* __restrict__ base,
                                                      double scale, double* __restrict__ out) {
+  PDL_ENTRY();
   constexpr int W = CPLX ? 2 : 1;
   __shared__ double red[16][16 * W];
   const int o = threadIdx.x & 15, g = threadIdx.x >> 4;
@@ -394,17 +396,18 @@ cudaError_t launch_reduce_partials(const void* partial, int compute, int cplx, i
   if (count <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((count + 15) / 16);
   if (cplx) {
-    if (compute == 2) reduce_kernel<double, true><<<blocks, 256, 0, s>>>((const double*)partial, splits, count, nullptr, scale, out);
-    else reduce_kernel<float, true><<<blocks, 256, 0, s>>>((const float*)partial, splits, count, nullptr, scale, out);
+    if (compute == 2) launch_k(reduce_kernel<double, true>, blocks, 256, 0, s, (const double*)partial, splits, count, nullptr, scale, out);
+    else launch_k(reduce_kernel<float, true>, blocks, 256, 0, s, (const float*)partial, splits, count, nullptr, scale, out);
   } else {
-    if (compute == 2) reduce_kernel<double, false><<<blocks, 256, 0, s>>>((const double*)partial, splits, count, base, scale, out);
-    else reduce_kernel<float, false><<<blocks, 256, 0, s>>>((const float*)partial, splits, count, base, scale, out);
+    if (compute == 2) launch_k(reduce_kernel<double, false>, blocks, 256, 0, s, (const double*)partial, splits, count, base, scale, out);
+    else launch_k(reduce_kernel<float, false>, blocks, 256, 0, s, (const float*)partial, splits, count, base, scale, out);
   }
   return cudaGetLastError();
 }
 
 template <typename T, typename O>
 __global__ void reduce_to_kernel(const T* partial, int splits, int64_t count, double scale, O* out) {
+  PDL_ENTRY();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -417,11 +420,11 @@ cudaError_t launch_reduce_partials_to(const void* partial, int compute, int spli
                                       double scale, void* out, int out_type, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (compute == 2) {
-    if (out_type == XT_F64) reduce_to_kernel<double, double><<<grid_for(count), 256, 0, s>>>((const double*)partial, splits, count, scale, (double*)out);
-    else reduce_to_kernel<double, float><<<grid_for(count), 256, 0, s>>>((const double*)partial, splits, count, scale, (float*)out);
+    if (out_type == XT_F64) launch_k(reduce_to_kernel<double, double>, grid_for(count), 256, 0, s, (const double*)partial, splits, count, scale, (double*)out);
+    else launch_k(reduce_to_kernel<double, float>, grid_for(count), 256, 0, s, (const double*)partial, splits, count, scale, (float*)out);
   } else {
-    if (out_type == XT_F64) reduce_to_kernel<float, double><<<grid_for(count), 256, 0, s>>>((const float*)partial, splits, count, scale, (double*)out);
-    else reduce_to_kernel<float, float><<<grid_for(count), 256, 0, s>>>((const float*)partial, splits, count, scale, (float*)out);
+    if (out_type == XT_F64) launch_k(reduce_to_kernel<float, double>, grid_for(count), 256, 0, s, (const float*)partial, splits, count, scale, (double*)out);
+    else launch_k(reduce_to_kernel<float, float>, grid_for(count), 256, 0, s, (const float*)partial, splits, count, scale, (float*)out);
   }
   return cudaGetLastError();
 }

@@ -20,6 +20,7 @@ struct ChainArgs {
 template <typename T>
 __global__ void chain_table_kernel(ChainArgs ca, int k0, int k1, int transpose, int64_t J,
                                    T* __restrict__ table) {
+  PDL_ENTRY();
   const int Rf = ca.R[k0], Rl = ca.R[k1 + 1];
   const int64_t total = J * Rf;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -74,8 +75,8 @@ cudaError_t launch_chain_table(const void* const* cores, int compute, const int*
   ChainArgs ca;
   for (int k = 0; k < STR_MAXN; ++k) { ca.core[k] = k < N ? cores[k] : nullptr; ca.dim[k] = k < N ? dims[k] : 1; }
   for (int k = 0; k <= STR_MAXN; ++k) ca.R[k] = k <= N ? R[k] : 1;
-  if (compute == 2) chain_table_kernel<double><<<blocks, 128, 0, s>>>(ca, k0, k1, transpose, J, (double*)table);
-  else chain_table_kernel<float><<<blocks, 128, 0, s>>>(ca, k0, k1, transpose, J, (float*)table);
+  if (compute == 2) launch_k(chain_table_kernel<double>, blocks, 128, 0, s, ca, k0, k1, transpose, J, (double*)table);
+  else launch_k(chain_table_kernel<float>, blocks, 128, 0, s, ca, k0, k1, transpose, J, (float*)table);
   return cudaGetLastError();
 }
 
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(256) recon_kernel(const T* __restrict__ Lm, co
                                                     const void* __restrict__ X, int xtype,
                                                     const uint32_t* __restrict__ mask, void* out,
                                                     int out_type, double* __restrict__ block_sums) {
+  PDL_ENTRY();
   constexpr int KC = 32;
   __shared__ T sL[KC][64 + 1], sR[KC][64 + 1];
   __shared__ double red[2][256];
@@ -179,7 +181,7 @@ cudaError_t launch_recon(const void* Lm, const void* Rm, int compute, int64_t ro
   if (grid.y > 65535) return cudaErrorInvalidValue;
   if (nblocks) *nblocks = (int64_t)grid.x * grid.y;
 #define STR_RECON_CASE(T, M)                                                                 \
-  recon_kernel<T, M><<<grid, 256, 0, s>>>((const T*)Lm, (const T*)Rm, rows, cols, K, X, xtype, \
+  launch_k(recon_kernel<T, M>, grid, 256, 0, s, (const T*)Lm, (const T*)Rm, rows, cols, K, X, xtype, \
                                           mask, out, out_type, block_sums)
   if (compute == 2) {
     switch (mode) {
@@ -203,6 +205,7 @@ cudaError_t launch_recon(const void* Lm, const void* Rm, int compute, int64_t ro
 // fixed-order sum of per-block pairs: out[0] = sum of column 0, out[1] = column 1
 __global__ void sum_blocks_kernel(const double* __restrict__ bs, int64_t nb, int width,
                                   double* __restrict__ out, double scale) {
+  PDL_ENTRY();
   __shared__ double red[256];
   for (int c = 0; c < width; ++c) {
     double s = 0.0;
@@ -220,6 +223,6 @@ __global__ void sum_blocks_kernel(const double* __restrict__ bs, int64_t nb, int
 
 cudaError_t launch_sum_blocks(const double* block_sums, int64_t nblocks, int width, double* out,
                               double scale, cudaStream_t s) {
-  sum_blocks_kernel<<<1, 256, 0, s>>>(block_sums, nblocks, width, out, scale);
+  launch_k(sum_blocks_kernel, 1, 256, 0, s, block_sums, nblocks, width, out, scale);
   return cudaGetLastError();
 }

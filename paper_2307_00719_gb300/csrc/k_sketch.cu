@@ -13,6 +13,7 @@
 // ---------------------------------------------------------------------------
 __global__ void draw_indices_kernel(int32_t* __restrict__ out, int64_t m, int64_t I, uint64_t seed,
                                     int k, uint64_t tau, uint32_t sid, const double* __restrict__ p) {
+  PDL_ENTRY();
   extern __shared__ double cdf[];
   __shared__ int s_last;
   if (p) {
@@ -60,11 +61,12 @@ cudaError_t launch_draw_indices(int32_t* out, int64_t m, int64_t I, uint64_t see
     if (e != cudaSuccess) return e;
   }
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((m + 511) / 512, 152));
-  draw_indices_kernel<<<(unsigned)blocks, 512, sm, s>>>(out, m, I, seed, k, tau, stream_id, p);
+  launch_k(draw_indices_kernel, (unsigned)blocks, 512, sm, s, out, m, I, seed, k, tau, stream_id, p);
   return cudaGetLastError();
 }
 
 __global__ void signs_kernel(double* d, int64_t I, uint64_t seed, int k, uint64_t tau, uint32_t sid) {
+  PDL_ENTRY();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < I;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t u = draw_u64(seed, (uint64_t)i, (uint64_t)k, tau, 1u, sid);
@@ -75,7 +77,7 @@ __global__ void signs_kernel(double* d, int64_t I, uint64_t seed, int k, uint64_
 cudaError_t launch_signs(double* d, int64_t I, uint64_t seed, int k, uint64_t tau,
                          uint32_t stream_id, cudaStream_t s) {
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((I + 255) / 256, 256));
-  signs_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, I, seed, k, tau, stream_id);
+  launch_k(signs_kernel, (unsigned)blocks, 256, 0, s, d, I, seed, k, tau, stream_id);
   return cudaGetLastError();
 }
 
@@ -86,6 +88,7 @@ cudaError_t launch_signs(double* d, int64_t I, uint64_t seed, int k, uint64_t ta
 template <typename T, bool C>
 __global__ void __launch_bounds__(256) wgram_kernel(const T* __restrict__ g, const double* __restrict__ w,
                                                     int64_t m, int64_t per, int RR, double* __restrict__ part) {
+  PDL_ENTRY();
   constexpr int CH = 32;
   constexpr int W = C ? 2 : 1;
   __shared__ double sa[CH][16 * W], sb[CH][16 * W];
@@ -132,11 +135,11 @@ cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const do
   splits = (m + per - 1) / per;
   dim3 grid((unsigned)ceil_div_i(RR, 16), (unsigned)ceil_div_i(RR, 16), (unsigned)splits);
   if (compute == 2) {
-    if (cplx) wgram_kernel<double, true><<<grid, 256, 0, s>>>((const double*)gs, w, m, per, RR, part);
-    else wgram_kernel<double, false><<<grid, 256, 0, s>>>((const double*)gs, w, m, per, RR, part);
+    if (cplx) launch_k(wgram_kernel<double, true>, grid, 256, 0, s, (const double*)gs, w, m, per, RR, part);
+    else launch_k(wgram_kernel<double, false>, grid, 256, 0, s, (const double*)gs, w, m, per, RR, part);
   } else {
-    if (cplx) wgram_kernel<float, true><<<grid, 256, 0, s>>>((const float*)gs, w, m, per, RR, part);
-    else wgram_kernel<float, false><<<grid, 256, 0, s>>>((const float*)gs, w, m, per, RR, part);
+    if (cplx) launch_k(wgram_kernel<float, true>, grid, 256, 0, s, (const float*)gs, w, m, per, RR, part);
+    else launch_k(wgram_kernel<float, false>, grid, 256, 0, s, (const float*)gs, w, m, per, RR, part);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -153,6 +156,7 @@ template <typename T>
 __global__ void dft_mode_kernel(const void* __restrict__ in, int in_type, T* __restrict__ out,
                                 int64_t L, int64_t inner, int64_t nfib, const double* __restrict__ d,
                                 const double* __restrict__ tw, int FB) {
+  PDL_ENTRY();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sre = (T*)smraw;                 // L * FB
   T* sim = sre + L * FB;              // L * FB
@@ -243,6 +247,7 @@ __global__ void fft_mode_kernel(const void* __restrict__ in, int in_type, void* 
                                 int64_t inner, int64_t nfib, const double* __restrict__ dpre,
                                 const double* __restrict__ dpost, int inverse,
                                 const double* __restrict__ tw, int FB) {
+  PDL_ENTRY();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sre = (T*)smraw;                 // L * FB
   T* sim = sre + L * FB;              // L * FB
@@ -327,7 +332,7 @@ static cudaError_t launch_fft(const void* in, int in_type, void* out, int out_re
   cudaError_t e = cudaFuncSetAttribute(fft_mode_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nfib + FB - 1) / FB, 152 * 8));
-  fft_mode_kernel<T><<<(unsigned)blocks, 256, sm, s>>>(in, in_type, out, out_real, base, L, logL, inner, nfib,
+  launch_k(fft_mode_kernel<T>, (unsigned)blocks, 256, sm, s, in, in_type, out, out_real, base, L, logL, inner, nfib,
                                                        dpre, dpost, inverse, tw, FB);
   return cudaGetLastError();
 }
@@ -353,10 +358,10 @@ cudaError_t launch_dft_mode(const void* in, int in_type, void* out, int out_cplx
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nfib + FB - 1) / FB, 152 * 8));
   if (out_cplx_compute == 2) {
     cudaFuncSetAttribute(dft_mode_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dft_mode_kernel<double><<<(unsigned)blocks, 256, sm, s>>>(in, in_type, (double*)out, L, inner, nfib, d, tw, FB);
+    launch_k(dft_mode_kernel<double>, (unsigned)blocks, 256, sm, s, in, in_type, (double*)out, L, inner, nfib, d, tw, FB);
   } else {
     cudaFuncSetAttribute(dft_mode_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dft_mode_kernel<float><<<(unsigned)blocks, 256, sm, s>>>(in, in_type, (float*)out, L, inner, nfib, d, tw, FB);
+    launch_k(dft_mode_kernel<float>, (unsigned)blocks, 256, sm, s, in, in_type, (float*)out, L, inner, nfib, d, tw, FB);
   }
   return cudaGetLastError();
 }
@@ -366,6 +371,7 @@ cudaError_t launch_dft_mode(const void* in, int in_type, void* out, int out_cplx
 __global__ void unmix_rows_kernel(const double* __restrict__ Y, int64_t L, int RR,
                                   const double* __restrict__ d, const double* __restrict__ tw,
                                   const double* __restrict__ base, double* __restrict__ out) {
+  PDL_ENTRY();
   const double scale = 1.0 / sqrt((double)L);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L * RR;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -390,7 +396,7 @@ cudaError_t launch_unmix_rows(const double* Y, int64_t L, int RR, const double* 
   if (logL > 0)   // Y as a (RR, L) tensor, inverse transform along L
     return launch_fft<double>(Y, XT_C64, out, 1, base, L, logL, RR, RR, nullptr, d, 1, tw, s);
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((L * RR + 255) / 256, 2048));
-  unmix_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y, L, RR, d, tw, base, out);
+  launch_k(unmix_rows_kernel, (unsigned)blocks, 256, 0, s, Y, L, RR, d, tw, base, out);
   return cudaGetLastError();
 }
 
@@ -399,6 +405,7 @@ cudaError_t launch_unmix_rows(const double* Y, int64_t L, int RR, const double* 
 // ---------------------------------------------------------------------------
 template <typename I, typename O>
 __global__ void convert_kernel(const I* __restrict__ in, O* __restrict__ out, int64_t count) {
+  PDL_ENTRY();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (O)in[i];
@@ -408,16 +415,17 @@ cudaError_t launch_convert(const void* in, int in_type, void* out, int out_type,
                            cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 4096));
-  if (in_type == XT_F64 && out_type == XT_F32) convert_kernel<double, float><<<blocks, 256, 0, s>>>((const double*)in, (float*)out, count);
-  else if (in_type == XT_F32 && out_type == XT_F64) convert_kernel<float, double><<<blocks, 256, 0, s>>>((const float*)in, (double*)out, count);
-  else if (in_type == XT_F64 && out_type == XT_F64) convert_kernel<double, double><<<blocks, 256, 0, s>>>((const double*)in, (double*)out, count);
-  else if (in_type == XT_F32 && out_type == XT_F32) convert_kernel<float, float><<<blocks, 256, 0, s>>>((const float*)in, (float*)out, count);
+  if (in_type == XT_F64 && out_type == XT_F32) launch_k(convert_kernel<double, float>, blocks, 256, 0, s, (const double*)in, (float*)out, count);
+  else if (in_type == XT_F32 && out_type == XT_F64) launch_k(convert_kernel<float, double>, blocks, 256, 0, s, (const float*)in, (double*)out, count);
+  else if (in_type == XT_F64 && out_type == XT_F64) launch_k(convert_kernel<double, double>, blocks, 256, 0, s, (const double*)in, (double*)out, count);
+  else if (in_type == XT_F32 && out_type == XT_F32) launch_k(convert_kernel<float, float>, blocks, 256, 0, s, (const float*)in, (float*)out, count);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void check_finite_kernel(const T* __restrict__ x, int64_t count, int* status) {
+  PDL_ENTRY();
   bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -426,6 +434,7 @@ __global__ void check_finite_kernel(const T* __restrict__ x, int64_t count, int*
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, DEV_ERR_NONFINITE);
 }
 __global__ void check_finite_bf16_kernel(const __nv_bfloat16* __restrict__ x, int64_t count, int* status) {
+  PDL_ENTRY();
   bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -435,8 +444,8 @@ __global__ void check_finite_bf16_kernel(const __nv_bfloat16* __restrict__ x, in
 
 cudaError_t launch_check_finite(const void* X, int xtype, int64_t count, int* status, cudaStream_t s) {
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 8));
-  if (xtype == XT_F64) check_finite_kernel<double><<<blocks, 256, 0, s>>>((const double*)X, count, status);
-  else if (xtype == XT_F32) check_finite_kernel<float><<<blocks, 256, 0, s>>>((const float*)X, count, status);
-  else check_finite_bf16_kernel<<<blocks, 256, 0, s>>>((const __nv_bfloat16*)X, count, status);
+  if (xtype == XT_F64) launch_k(check_finite_kernel<double>, blocks, 256, 0, s, (const double*)X, count, status);
+  else if (xtype == XT_F32) launch_k(check_finite_kernel<float>, blocks, 256, 0, s, (const float*)X, count, status);
+  else launch_k(check_finite_bf16_kernel, blocks, 256, 0, s, (const __nv_bfloat16*)X, count, status);
   return cudaGetLastError();
 }

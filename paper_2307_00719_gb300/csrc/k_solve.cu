@@ -16,6 +16,7 @@
 __global__ void __launch_bounds__(256) core_gram_kernel(const double* __restrict__ G, int64_t I, int Ra,
                                                         int Rb, double* __restrict__ M,
                                                         double* __restrict__ E) {
+  PDL_ENTRY();
   // 64 pairs per CTA, 4 threads per pair each summing every 4th row; the four
   // partial sums are added in a fixed order
   __shared__ double red[4][64];
@@ -51,7 +52,7 @@ cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double*
   const int RR = Ra * Rb;
   const int64_t npairs = (int64_t)RR * (RR + 1) / 2;
   const int64_t blocks = std::max<int64_t>(1, (npairs + 63) / 64);
-  core_gram_kernel<<<(unsigned)blocks, 256, 0, s>>>(G, I, Ra, Rb, M, E);
+  launch_k(core_gram_kernel, (unsigned)blocks, 256, 0, s, G, I, Ra, Rb, M, E);
   return cudaGetLastError();
 }
 
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ 
                                                      const double* __restrict__ B,
                                                      double* __restrict__ C, int M, int K, int N,
                                                      int pRa, int pRb, const double* __restrict__ base) {
+  PDL_ENTRY();
   extern __shared__ double gsm[];
   double* sA = gsm;            // 8 x K
   double* sB = gsm + 8 * K;    // K x 8
@@ -107,7 +109,7 @@ cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, in
     cudaError_t e = cudaFuncSetAttribute(gemm64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  gemm64_kernel<<<grid, 256, sm, s>>>(A, B, C, M, K, N, perm_Ra, perm_Rb, base);
+  launch_k(gemm64_kernel, grid, 256, sm, s, A, B, C, M, K, N, perm_Ra, perm_Rb, base);
   return cudaGetLastError();
 }
 
@@ -129,6 +131,7 @@ template <typename T, int B>
 __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __restrict__ Q, int n,
                                                             T* __restrict__ W, int* status,
                                                             double* pivot_ratio) {
+  PDL_ENTRY();
   __shared__ T col[2][16 * B];
   __shared__ T qd[16 * B];
   __shared__ T pivs[16 * B];   // pivot k as met (before any replacement)
@@ -235,11 +238,11 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
 
 template <typename T>
 static cudaError_t launch_sweep(const double* Q, int n, T* W, int* status, double* pivot_ratio, cudaStream_t s) {
-  if (n <= 16) sweep_inverse_kernel<T, 1><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
-  else if (n <= 32) sweep_inverse_kernel<T, 2><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
-  else if (n <= 64) sweep_inverse_kernel<T, 4><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
-  else if (n <= 112) sweep_inverse_kernel<T, 7><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
-  else if (n <= 160) sweep_inverse_kernel<T, 10><<<1, 256, 0, s>>>(Q, n, W, status, pivot_ratio);
+  if (n <= 16) launch_k(sweep_inverse_kernel<T, 1>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
+  else if (n <= 32) launch_k(sweep_inverse_kernel<T, 2>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
+  else if (n <= 64) launch_k(sweep_inverse_kernel<T, 4>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
+  else if (n <= 112) launch_k(sweep_inverse_kernel<T, 7>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
+  else if (n <= 160) launch_k(sweep_inverse_kernel<T, 10>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
@@ -255,6 +258,7 @@ template <int B>
 __global__ void __launch_bounds__(256) ldlt64_kernel(const double* __restrict__ Q, int n,
                                                      double* __restrict__ L, double* __restrict__ invdiag,
                                                      int* status, double* pivot_ratio) {
+  PDL_ENTRY();
   __shared__ double col[2][16 * B];
   __shared__ double rb[2];
   __shared__ double sinv[16 * B];
@@ -332,11 +336,11 @@ __global__ void __launch_bounds__(256) ldlt64_kernel(const double* __restrict__ 
 
 cudaError_t launch_chol_factor(const double* Q, int n, double* L, double* invdiag, int* status,
                                double* pivot_ratio, cudaStream_t s) {
-  if (n <= 16) ldlt64_kernel<1><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
-  else if (n <= 32) ldlt64_kernel<2><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
-  else if (n <= 64) ldlt64_kernel<4><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
-  else if (n <= 112) ldlt64_kernel<7><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
-  else if (n <= 160) ldlt64_kernel<10><<<1, 256, 0, s>>>(Q, n, L, invdiag, status, pivot_ratio);
+  if (n <= 16) launch_k(ldlt64_kernel<1>, 1, 256, 0, s, Q, n, L, invdiag, status, pivot_ratio);
+  else if (n <= 32) launch_k(ldlt64_kernel<2>, 1, 256, 0, s, Q, n, L, invdiag, status, pivot_ratio);
+  else if (n <= 64) launch_k(ldlt64_kernel<4>, 1, 256, 0, s, Q, n, L, invdiag, status, pivot_ratio);
+  else if (n <= 112) launch_k(ldlt64_kernel<7>, 1, 256, 0, s, Q, n, L, invdiag, status, pivot_ratio);
+  else if (n <= 160) launch_k(ldlt64_kernel<10>, 1, 256, 0, s, Q, n, L, invdiag, status, pivot_ratio);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
@@ -350,6 +354,7 @@ __global__ void __launch_bounds__(128) chol_solve_kernel(const double* __restric
                                                          const double* __restrict__ invdiag, int n,
                                                          const double* __restrict__ P, int64_t rows,
                                                          double* out64, float* out32, double* lev) {
+  PDL_ENTRY();
   extern __shared__ double sm[];
   const int ld = n + 1;
   double* L = sm;                       // n x ld
@@ -400,7 +405,7 @@ cudaError_t launch_chol_solve(const double* L, const double* invdiag, int n, con
   cudaError_t e = cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((rows + 3) / 4, 152 * 2));
-  chol_solve_kernel<<<(unsigned)blocks, 128, sm, s>>>(L, invdiag, n, P, rows, out64, out32, lev);
+  launch_k(chol_solve_kernel, (unsigned)blocks, 128, sm, s, L, invdiag, n, P, rows, out64, out32, lev);
   return cudaGetLastError();
 }
 
@@ -414,6 +419,7 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
                                                            const double* __restrict__ P, int64_t rows,
                                                            int iters, int q_in_smem, double* out64,
                                                            float* out32, PartialSum ps) {
+  PDL_ENTRY();
   // one row of P per CTA at a time, one thread per column of the solution
   extern __shared__ unsigned char smr[];
   float* Wm = (float*)smr;                                                    // n x n
@@ -501,7 +507,7 @@ cudaError_t launch_apply_mixed(const float* W32, const double* Q, int n, const d
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 4));
   const int threads = ((n + 31) / 32) * 32;
   PartialSum none;
-  solve_refine_kernel<<<(unsigned)blocks, threads, sms, s>>>(W32, Q, n, P, rows, iters, q_in_smem, out64, out32,
+  launch_k(solve_refine_kernel, (unsigned)blocks, threads, sms, s, W32, Q, n, P, rows, iters, q_in_smem, out64, out32,
                                                             ps ? *ps : none);
   return cudaGetLastError();
 }
@@ -515,6 +521,7 @@ cudaError_t launch_solve_mixed(const double* Q, int n, const double* P, int64_t 
 }
 
 __global__ void fill_kernel(double* p, int64_t count, double v) {
+  PDL_ENTRY();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
@@ -523,6 +530,6 @@ __global__ void fill_kernel(double* p, int64_t count, double v) {
 cudaError_t launch_fill(double* p, int64_t count, double v, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 1024));
-  fill_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, count, v);
+  launch_k(fill_kernel, (unsigned)blocks, 256, 0, s, p, count, v);
   return cudaGetLastError();
 }

@@ -98,15 +98,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                    smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&v)[16]) {
+// issue only; tmem_wait_ld() before the registers are read
+__device__ __forceinline__ void tmem_ld_x16_nw(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld_x8(uint32_t taddr, uint32_t (&v)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_kernel(const __grid_constant
                                                            const float* __restrict__ Blo, int M,
                                                            int Kpad, int N, int Npad, uint32_t tmem_cols,
                                                            float* __restrict__ Y, int* status) {
+  PDL_ENTRY();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sAhi = smem;                              // 128 x 128 B
@@ -269,29 +271,43 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_kernel(const __grid_constant
 }
 
 // ---------------------------------------------------------------------------
-// stage 1, persistent form: one CTA per SM loops over 128-row tiles.  The split
-// B operand (all K chunks) is loaded once into shared memory; the next tile's
-// A chunks are prefetched by TMA into a second raw buffer while the current
-// tile is converted, multiplied and written out.
+// stage 1, persistent form: one CTA per SM loops over 128-row tiles.
+// * The split B operand (all K chunks) is copied once into shared memory with
+//   cp.async, swizzled, overlapping the first tile's TMA load.
+// * FP32 slab: TMA loads each A chunk with the 128-byte swizzle, so the raw tile
+//   already is the K-major operand.  The tensor core reads an FP32 word as TF32
+//   by dropping its 13 low mantissa bits, so the raw tile serves as X_hi =
+//   trunc(X) and only X_lo = rn(X - trunc(X)) (exact residual, rounded to the
+//   nearest TF32) is formed: X_hi + X_lo equals X to 2^-22 relative, unbiased.
+// * BF16 slab: the raw tile is widened to FP32 into the operand tile (exact;
+//   no X_lo term).
+// * The next tile's A chunks are prefetched by TMA into the other buffer while
+//   the current tile is split, multiplied and written out; the epilogue writes
+//   whole 32-byte sectors (float4 pairs) of Y.
 // ---------------------------------------------------------------------------
 template <bool SRC_BF16>
 __global__ void __launch_bounds__(128, 1) stage1_tc_persist_kernel(
     const __grid_constant__ CUtensorMap tmA, const float* __restrict__ Bhi, const float* __restrict__ Blo,
     int M, int Kpad, int N, int Npad, uint32_t tmem_cols, float* __restrict__ Y, int* status) {
+  PDL_ENTRY();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int nch = Kpad / 32;
   const size_t bchunk = (size_t)Npad * 128;
   unsigned char* sBhi = smem;                                   // nch x (Npad x 128 B)
   unsigned char* sBlo = sBhi + nch * bchunk;
-  unsigned char* sAhi = sBlo + nch * bchunk;                    // nch x 16 KB
-  unsigned char* sAlo = sAhi + (size_t)nch * 16384;
-  unsigned char* sRaw = sAlo + (size_t)nch * 16384;             // 2 x nch x 16 KB
-  uint64_t* bars = (uint64_t*)(sRaw + (size_t)2 * nch * 16384); // tma[0], tma[1], mma
+  unsigned char* sA = sBlo + nch * bchunk;
+  // FP32: sA = 2 buffers x nch x 16 KB (TMA targets = X_hi), then sLo = nch x 16 KB
+  // BF16: sA = nch x 16 KB (widened operand), then sRaw = 2 buffers x nch x 8 KB
+  constexpr uint32_t kRawChunk = SRC_BF16 ? 8192u : 16384u;
+  unsigned char* sLo = sA + (size_t)2 * nch * 16384;            // FP32 only
+  unsigned char* sRaw = sA + (size_t)nch * 16384;               // BF16 only
+  unsigned char* tma_base = SRC_BF16 ? sRaw : sA;               // buffer b, chunk c at + (b nch + c) kRawChunk
+  unsigned char* after = SRC_BF16 ? sRaw + (size_t)2 * nch * kRawChunk : sLo + (size_t)nch * 16384;
+  uint64_t* bars = (uint64_t*)after;                            // tma[0], tma[1], mma
   uint32_t* tslot = (uint32_t*)(bars + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = (M + 127) / 128;
-  const uint32_t chunk_bytes = SRC_BF16 ? 128 * 32 * 2 : 128 * 32 * 4;
 
   if (warp == 0) tmem_alloc(tslot, tmem_cols);
   if (tid == 0) {
@@ -305,60 +321,67 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_persist_kernel(
   tc_fence_after();
   const uint32_t tmem = *tslot;
   if (tid == 0 && (int)blockIdx.x < ntiles) {
-    mbar_expect_tx(&bars[0], chunk_bytes * nch);
-    for (int c = 0; c < nch; ++c) tma_load_2d(sRaw + (size_t)c * 16384, &tmA, &bars[0], c * 32, blockIdx.x * 128);
+    mbar_expect_tx(&bars[0], kRawChunk * nch);
+    for (int c = 0; c < nch; ++c) tma_load_2d(tma_base + (size_t)c * kRawChunk, &tmA, &bars[0], c * 32, blockIdx.x * 128);
   }
-  // the whole split B operand, swizzled, once per CTA
+  // the whole split B operand, swizzled, once per CTA (asynchronous copies)
   for (int c = 0; c < nch; ++c)
     for (int r = tid >> 3; r < Npad; r += 16) {
       const int j = tid & 7;
-      *(float4*)(sBhi + c * bchunk + sw128_off(r, j)) = *(const float4*)(Bhi + (size_t)r * Kpad + c * 32 + j * 4);
-      *(float4*)(sBlo + c * bchunk + sw128_off(r, j)) = *(const float4*)(Blo + (size_t)r * Kpad + c * 32 + j * 4);
+      cp_async16(sBhi + c * bchunk + sw128_off(r, j), Bhi + (size_t)r * Kpad + c * 32 + j * 4);
+      cp_async16(sBlo + c * bchunk + sw128_off(r, j), Blo + (size_t)r * Kpad + c * 32 + j * 4);
     }
+  cp_async_commit();
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Npad >> 3) << 17) |
                          ((uint32_t)(128 >> 4) << 24);
-  uint32_t ph_tma = 0, ph_mma = 0;   // ph_tma bit b: phase of raw buffer b
+  uint32_t ph_tma = 0, ph_mma = 0;   // ph_tma bit b: phase of buffer b
   bool failed = false;
   int it = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
     const int buf = it & 1;
     const int tn = t + gridDim.x;
-    if (tid == 0 && tn < ntiles) {   // prefetch the next tile into the other raw buffer
-      mbar_expect_tx(&bars[buf ^ 1], chunk_bytes * nch);
+    if (tid == 0 && tn < ntiles) {   // prefetch the next tile into the other buffer
+      mbar_expect_tx(&bars[buf ^ 1], kRawChunk * nch);
       for (int c = 0; c < nch; ++c)
-        tma_load_2d(sRaw + ((size_t)(buf ^ 1) * nch + c) * 16384, &tmA, &bars[buf ^ 1], c * 32, tn * 128);
+        tma_load_2d(tma_base + ((size_t)(buf ^ 1) * nch + c) * kRawChunk, &tmA, &bars[buf ^ 1], c * 32, tn * 128);
     }
     const bool ok = mbar_wait(&bars[buf], (ph_tma >> buf) & 1u, kWaitNs);
     ph_tma ^= 1u << buf;
     if (__syncthreads_or(!ok)) { failed = true; break; }
-    for (int c = 0; c < nch; ++c) {
-      const unsigned char* raw = sRaw + ((size_t)buf * nch + c) * 16384;
-      unsigned char* ah = sAhi + (size_t)c * 16384;
-      unsigned char* al = sAlo + (size_t)c * 16384;
-      for (int p = 0; p < 8; ++p) {
-        const int r = p * 16 + (tid >> 3);
-        const int j = tid & 7;
-        float4 v;
-        if (SRC_BF16) {
+    const unsigned char* araw = tma_base + (size_t)buf * nch * kRawChunk;
+    if (!SRC_BF16) {
+      // X_lo at the same (swizzled) position as X in the TMA tile
+      for (int q = tid; q < nch * 1024; q += 128) {
+        const float4 v = *(const float4*)(araw + (size_t)q * 16);
+        const float4 h = make_float4(__uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u),
+                                     __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u),
+                                     __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u),
+                                     __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u));
+        *(float4*)(sLo + (size_t)q * 16) =
+            make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
+      }
+    } else {
+      for (int c = 0; c < nch; ++c) {
+        const unsigned char* raw = araw + (size_t)c * kRawChunk;
+        unsigned char* ah = sA + (size_t)c * 16384;
+        for (int p = 0; p < 8; ++p) {
+          const int r = p * 16 + (tid >> 3);
+          const int j = tid & 7;
           const __nv_bfloat162* q = (const __nv_bfloat162*)(raw + r * 64 + j * 8);
           const float2 x0 = __bfloat1622float2(q[0]), x1 = __bfloat1622float2(q[1]);
-          v = make_float4(x0.x, x0.y, x1.x, x1.y);
-        } else {
-          v = *(const float4*)(raw + r * 128 + j * 16);
+          *(float4*)(ah + sw128_off(r, j)) = make_float4(x0.x, x0.y, x1.x, x1.y);
         }
-        const float4 hi = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
-        *(float4*)(ah + sw128_off(r, j)) = hi;
-        if (!SRC_BF16)
-          *(float4*)(al + sw128_off(r, j)) = make_float4(tf32_rn(v.x - hi.x), tf32_rn(v.y - hi.y),
-                                                         tf32_rn(v.z - hi.z), tf32_rn(v.w - hi.w));
       }
     }
+    if (it == 0) cp_async_wait_all();
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
+      const unsigned char* ahi = SRC_BF16 ? sA : araw;
       for (int c = 0; c < nch; ++c) {
-        const uint64_t ah = desc_sw128(sAhi + (size_t)c * 16384), al = desc_sw128(sAlo + (size_t)c * 16384);
+        const uint64_t ah = desc_sw128(ahi + (size_t)c * (SRC_BF16 ? 16384 : kRawChunk));
+        const uint64_t al = desc_sw128(sLo + (size_t)c * 16384);
         const uint64_t bh = desc_sw128(sBhi + c * bchunk), bl = desc_sw128(sBlo + c * bchunk);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
@@ -378,26 +401,44 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_persist_kernel(
     if (__syncthreads_or(!ok2)) { failed = true; break; }
     tc_fence_after();
     const int row = t * 128 + 32 * warp + lane;
+    const bool vec = (N & 3) == 0;
     for (int col = 0; col < Npad; col += 16) {
       const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col;
       uint32_t v0[16], v1[16], vx[16];
-      tmem_ld_x16(base, v0);
-      tmem_ld_x16(base + (uint32_t)Npad, v1);
-      tmem_ld_x16(base + (uint32_t)(2 * Npad), vx);
+      tmem_ld_x16_nw(base, v0);
+      tmem_ld_x16_nw(base + (uint32_t)Npad, v1);
+      tmem_ld_x16_nw(base + (uint32_t)(2 * Npad), vx);
+      tmem_wait_ld();
       if (row < M) {
-        float* yrow = Y + (size_t)row * N + col;
+        float y[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (col + j < N) yrow[j] = (__uint_as_float(v0[j]) + __uint_as_float(vx[j])) + __uint_as_float(v1[j]);
+          y[j] = (__uint_as_float(v0[j]) + __uint_as_float(vx[j])) + __uint_as_float(v1[j]);
+        float* yrow = Y + (size_t)row * N + col;
+        if (vec && col + 16 <= N) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) *(float4*)(yrow + j) = make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (col + j < N) yrow[j] = y[j];
+        }
       }
     }
     tc_fence_before();
     __syncthreads();
   }
+  if (it == 0) cp_async_wait_all();   // no tile: B copies still complete before exit
   if (failed && tid == 0) atomicOr(status, DEV_ERR_TIMEOUT);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, tmem_cols);
+}
+
+size_t stage1_persist_smem_bytes(int Npad, int nch, bool bf16) {
+  const size_t b = (size_t)2 * nch * Npad * 128;
+  const size_t a = bf16 ? (size_t)nch * 16384 + (size_t)2 * nch * 8192 : (size_t)3 * nch * 16384;
+  return 1024 + b + a + 64;
 }
 
 // ---------------------------------------------------------------------------
@@ -405,6 +446,7 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_persist_kernel(
 // ---------------------------------------------------------------------------
 __global__ void prep_b_kernel(const double* __restrict__ G, int K, int N, int Kpad, int Npad,
                               float* __restrict__ Bhi, float* __restrict__ Blo) {
+  PDL_ENTRY();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)Kpad * Npad;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int n = (int)(e / Kpad), k = (int)(e % Kpad);
@@ -424,6 +466,7 @@ __global__ void prep_b_kernel(const double* __restrict__ G, int K, int N, int Kp
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void transpose01_kernel(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int64_t rest) {
+  PDL_ENTRY();
   __shared__ T tile[32][33];
   const int64_t r = blockIdx.z;
   const int i0b = blockIdx.x * 32, i1b = blockIdx.y * 32;
@@ -502,6 +545,7 @@ __device__ __forceinline__ float s2_dot(const float* L, const float* M) {
 // RT > 0: all four ranks equal RT (compile-time strides); RT = 0: any ranks
 template <int RT>
 __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
+  PDL_ENTRY();
   extern __shared__ __align__(16) float s2[];
   const int Rk = a.Rk, Rk1 = a.Rk1, Rn = a.Rn, Rn1 = a.Rn1;
   const int RRk = Rk * Rk1;
@@ -677,7 +721,7 @@ cudaError_t launch_prep_b(const double* G, int K, int N, int Kpad, int Npad, flo
                           cudaStream_t s) {
   const int64_t total = (int64_t)Kpad * Npad;
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 1024));
-  prep_b_kernel<<<blocks, 256, 0, s>>>(G, K, N, Kpad, Npad, Bhi, Blo);
+  launch_k(prep_b_kernel, blocks, 256, 0, s, G, K, N, Kpad, Npad, Bhi, Blo);
   return cudaGetLastError();
 }
 
@@ -687,9 +731,9 @@ cudaError_t launch_transpose01(const void* in, void* out, int xtype, int d0, int
   dim3 block(32, 8);
   if (rest > 65535) return cudaErrorInvalidValue;
   if (xtype == XT_BF16)
-    transpose01_kernel<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, d0, d1, rest);
+    launch_k(transpose01_kernel<__nv_bfloat16>, grid, block, 0, s, (const __nv_bfloat16*)in, (__nv_bfloat16*)out, d0, d1, rest);
   else
-    transpose01_kernel<float><<<grid, block, 0, s>>>((const float*)in, (float*)out, d0, d1, rest);
+    launch_k(transpose01_kernel<float>, grid, block, 0, s, (const float*)in, (float*)out, d0, d1, rest);
   return cudaGetLastError();
 }
 
@@ -697,49 +741,54 @@ cudaError_t launch_stage1_tc(const void* Xa, int xtype, int64_t M, int K, const 
                              int Kpad, int N, int Npad, float* Y, int* status, cudaStream_t s) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
-  CUtensorMap tm;
-  const int es = xtype == XT_BF16 ? 2 : 4;
-  cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)M};
-  cuuint64_t gstride[1] = {(cuuint64_t)K * es};
-  cuuint32_t box[2] = {32, 128};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(&tm, xtype == XT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                   const_cast<void*>(Xa), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const bool bf16 = xtype == XT_BF16;
+  const int es = bf16 ? 2 : 4;
   uint32_t cols = 32;
   while ((int)cols < 3 * Npad) cols <<= 1;
   if (cols > 512) return cudaErrorInvalidValue;
   const int nch = Kpad / 32;
-  const size_t smp = 1024 + (size_t)2 * nch * Npad * 128 + (size_t)4 * nch * 16384 + 64;
-  if (smp <= 200 * 1024) {
+  const size_t smp = stage1_persist_smem_bytes(Npad, nch, bf16);
+  const bool persist = smp <= 200 * 1024;
+  // FP32 persistent path: the TMA tile lands already swizzled (it is the X_hi operand)
+  auto encode = [&](CUtensorMap* tm, bool swz) {
+    cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)M};
+    cuuint64_t gstride[1] = {(cuuint64_t)K * es};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+               const_cast<void*>(Xa), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  };
+  CUtensorMap tm;
+  if (encode(&tm, persist && !bf16) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  if (persist) {
     int sms = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = (M + 127) / 128;
     const unsigned gridp = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, sms));
-    if (xtype == XT_BF16) {
+    if (bf16) {
       cudaError_t e = cudaFuncSetAttribute(stage1_tc_persist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
       if (e != cudaSuccess) return e;
-      stage1_tc_persist_kernel<true><<<gridp, 128, smp, s>>>(tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+      launch_k(stage1_tc_persist_kernel<true>, gridp, 128, smp, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
     } else {
       cudaError_t e = cudaFuncSetAttribute(stage1_tc_persist_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
       if (e != cudaSuccess) return e;
-      stage1_tc_persist_kernel<false><<<gridp, 128, smp, s>>>(tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+      launch_k(stage1_tc_persist_kernel<false>, gridp, 128, smp, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
     }
     return cudaGetLastError();
   }
   const size_t sm = stage1_smem_bytes(Npad);
   const unsigned grid = (unsigned)((M + 127) / 128);
-  if (xtype == XT_BF16) {
+  if (bf16) {
     cudaError_t e = cudaFuncSetAttribute(stage1_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    stage1_tc_kernel<true><<<grid, 128, sm, s>>>(tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+    launch_k(stage1_tc_kernel<true>, grid, 128, sm, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
   } else {
     cudaError_t e = cudaFuncSetAttribute(stage1_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    stage1_tc_kernel<false><<<grid, 128, sm, s>>>(tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+    launch_k(stage1_tc_kernel<false>, grid, 128, sm, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
   }
   return cudaGetLastError();
 }
@@ -767,6 +816,6 @@ cudaError_t launch_stage2(const Stage2Args& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)a.dn, (unsigned)a.splits);
-  kern<<<grid, S2_THREADS, sm, s>>>(a);
+  launch_k(kern, grid, S2_THREADS, sm, s, a);
   return cudaGetLastError();
 }
