@@ -106,6 +106,7 @@ struct str_ctx {
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   bool side2_used = false;
   DevBuf mbuf[2];
+  DevBuf qf, fcount, ring2, ring3;   // FP32 copy of Q and the last-CTA counter of the fused ring GEMM + factor
 
   int RR(int n) const { return R[n] * R[n + 1]; }
   int64_t m() const { return opt.m; }
@@ -262,12 +263,13 @@ str_status ring_prefix(str_ctx* c, int n, const double* ENew, double* out, const
   auto Eptr = [&](int k) -> const double* { return k == N - 1 ? ENew : E_of(c, k); };
   const int f0 = (n + 1) % N;
   if (N == 3) { *M = Eptr(f0); return STR_OK; }
-  TRY(grow(c, c->ring0, (size_t)STR_MAXRR * STR_MAXRR * 8));
-  TRY(grow(c, c->ring1, (size_t)STR_MAXRR * STR_MAXRR * 8));
+  // own scratch: runs on the third stream beside ring_Q
+  TRY(grow(c, c->ring2, (size_t)STR_MAXRR * STR_MAXRR * 8));
+  TRY(grow(c, c->ring3, (size_t)STR_MAXRR * STR_MAXRR * 8));
   const double* A = Eptr(f0);
   const int Mrows = c->R[f0] * c->R[f0];
   int Kc = c->R[f0 + 1] * c->R[f0 + 1];
-  double* bufs[2] = {(double*)c->ring0.p, (double*)c->ring1.p};
+  double* bufs[2] = {(double*)c->ring2.p, (double*)c->ring3.p};
   int bi = 0;
   for (int t = 1; t < N - 2; ++t) {
     const int k = (n + 1 + t) % N;
@@ -290,6 +292,25 @@ str_status ring_last(str_ctx* c, int n, const double* M, const double* ENew, con
   const double* El = kl == N - 1 ? ENew : E_of(c, kl);
   LCHK(c, STR_K_GRAM, launch_gemm64(M, El, Qout, c->R[f0] * c->R[f0], c->R[kl] * c->R[kl],
                                     c->R[kl + 1] * c->R[kl + 1], c->R[n], c->R[n + 1], base, s));
+  return STR_OK;
+}
+
+// Q_n = base + perm(M_n E_{n-1}) and, in the same kernel, the FP32 sweep
+// inverse of Q_n that factor_q would produce (FP32 slab arithmetic only)
+str_status ring_last_factor(str_ctx* c, int n, const double* M, const double* ENew, const double* base,
+                            double* Qout, cudaStream_t s) {
+  const int N = c->N;
+  const int f0 = (n + 1) % N, kl = (n + N - 1) % N;
+  const double* El = kl == N - 1 ? ENew : E_of(c, kl);
+  const int RRn = c->RR(n);
+  TRY(grow(c, c->lfac, (size_t)RRn * RRn * 8));
+  TRY(grow(c, c->invd, (size_t)RRn * 8));
+  TRY(grow(c, c->qf, (size_t)RRn * RRn * 4));
+  TRY(grow(c, c->fcount, 16));
+  LCHK(c, STR_K_FACTOR, launch_gemm64_factor(M, El, Qout, c->R[f0] * c->R[f0], c->R[kl] * c->R[kl],
+                                             c->R[kl + 1] * c->R[kl + 1], c->R[n], c->R[n + 1], base,
+                                             (float*)c->qf.p, (float*)c->lfac.p, (unsigned*)c->fcount.p,
+                                             c->d_status, c->d_pivot, s));
   return STR_OK;
 }
 
@@ -330,7 +351,10 @@ str_status solve_rows(str_ctx* c, const double* Qm, int n, const double* Pm, int
 // captured update becomes a graph with two branches per mode
 str_status fork_side(str_ctx* c, cudaStream_t s) {
   if (!c->side) {
-    STR_CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    // the Q-side chain is the critical path of a mode: highest stream priority
+    int lo = 0, hi = 0;
+    STR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    STR_CUDA_TRY(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi));
     STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   }
@@ -351,13 +375,16 @@ str_status join_side(str_ctx* c, cudaStream_t s) {
 }
 
 // third stream: forms M for the next mode from the side stream's current point
-str_status fork_side2(str_ctx* c) {
+// (or, at the start of a step, the slab transpose from the caller's stream)
+str_status fork_side2(str_ctx* c, cudaStream_t from = nullptr) {
   if (!c->side2) {
-    STR_CUDA_TRY(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+    int lo = 0, hi = 0;
+    STR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    STR_CUDA_TRY(cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, hi));
     STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming));
     STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
   }
-  STR_CUDA_TRY(cudaEventRecord(c->ev_fork2, c->side));
+  STR_CUDA_TRY(cudaEventRecord(c->ev_fork2, from ? from : c->side));
   STR_CUDA_TRY(cudaStreamWaitEvent(c->side2, c->ev_fork2, 0));
   c->side2_used = true;
   return STR_OK;
@@ -485,6 +512,26 @@ void reset_chains(str_ctx* c) {
   for (auto& e : c->chains) e.valid = false;
 }
 
+// Stage 1 of mode 1 (contracted mode 2) needs that mode contiguous: the slab
+// with its two fastest modes swapped, made once per slab.  *ok = false when the
+// tensor-core path cannot take the slab.
+str_status ensure_transposed(str_ctx* c, const SlabView& v, cudaStream_t s, bool* ok) {
+  *ok = false;
+  if (v.xtype != XT_F32 && v.xtype != XT_BF16) return STR_OK;
+  int64_t E = 1;
+  for (int j = 0; j < c->N; ++j) E *= v.dim[j];
+  const size_t es = v.xtype == XT_BF16 ? 2 : 4;
+  if (((size_t)v.dim[1] * es) % 16 != 0 || E / (v.dim[0] * v.dim[1]) > 65535) return STR_OK;
+  if (c->tc_xt_src != v.X) {
+    TRY(grow(c, c->tc_xt, (size_t)E * es));
+    LCHK(c, STR_K_OTHER, launch_transpose01(v.X, c->tc_xt.p, v.xtype, (int)v.dim[0], (int)v.dim[1],
+                                            E / (v.dim[0] * v.dim[1]), s));
+    c->tc_xt_src = v.X;
+  }
+  *ok = true;
+  return STR_OK;
+}
+
 // Dense FP32-compute MTTKRP on the tensor cores (two stages, see k_tc.cu).
 // cores: FP32 cores as seen in the step (temporal = the slab's rows);
 // G64k: FP64 master of the contracted core k.  Returns false (and does
@@ -500,15 +547,9 @@ str_status mttkrp_tc(str_ctx* c, const SlabView& v, int n, const void* const* co
   const void* Xa = v.X;
   if (v.xtype != XT_F32 && v.xtype != XT_BF16) return STR_OK;
   if (k == 1) {
-    // stage 1 needs the contracted mode contiguous: swap the two fastest modes once per slab
-    const size_t es = v.xtype == XT_BF16 ? 2 : 4;
-    if ((K * es) % 16 != 0 || E / (v.dim[0] * v.dim[1]) > 65535) return STR_OK;
-    if (c->tc_xt_src != v.X) {
-      TRY(grow(c, c->tc_xt, (size_t)E * es));
-      LCHK(c, STR_K_OTHER, launch_transpose01(v.X, c->tc_xt.p, v.xtype, (int)v.dim[0], (int)v.dim[1],
-                                              E / (v.dim[0] * v.dim[1]), s));
-      c->tc_xt_src = v.X;
-    }
+    bool ok = false;
+    TRY(ensure_transposed(c, v, s, &ok));
+    if (!ok) return STR_OK;
     Xa = c->tc_xt.p;
   }
   if (!tc_supported(K, v.xtype, Xa)) return STR_OK;
@@ -878,6 +919,12 @@ str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
     TRY(grow(c, c->mbuf[1], (size_t)RRmax * RRmax * 8));
   }
   bool have_M = false;           // M of the mode about to run is already formed
+  // the slab transpose for mode 1's stage 1 runs beside the temporal mode
+  if (c->compute == 1 && c->opt.mttkrp_path == 0 && c->opt.sweeps > 0) {
+    TRY(fork_side2(c, s));
+    bool ok = false;
+    TRY(ensure_transposed(c, v, c->side2, &ok));
+  }
   const int nmodes = c->opt.sweeps * N;
   int step_i = 0;                // position in the mode sequence T, 0, 1, .., N-2, T, ..
   auto mode_at = [&](int i) { return (i % N) == 0 ? N - 1 : (i % N) - 1; };
@@ -885,6 +932,7 @@ str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
   // ahead), Q_n = base + perm(M_n E_{n-1}), its factor; then M of the next mode
   auto side_branch = [&](int n, const double* base, double* Qout, int RRn) -> str_status {
     cudaStream_t s2 = c->side;
+    bool factored = false;
     if (last == N - 1)
       LCHKS(c, STR_K_GRAM, s2, launch_core_gram(gn64, tn, c->R[N - 1], c->R[N], nullptr, (double*)c->enew.p, s2));
     else if (last >= 0)
@@ -892,25 +940,33 @@ str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
                                                 c->R[last + 1], nullptr, c->E[last][1 - c->cur[last]], s2));
     const double* enew = (const double*)c->enew.p;
     const double* ENew = (n == N - 1) ? nullptr : enew;
-    if (N == 3 || (n == N - 1 && last < 0)) {
-      // first temporal mode of the step (E_new of this step not formed yet) or N = 3
-      TRY(ring_Q(c, n, ENew, base, Qout, s2));
-    } else {
-      const double* M = nullptr;
-      if (!have_M) TRY(ring_prefix(c, n, ENew, (double*)c->mbuf[n & 1].p, &M, s2));
-      else M = (const double*)c->mbuf[n & 1].p;
-      TRY(ring_last(c, n, M, enew, base, Qout, s2));
+    const bool full_ring = N == 3 || (n == N - 1 && last < 0);
+    // M of this mode (if not formed ahead), slot = position parity
+    const double* M = nullptr;
+    if (!full_ring) {
+      if (!have_M) TRY(ring_prefix(c, n, ENew, (double*)c->mbuf[step_i & 1].p, &M, s2));
+      else M = (const double*)c->mbuf[step_i & 1].p;
     }
     have_M = false;
     if (N >= 4 && step_i + 1 < nmodes) {
-      // M of the next mode: needs every E but the one of the core updated now
+      // M of the next mode on the third stream: it needs every E but the one of
+      // the core updated in this mode, all formed by now
       const int nx = mode_at(step_i + 1);
       TRY(fork_side2(c));
       const double* Mx = nullptr;
-      TRY(ring_prefix(c, nx, enew, (double*)c->mbuf[nx & 1].p, &Mx, c->side2));
+      TRY(ring_prefix(c, nx, enew, (double*)c->mbuf[(step_i + 1) & 1].p, &Mx, c->side2));
       have_M = true;
     }
-    TRY(factor_q(c, Qout, RRn, s2));
+    if (full_ring) {
+      // first temporal mode of the step (E_new of this step not formed yet) or N = 3
+      TRY(ring_Q(c, n, ENew, base, Qout, s2));
+    } else if (c->compute == 1) {
+      TRY(ring_last_factor(c, n, M, enew, base, Qout, s2));
+      factored = true;
+    } else {
+      TRY(ring_last(c, n, M, enew, base, Qout, s2));
+    }
+    if (!factored) TRY(factor_q(c, Qout, RRn, s2));
     return STR_OK;
   };
   for (int sw = 0; sw < c->opt.sweeps; ++sw) {
@@ -1007,7 +1063,7 @@ str_status str_step_graph(str_ctx* c, SlabView& v, int64_t count, size_t es, cud
     return str_step(c, v, s);
   }
   cudaGraphExec_t exec = nullptr;
-  ce = cudaGraphInstantiate(&exec, graph, 0);
+  ce = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (ce != cudaSuccess) return from_cuda(ce, "cudaGraphInstantiate");
   c->graphs.push_back({parity, tn, v.xtype, c->gen, exec, c->launches});

@@ -57,63 +57,6 @@ cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double*
 }
 
 // ---------------------------------------------------------------------------
-// small FP64 GEMM: 8x8 output tile per 64-thread CTA, A rows and B columns of
-// the tile staged in shared memory (K <= 256); optional ring-permute epilogue
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ A,
-                                                     const double* __restrict__ B,
-                                                     double* __restrict__ C, int M, int K, int N,
-                                                     int pRa, int pRb, const double* __restrict__ base) {
-  PDL_ENTRY();
-  extern __shared__ double gsm[];
-  double* sA = gsm;            // 8 x K
-  double* sB = gsm + 8 * K;    // K x 8
-  __shared__ double red[4][64];
-  const int r0 = blockIdx.y * 8, c0 = blockIdx.x * 8;
-  for (int e = threadIdx.x; e < 8 * K; e += 256) {
-    const int r = e / K, k = e % K;
-    sA[e] = (r0 + r < M) ? A[(int64_t)(r0 + r) * K + k] : 0.0;
-    const int kk = e / 8, c = e % 8;
-    sB[e] = (c0 + c < N) ? B[(int64_t)kk * N + c0 + c] : 0.0;
-  }
-  __syncthreads();
-  // 64 outputs x 4 slices of K; slices summed in a fixed order
-  const int o = threadIdx.x & 63, q = threadIdx.x >> 6;
-  const double* a = sA + (o >> 3) * K;
-  const double* b = sB + (o & 7);
-  double s0 = 0.0;
-  for (int k = q; k < K; k += 4) s0 = fma(a[k], b[k * 8], s0);
-  red[q][o] = s0;
-  __syncthreads();
-  if (q != 0) return;
-  const int col = c0 + (o & 7);
-  const int row = r0 + (o >> 3);
-  if (row >= M || col >= N) return;
-  const double s = (red[0][o] + red[1][o]) + (red[2][o] + red[3][o]);
-  if (pRa <= 0) {
-    C[(int64_t)row * N + col] = s;
-  } else {
-    // row = b + Rb b', col = a + Ra a'  ->  Q[a + Ra b][a' + Ra b']
-    const int bb = row % pRb, bp = row / pRb, aa = col % pRa, ap = col / pRa;
-    const int RR = pRa * pRb;
-    const int64_t qi = (int64_t)(aa + pRa * bb) * RR + (ap + pRa * bp);
-    C[qi] = (base ? base[qi] : 0.0) + s;
-  }
-}
-
-cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, int K, int N,
-                          int perm_Ra, int perm_Rb, const double* base, cudaStream_t s) {
-  dim3 grid((unsigned)ceil_div_i(N, 8), (unsigned)ceil_div_i(M, 8));
-  const size_t sm = (size_t)16 * K * sizeof(double);
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gemm64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  launch_k(gemm64_kernel, grid, 256, sm, s, A, B, C, M, K, N, perm_Ra, perm_Rb, base);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Inverse of an SPD matrix by the symmetric sweep (in-place Gauss-Jordan without
 // pivoting; its pivots are the Schur-complement pivots of the LDL^T / Cholesky
 // factorisation).  256 threads as a 16 x 16 grid; thread (ty, tx) keeps the
@@ -122,16 +65,21 @@ cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, in
 // updates its entries: one barrier per pivot.  After n sweeps the matrix holds
 // -Q^{-1}.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+// fast reciprocal for the FP32 inverse (CUDA's approximate division, <= 2 ulp):
+// the FP32 inverse only seeds an FP64-residual refinement
+__device__ __forceinline__ float recip_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip_fast(double x) { return __drcp_rn(x); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
-template <typename T, int B>
-__global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __restrict__ Q, int n,
-                                                            T* __restrict__ W, int* status,
-                                                            double* pivot_ratio) {
-  PDL_ENTRY();
+// Q read through ldq (FP64 or FP32 source; the fused form reads an FP32 copy
+// written by other CTAs of the same kernel, past L1)
+__device__ __forceinline__ float ldq(const float* p, bool cg) { return cg ? __ldcg(p) : *p; }
+__device__ __forceinline__ double ldq(const double* p, bool cg) { return cg ? __ldcg(p) : *p; }
+
+template <typename T, int B, typename SRC>
+__device__ __forceinline__ void sweep_body(const SRC* __restrict__ Q, int n, T* __restrict__ W, int* status,
+                                           double* pivot_ratio, bool cg) {
   __shared__ T col[2][16 * B];
   __shared__ T qd[16 * B];
   __shared__ T pivs[16 * B];   // pivot k as met (before any replacement)
@@ -143,9 +91,9 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
 #pragma unroll
     for (int j = 0; j < B; ++j) {
       const int r = ty + 16 * i, c = tx + 16 * j;
-      a[i][j] = (r < n && c < n) ? (T)Q[(int64_t)r * n + c] : (T)0;
+      a[i][j] = (r < n && c < n) ? (T)ldq(Q + (int64_t)r * n + c, cg) : (T)0;
     }
-  for (int k = tid; k < n; k += 256) qd[k] = (T)Q[(int64_t)k * n + k];
+  for (int k = tid; k < n; k += 256) qd[k] = (T)ldq(Q + (int64_t)k * n + k, cg);
   __syncthreads();
   if (tid < 32) {
     T mx = 0;
@@ -179,7 +127,7 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
       T piv = col[par][k];
       if (tid == 0) pivs[k] = piv;
       if (!(piv > tol)) piv = (T)1;   // recorded as singular after the loop
-      const T rcp = recip(piv);
+      const T rcp = recip_fast(piv);
       // generic update a_ij -= a_ik a_kj / a_kk for every owned entry, then the
       // owners of row k / column k overwrite theirs (row k and column k scale
       // by 1/a_kk, the pivot becomes -1/a_kk)
@@ -236,14 +184,136 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
   }
 }
 
+template <typename T, int B>
+__global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __restrict__ Q, int n,
+                                                            T* __restrict__ W, int* status,
+                                                            double* pivot_ratio) {
+  PDL_ENTRY();
+  sweep_body<T, B, double>(Q, n, W, status, pivot_ratio, false);
+}
+
+// ---------------------------------------------------------------------------
+// small FP64 GEMM: 8x8 output tile per CTA, A rows and B columns of the tile
+// staged in shared memory (K <= 256); optional ring-permute epilogue.
+// SB > 0 (fused factor): the permuted result Q is also written as an FP32 copy
+// Qf, and the last CTA to finish (device-scope counter, wrapping to zero)
+// runs the FP32 sweep inverse W = Q^{-1} on it -- one kernel boundary less on
+// the critical path of a mode update.  The other CTAs exit without waiting.
+// ---------------------------------------------------------------------------
+struct FuseFactor {
+  float* Qf = nullptr;
+  float* W = nullptr;
+  unsigned* counter = nullptr;
+  int* status = nullptr;
+  double* pivot_ratio = nullptr;
+};
+
+template <int SB>
+__global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ A,
+                                                     const double* __restrict__ B,
+                                                     double* __restrict__ C, int M, int K, int N,
+                                                     int pRa, int pRb, const double* __restrict__ base,
+                                                     FuseFactor ff) {
+  PDL_ENTRY();
+  extern __shared__ double gsm[];
+  double* sA = gsm;            // 8 x K
+  double* sB = gsm + 8 * K;    // K x 8
+  __shared__ double red[4][64];
+  __shared__ int s_last;
+  const int r0 = blockIdx.y * 8, c0 = blockIdx.x * 8;
+  for (int e = threadIdx.x; e < 8 * K; e += 256) {
+    const int r = e / K, k = e % K;
+    sA[e] = (r0 + r < M) ? A[(int64_t)(r0 + r) * K + k] : 0.0;
+    const int kk = e / 8, c = e % 8;
+    sB[e] = (c0 + c < N) ? B[(int64_t)kk * N + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  // 64 outputs x 4 slices of K; slices summed in a fixed order
+  const int o = threadIdx.x & 63, q = threadIdx.x >> 6;
+  const double* a = sA + (o >> 3) * K;
+  const double* b = sB + (o & 7);
+  double s0 = 0.0;
+  for (int k = q; k < K; k += 4) s0 = fma(a[k], b[k * 8], s0);
+  red[q][o] = s0;
+  __syncthreads();
+  const int col = c0 + (o & 7);
+  const int row = r0 + (o >> 3);
+  if (q == 0 && row < M && col < N) {
+    const double s = (red[0][o] + red[1][o]) + (red[2][o] + red[3][o]);
+    if (pRa <= 0) {
+      C[(int64_t)row * N + col] = s;
+    } else {
+      // row = b + Rb b', col = a + Ra a'  ->  Q[a + Ra b][a' + Ra b']
+      const int bb = row % pRb, bp = row / pRb, aa = col % pRa, ap = col / pRa;
+      const int RR = pRa * pRb;
+      const int64_t qi = (int64_t)(aa + pRa * bb) * RR + (ap + pRa * bp);
+      const double v = (base ? base[qi] : 0.0) + s;
+      C[qi] = v;
+      if (SB > 0) ff.Qf[qi] = (float)v;
+    }
+  }
+  if constexpr (SB > 0) {
+    __threadfence();
+    __syncthreads();
+    // atomicInc wraps to 0 after the last CTA: the counter is ready for the next launch
+    const unsigned total = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) s_last = atomicInc(ff.counter, total - 1) == total - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    sweep_body<float, SB, float>(ff.Qf, pRa * pRb, ff.W, ff.status, ff.pivot_ratio, true);
+  }
+}
+
+cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, int K, int N,
+                          int perm_Ra, int perm_Rb, const double* base, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div_i(N, 8), (unsigned)ceil_div_i(M, 8));
+  const size_t sm = (size_t)16 * K * sizeof(double);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gemm64_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  launch_k(gemm64_kernel<0>, grid, 256, sm, s, A, B, C, M, K, N, perm_Ra, perm_Rb, base, FuseFactor());
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm64_factor(const double* A, const double* B, double* Qout, int M, int K, int N, int Ra,
+                                 int Rb, const double* base, float* Qf, float* W32, unsigned* counter,
+                                 int* status, double* pivot_ratio, cudaStream_t s) {
+  const int n = Ra * Rb;
+  void (*k)(const double*, const double*, double*, int, int, int, int, int, const double*, FuseFactor) = nullptr;
+  if (n <= 16) k = gemm64_kernel<1>;
+  else if (n <= 32) k = gemm64_kernel<2>;
+  else if (n <= 64) k = gemm64_kernel<4>;
+  else if (n <= 112) k = gemm64_kernel<7>;
+  else if (n <= 160) k = gemm64_kernel<10>;
+  else return cudaErrorInvalidValue;
+  dim3 grid((unsigned)ceil_div_i(N, 8), (unsigned)ceil_div_i(M, 8));
+  const size_t sm = (size_t)16 * K * sizeof(double);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  FuseFactor ff;
+  ff.Qf = Qf;
+  ff.W = W32;
+  ff.counter = counter;
+  ff.status = status;
+  ff.pivot_ratio = pivot_ratio;
+  launch_k(k, grid, 256, sm, s, A, B, Qout, M, K, N, Ra, Rb, base, ff);
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t launch_sweep(const double* Q, int n, T* W, int* status, double* pivot_ratio, cudaStream_t s) {
-  if (n <= 16) launch_k(sweep_inverse_kernel<T, 1>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
-  else if (n <= 32) launch_k(sweep_inverse_kernel<T, 2>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
-  else if (n <= 64) launch_k(sweep_inverse_kernel<T, 4>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
-  else if (n <= 112) launch_k(sweep_inverse_kernel<T, 7>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
-  else if (n <= 160) launch_k(sweep_inverse_kernel<T, 10>, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
+  void (*k)(const double*, int, T*, int*, double*) = nullptr;
+  if (n <= 16) k = sweep_inverse_kernel<T, 1>;
+  else if (n <= 32) k = sweep_inverse_kernel<T, 2>;
+  else if (n <= 64) k = sweep_inverse_kernel<T, 4>;
+  else if (n <= 112) k = sweep_inverse_kernel<T, 7>;
+  else if (n <= 160) k = sweep_inverse_kernel<T, 10>;
   else return cudaErrorInvalidValue;
+  launch_k(k, 1, 256, 0, s, Q, n, W, status, pivot_ratio);
   return cudaGetLastError();
 }
 
@@ -427,27 +497,45 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
   double* gs = Qs + (q_in_smem ? n * n : 0);                                  // n: current solution
   float* vf = (float*)(gs + n);                                               // n: right-hand side (FP32)
   const int tid = threadIdx.x;
-  for (int e = tid; e < n * n; e += blockDim.x) cp_async4(&Wm[e], &Wg[e]);
-  if (q_in_smem)
-    for (int e = tid; e < n * n; e += blockDim.x) cp_async8(&Qs[e], &Qg[e]);
-  cp_async_wait_all();
-  __syncthreads();
+  // stage W32 and Q (16-byte copies when the sizes allow); completion is awaited
+  // only before the first use, so it overlaps the first right-hand side's loads
+  if ((n & 3) == 0 && (((uintptr_t)Wg | (uintptr_t)Qg) & 15) == 0) {
+    for (int e = 4 * tid; e < n * n; e += 4 * blockDim.x) cp_async16(&Wm[e], &Wg[e]);
+    if (q_in_smem)
+      for (int e = 2 * tid; e < n * n; e += 2 * blockDim.x) cp_async16(&Qs[e], &Qg[e]);
+  } else {
+    for (int e = tid; e < n * n; e += blockDim.x) cp_async4(&Wm[e], &Wg[e]);
+    if (q_in_smem)
+      for (int e = tid; e < n * n; e += blockDim.x) cp_async8(&Qs[e], &Qg[e]);
+  }
+  cp_async_commit();
   const double* Q = q_in_smem ? Qs : Qg;
   const int c = tid;
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     double pc = 0.0;
     if (c < n) {
       if (ps.part) {
-        // P = base + sum of the split partials, in split order; stored, then solved
+        // P = base + sum of the split partials, in split order; stored, then solved.
+        // Loads are issued eight at a time ahead of the (ordered) additions.
         pc = ps.base ? ps.base[r * n + c] : 0.0;
         double acc = 0.0;
-        for (int k = 0; k < ps.splits; ++k) acc += (double)ps.part[(int64_t)k * rows * n + r * n + c];
+        const float* pp = ps.part + r * n + c;
+        const int64_t st = rows * n;
+        for (int k0 = 0; k0 < ps.splits; k0 += 8) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = (k0 + u < ps.splits) ? pp[(int64_t)(k0 + u) * st] : 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (k0 + u < ps.splits) acc += (double)v[u];
+        }
         pc += acc;
         ps.pout[r * n + c] = pc;
       } else {
         pc = P[r * n + c];
       }
     }
+    cp_async_wait_all();
     if (c < n) vf[c] = (float)pc;
     double g = 0.0;
     __syncthreads();

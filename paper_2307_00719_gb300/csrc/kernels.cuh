@@ -53,6 +53,12 @@ cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double*
                              cudaStream_t s);
 // C = A(MxK) B(KxN), FP64.  If perm_Ra > 0 the result W (rows (b + Rb b'), cols
 // (a + Ra a')) is scattered into Q[(a + Ra b), (a' + Ra b')] = base + W (ring epilogue).
+// ring-product GEMM with the permuting epilogue, fused with the FP32 sweep
+// inverse of its result (Qout = base + perm(A B); Qf = FP32 copy; W32 = Qf^{-1});
+// counter: one device word, zero between launches
+cudaError_t launch_gemm64_factor(const double* A, const double* B, double* Qout, int M, int K, int N, int Ra,
+                                 int Rb, const double* base, float* Qf, float* W32, unsigned* counter,
+                                 int* status, double* pivot_ratio, cudaStream_t s);
 cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, int K, int N,
                           int perm_Ra, int perm_Rb, const double* base, cudaStream_t s);
 
