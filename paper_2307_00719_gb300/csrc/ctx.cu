@@ -106,7 +106,8 @@ struct str_ctx {
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   bool side2_used = false;
   DevBuf mbuf[2];
-  DevBuf qf, fcount, ring2, ring3;   // FP32 copy of Q and the last-CTA counter of the fused ring GEMM + factor
+  DevBuf qf, qlo, fcount, ring2, ring3;
+  const double* qsplit_of = nullptr;   // the Q whose FP32 pair (qf, qlo) is current   // FP32 copy of Q and the last-CTA counter of the fused ring GEMM + factor
 
   int RR(int n) const { return R[n] * R[n + 1]; }
   int64_t m() const { return opt.m; }
@@ -243,7 +244,17 @@ str_status ring_Q(str_ctx* c, int n, const double* ENew, const double* base, dou
     const int Ncols = c->R[k + 1] * c->R[k + 1];
     const bool last = (t == N - 2);
     if (last) {
-      LCHK(c, STR_K_GRAM, launch_gemm64(A, B, Qout, Mrows, Kc, Ncols, c->R[n], c->R[n + 1], base, s));
+      float* qh = nullptr;
+      float* ql = nullptr;
+      if (c->compute == 1) {
+        const int RRn = c->RR(n);
+        TRY(grow(c, c->qf, (size_t)RRn * RRn * 4));
+        TRY(grow(c, c->qlo, (size_t)RRn * RRn * 4));
+        qh = (float*)c->qf.p;
+        ql = (float*)c->qlo.p;
+      }
+      LCHK(c, STR_K_GRAM, launch_gemm64(A, B, Qout, Mrows, Kc, Ncols, c->R[n], c->R[n + 1], base, s, qh, ql));
+      c->qsplit_of = qh ? Qout : nullptr;
     } else {
       LCHK(c, STR_K_GRAM, launch_gemm64(A, B, bufs[bi], Mrows, Kc, Ncols, 0, 0, nullptr, s));
       A = bufs[bi];
@@ -306,11 +317,13 @@ str_status ring_last_factor(str_ctx* c, int n, const double* M, const double* EN
   TRY(grow(c, c->lfac, (size_t)RRn * RRn * 8));
   TRY(grow(c, c->invd, (size_t)RRn * 8));
   TRY(grow(c, c->qf, (size_t)RRn * RRn * 4));
+  TRY(grow(c, c->qlo, (size_t)RRn * RRn * 4));
   TRY(grow(c, c->fcount, 16));
   LCHK(c, STR_K_FACTOR, launch_gemm64_factor(M, El, Qout, c->R[f0] * c->R[f0], c->R[kl] * c->R[kl],
                                              c->R[kl + 1] * c->R[kl + 1], c->R[n], c->R[n + 1], base,
-                                             (float*)c->qf.p, (float*)c->lfac.p, (unsigned*)c->fcount.p,
-                                             c->d_status, c->d_pivot, s));
+                                             (float*)c->qf.p, (float*)c->qlo.p, (float*)c->lfac.p,
+                                             (unsigned*)c->fcount.p, c->d_status, c->d_pivot, s));
+  c->qsplit_of = Qout;
   return STR_OK;
 }
 
@@ -331,7 +344,17 @@ str_status factor_q(str_ctx* c, const double* Qm, int n, cudaStream_t s) {
 
 str_status apply_q(str_ctx* c, const double* Qm, int n, const double* Pm, int64_t rows, double* out64,
                    float* out32, cudaStream_t s, const PartialSum* ps = nullptr) {
-  if (c->compute == 1) {
+  if (c->compute == 1 && apply_df_supported(n)) {
+    // the FP32 pair of Q: from the GEMM that formed Q, else split here
+    if (c->qsplit_of != Qm) {
+      TRY(grow(c, c->qf, (size_t)n * n * 4));
+      TRY(grow(c, c->qlo, (size_t)n * n * 4));
+      LCHK(c, STR_K_SOLVE, launch_split_pair(Qm, (int64_t)n * n, (float*)c->qf.p, (float*)c->qlo.p, s));
+      c->qsplit_of = Qm;
+    }
+    LCHK(c, STR_K_SOLVE, launch_apply_df((const float*)c->lfac.p, (const float*)c->qf.p, (const float*)c->qlo.p, n,
+                                         Pm, rows, out64, out32, ps && ps->part ? ps : nullptr, c->d_status, s));
+  } else if (c->compute == 1) {
     LCHK(c, STR_K_SOLVE, launch_apply_mixed((const float*)c->lfac.p, Qm, n, Pm, rows, 1, out64, out32,
                                             ps && ps->part ? ps : nullptr, s));
   } else {
@@ -777,6 +800,7 @@ double sketch_wscale(const str_ctx* c, int n, const int64_t* dims) {
 
 // rSTR initialisation stage (Algs. 7-9, lines 2-19): draws at tau = 0, sketched P_n, Q_n
 str_status rstr_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
+  c->qsplit_of = nullptr;
   const int N = c->N;
   const int64_t m = c->opt.m;
   const bool lev = c->opt.sketch == STR_SKETCH_LEVERAGE && c->opt.rescale;
@@ -846,6 +870,7 @@ str_status rstr_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
 
 // exact initialisation (Alg. 4 lines 2-6): P_n = X0_[n] G^{!=n}_[2], Q_n = ring with Z_N of G_N^init
 str_status str_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
+  c->qsplit_of = nullptr;
   const int N = c->N;
   const int RRN = c->RR(N - 1);
   TRY(grow(c, c->enew, (size_t)RRN * RRN * 8));
@@ -911,6 +936,7 @@ str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
   // then G_n = P_n Q_n^{-1} on the main stream.
   int last = -1;   // core whose Gram matrix is still to be formed (-1: none, N-1: temporal)
   reset_chains(c);
+  c->qsplit_of = nullptr;
   // ring prefixes M (Q_n = M_n E_{n-1}): M of the next mode is formed on a third
   // stream while the current mode factors; slot = mode parity
   const int RRmax = STR_MAXRR;
@@ -1075,6 +1101,7 @@ str_status str_step_graph(str_ctx* c, SlabView& v, int64_t count, size_t es, cud
 // rSTR step (Alg. 5; schedules of Algs. 7, 8, 9)
 // ---------------------------------------------------------------------------
 str_status rstr_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
+  c->qsplit_of = nullptr;
   const int N = c->N;
   const int64_t m = c->opt.m;
   const int64_t tn = v.dim[N - 1];
@@ -1300,6 +1327,7 @@ str_status str_init(str_ctx** out, const str_tensor* X0, const int* ranks, const
   SlabView v;
   if (st == STR_OK) st = take_slab(c, X0, &v, s);
   // TR-ALS-NE (Alg. 2) on X0: every core, including the temporal one, in turn
+  c->qsplit_of = nullptr;
   double prev = -1.0;
   for (int it = 0; st == STR_OK && it < o.init_max_it; ++it) {
     for (int n = 0; n < N && st == STR_OK; ++n) {

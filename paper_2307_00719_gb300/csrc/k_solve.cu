@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "ptx.cuh"
 
 // ---------------------------------------------------------------------------
 // core Gram: one thread per (c, c') pair with c <= c'; writes both halves
@@ -201,7 +202,8 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
 // the critical path of a mode update.  The other CTAs exit without waiting.
 // ---------------------------------------------------------------------------
 struct FuseFactor {
-  float* Qf = nullptr;
+  float* Qf = nullptr;    // Q as an FP32 pair Qf + Qlo (Qlo may be null)
+  float* Qlo = nullptr;
   float* W = nullptr;
   unsigned* counter = nullptr;
   int* status = nullptr;
@@ -249,7 +251,11 @@ __global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ 
       const int64_t qi = (int64_t)(aa + pRa * bb) * RR + (ap + pRa * bp);
       const double v = (base ? base[qi] : 0.0) + s;
       C[qi] = v;
-      if (SB > 0) ff.Qf[qi] = (float)v;
+      if (ff.Qf) {
+        const float hi = (float)v;
+        ff.Qf[qi] = hi;
+        if (ff.Qlo) ff.Qlo[qi] = (float)(v - (double)hi);
+      }
     }
   }
   if constexpr (SB > 0) {
@@ -266,19 +272,21 @@ __global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ 
 }
 
 cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, int K, int N,
-                          int perm_Ra, int perm_Rb, const double* base, cudaStream_t s) {
+                          int perm_Ra, int perm_Rb, const double* base, cudaStream_t s, float* Qhi, float* Qlo) {
   dim3 grid((unsigned)ceil_div_i(N, 8), (unsigned)ceil_div_i(M, 8));
   const size_t sm = (size_t)16 * K * sizeof(double);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(gemm64_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  launch_k(gemm64_kernel<0>, grid, 256, sm, s, A, B, C, M, K, N, perm_Ra, perm_Rb, base, FuseFactor());
+  FuseFactor ff;
+  if (perm_Ra > 0) { ff.Qf = Qhi; ff.Qlo = Qlo; }
+  launch_k(gemm64_kernel<0>, grid, 256, sm, s, A, B, C, M, K, N, perm_Ra, perm_Rb, base, ff);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemm64_factor(const double* A, const double* B, double* Qout, int M, int K, int N, int Ra,
-                                 int Rb, const double* base, float* Qf, float* W32, unsigned* counter,
+                                 int Rb, const double* base, float* Qf, float* Qlo, float* W32, unsigned* counter,
                                  int* status, double* pivot_ratio, cudaStream_t s) {
   const int n = Ra * Rb;
   void (*k)(const double*, const double*, double*, int, int, int, int, int, const double*, FuseFactor) = nullptr;
@@ -296,6 +304,7 @@ cudaError_t launch_gemm64_factor(const double* A, const double* B, double* Qout,
   }
   FuseFactor ff;
   ff.Qf = Qf;
+  ff.Qlo = Qlo;
   ff.W = W32;
   ff.counter = counter;
   ff.status = status;
@@ -576,6 +585,206 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
       if (out32) out32[r * n + c] = (float)g;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Refined solve for n <= 64 (even), one row of P per CTA at a time, 256
+// threads: thread (c, part) owns column c and the quarter part of every inner
+// sum.  W32 and Q = Qh + Ql (an FP32 pair carrying Q to about 2^-48) are
+// staged by bulk copies; the right-hand side is formed from the split
+// partials as in solve_refine_kernel.
+//   g  = p W32                           (FP32)
+//   r  = p - g Q                         (double-FP32 arithmetic: exact products
+//                                         and error-free sums, Dekker / Knuth)
+//   g += r W32                           (FP32), result rounded to FP64 / FP32
+// The FP64 pipe is not used in the inner loops.
+// ---------------------------------------------------------------------------
+struct ApplyDF {
+  const float* W = nullptr;
+  const float* Qh = nullptr;
+  const float* Ql = nullptr;
+  int n = 0;
+  int64_t rows = 0;
+  const double* P = nullptr;   // right-hand sides when ps.part is null
+  PartialSum ps;
+  double* out64 = nullptr;
+  float* out32 = nullptr;
+  int* status = nullptr;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
+  PDL_ENTRY();
+  extern __shared__ __align__(16) unsigned char sma[];
+  const int n = a.n, nn = n * n;
+  float* Wm = (float*)sma;                  // n x n
+  float* Qh = Wm + nn;                      // n x n
+  float* Ql = Qh + nn;                      // n x n
+  double* pd = (double*)(Ql + nn);          // n: right-hand side (FP64)
+  float* vf = (float*)(pd + n);             // n: FP32 vector of the current product
+  float* red = vf + n;                      // 4 x n partial sums (x2 for pairs)
+  __shared__ __align__(8) uint64_t bar;
+  const int tid = threadIdx.x, c = tid & 63, part = tid >> 6;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(&bar, 3u * nn * 4u);
+    bulk_g2s(Wm, a.W, nn * 4, &bar);
+    bulk_g2s(Qh, a.Qh, nn * 4, &bar);
+    bulk_g2s(Ql, a.Ql, nn * 4, &bar);
+  }
+  bool staged = false;
+  const int k0 = part * ((n + 3) / 4), k1 = min(n, k0 + (n + 3) / 4);
+  for (int64_t r = blockIdx.x; r < a.rows; r += gridDim.x) {
+    // right-hand side: base + partials summed in split order (or P), by part 0
+    if (part == 0 && c < n) {
+      double pc;
+      if (a.ps.part) {
+        pc = a.ps.base ? a.ps.base[r * n + c] : 0.0;
+        double acc = 0.0;
+        const float* pp = a.ps.part + r * n + c;
+        const int64_t st = a.rows * n;
+        for (int s0 = 0; s0 < a.ps.splits; s0 += 8) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = (s0 + u < a.ps.splits) ? pp[(int64_t)(s0 + u) * st] : 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (s0 + u < a.ps.splits) acc += (double)v[u];
+        }
+        pc += acc;
+        a.ps.pout[r * n + c] = pc;
+      } else {
+        pc = a.P[r * n + c];
+      }
+      pd[c] = pc;
+      vf[c] = (float)pc;
+    }
+    if (!staged) {
+      const bool ok = mbar_wait(&bar, 0, 2000000000ull);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(a.status, DEV_ERR_TIMEOUT);
+        return;
+      }
+      staged = true;
+    } else {
+      __syncthreads();
+    }
+    // g = p W32
+    float g = 0.f;
+    if (c < n) {
+      float s0 = 0.f, s1 = 0.f;
+      int k = k0;
+      for (; k + 1 < k1; k += 2) {
+        s0 = fmaf(vf[k], Wm[k * n + c], s0);
+        s1 = fmaf(vf[k + 1], Wm[(k + 1) * n + c], s1);
+      }
+      if (k < k1) s0 = fmaf(vf[k], Wm[k * n + c], s0);
+      red[part * n + c] = s0 + s1;
+    }
+    __syncthreads();
+    if (part == 0 && c < n) {
+      g = (red[c] + red[n + c]) + (red[2 * n + c] + red[3 * n + c]);
+      vf[c] = g;                 // g, read by every part below
+    }
+    __syncthreads();
+    // s = g Q in pair arithmetic over this part's k
+    if (c < n) {
+      float sh = 0.f, sl = 0.f;
+      for (int k = k0; k < k1; ++k) {
+        const float gk = vf[k], qh = Qh[k * n + c], ql = Ql[k * n + c];
+        const float ph = gk * qh;
+        float pl = fmaf(gk, qh, -ph);     // exact: gk qh = ph + pl
+        pl = fmaf(gk, ql, pl);
+        float t, e;
+        two_sum(sh, ph, t, e);
+        sh = t;
+        sl += e + pl;
+      }
+      red[part * n + c] = sh;
+      red[4 * n + part * n + c] = sl;
+    }
+    __syncthreads();
+    float rfl = 0.f;
+    if (part == 0 && c < n) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s += (double)red[q * n + c] + (double)red[4 * n + q * n + c];
+      rfl = (float)(pd[c] - s);
+    }
+    __syncthreads();
+    if (part == 0 && c < n) vf[c] = rfl;
+    __syncthreads();
+    // g += r W32
+    if (c < n) {
+      float s0 = 0.f, s1 = 0.f;
+      int k = k0;
+      for (; k + 1 < k1; k += 2) {
+        s0 = fmaf(vf[k], Wm[k * n + c], s0);
+        s1 = fmaf(vf[k + 1], Wm[(k + 1) * n + c], s1);
+      }
+      if (k < k1) s0 = fmaf(vf[k], Wm[k * n + c], s0);
+      red[part * n + c] = s0 + s1;
+    }
+    __syncthreads();
+    if (part == 0 && c < n) {
+      const float d = (red[c] + red[n + c]) + (red[2 * n + c] + red[3 * n + c]);
+      const double gv = (double)g + (double)d;
+      if (a.out64) a.out64[r * n + c] = gv;
+      if (a.out32) a.out32[r * n + c] = (float)gv;
+    }
+    __syncthreads();
+  }
+  if (!staged) {   // no row: the bulk copies still complete before exit
+    mbar_wait(&bar, 0, 2000000000ull);
+  }
+}
+
+size_t apply_df_smem(int n) { return (size_t)3 * n * n * 4 + (size_t)n * 8 + (size_t)n * 4 + (size_t)8 * n * 4; }
+
+// Q (FP64) -> FP32 pair (hi, lo)
+__global__ void split_pair_kernel(const double* __restrict__ Q, int64_t count, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  PDL_ENTRY();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = Q[i];
+    const float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+  }
+}
+
+cudaError_t launch_split_pair(const double* Q, int64_t count, float* hi, float* lo, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152));
+  launch_k(split_pair_kernel, blocks, 256, 0, s, Q, count, hi, lo);
+  return cudaGetLastError();
+}
+
+bool apply_df_supported(int n) { return n >= 2 && n <= 64 && (n % 2) == 0; }
+
+cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, int n, const double* P, int64_t rows,
+                            double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (!apply_df_supported(n)) return cudaErrorInvalidValue;
+  const size_t sm = apply_df_smem(n);
+  cudaError_t e = cudaFuncSetAttribute(apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  ApplyDF a;
+  a.W = W32; a.Qh = Qh; a.Ql = Ql; a.n = n; a.rows = rows; a.P = P;
+  if (ps) a.ps = *ps;
+  a.out64 = out64; a.out32 = out32; a.status = status;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 4));
+  launch_k(apply_df_kernel, (unsigned)blocks, 256, sm, s, a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_factor_mixed(const double* Q, int n, float* W32, int* status, double* pivot_ratio,

@@ -57,10 +57,11 @@ cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double*
 // inverse of its result (Qout = base + perm(A B); Qf = FP32 copy; W32 = Qf^{-1});
 // counter: one device word, zero between launches
 cudaError_t launch_gemm64_factor(const double* A, const double* B, double* Qout, int M, int K, int N, int Ra,
-                                 int Rb, const double* base, float* Qf, float* W32, unsigned* counter,
+                                 int Rb, const double* base, float* Qf, float* Qlo, float* W32, unsigned* counter,
                                  int* status, double* pivot_ratio, cudaStream_t s);
 cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, int K, int N,
-                          int perm_Ra, int perm_Rb, const double* base, cudaStream_t s);
+                          int perm_Ra, int perm_Rb, const double* base, cudaStream_t s, float* Qhi = nullptr,
+                          float* Qlo = nullptr);
 
 // ---------------------------------------------------------------------------
 // FP64 LDL^T of an SPD matrix (one CTA, register-blocked): unit lower L and 1/d, pivot check ->
@@ -87,6 +88,12 @@ cudaError_t launch_factor_mixed(const double* Q, int n, float* W32, int* status,
                                 cudaStream_t s);
 cudaError_t launch_apply_mixed(const float* W32, const double* Q, int n, const double* P, int64_t rows,
                                int iters, double* out64, float* out32, const PartialSum* ps, cudaStream_t s);
+// refined solve with Q as an FP32 pair (n <= 64, even); Q (FP64) -> pair
+bool apply_df_supported(int n);
+cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, int n, const double* P, int64_t rows,
+                            double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s);
+cudaError_t launch_split_pair(const double* Q, int64_t count, float* hi, float* lo, cudaStream_t s);
+
 cudaError_t launch_solve_mixed(const double* Q, int n, const double* P, int64_t rows, int iters,
                                float* L32, float* invd32, double* out64, float* out32, int* status,
                                double* pivot_ratio, cudaStream_t s);
