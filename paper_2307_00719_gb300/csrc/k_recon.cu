@@ -65,6 +65,31 @@ __global__ void chain_table_kernel(ChainArgs ca, int k0, int k1, int transpose, 
   }
 }
 
+// Two-core chain table: T[i_a + I_a i_b] = G_a(i_a) G_b(i_b), (r, c) at r + Rf c.
+// CTA per (tile of 16 i_a, i_b): both operands staged in shared memory, each
+// thread forms four entries.
+template <typename T>
+__global__ void __launch_bounds__(256) chain2_kernel(const T* __restrict__ Ga, const T* __restrict__ Gb, int Ia,
+                                                    int Rf, int Rm, int Rl, T* __restrict__ table) {
+  PDL_ENTRY();
+  __shared__ T sa[16 * STR_MAXRR];
+  __shared__ T sb[STR_MAXRR];
+  const int ib = blockIdx.y, ia0 = blockIdx.x * 16;
+  const int na = min(16, Ia - ia0);
+  const int sza = Rf * Rm, szb = Rm * Rl, szo = Rf * Rl;
+  for (int e = threadIdx.x; e < na * sza; e += 256) sa[e] = Ga[(int64_t)ia0 * sza + e];
+  for (int e = threadIdx.x; e < szb; e += 256) sb[e] = Gb[(int64_t)ib * szb + e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < na * szo; e += 256) {
+    const int t = e / szo, o = e - t * szo;
+    const int r = o % Rf, c = o / Rf;
+    const T* ga = sa + t * sza;
+    T v = 0;
+    for (int x = 0; x < Rm; ++x) v += ga[r + Rf * x] * sb[x + Rm * c];
+    table[((int64_t)ib * Ia + ia0 + t) * szo + o] = v;
+  }
+}
+
 cudaError_t launch_chain_table(const void* const* cores, int compute, const int* R, int N,
                                const int64_t* dims, int k0, int k1, int64_t /*row_off_last*/,
                                int transpose, void* table, cudaStream_t s) {
@@ -72,6 +97,16 @@ cudaError_t launch_chain_table(const void* const* cores, int compute, const int*
   for (int k = k0; k <= k1; ++k) J *= dims[k];
   const int64_t total = J * R[k0];
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, 152 * 16));
+  if (k1 == k0 + 1 && !transpose && R[k0] * R[k0 + 1] <= STR_MAXRR && R[k0 + 1] * R[k1 + 1] <= STR_MAXRR) {
+    dim3 grid((unsigned)((dims[k0] + 15) / 16), (unsigned)dims[k1]);
+    if (compute == 2)
+      launch_k(chain2_kernel<double>, grid, 256, 0, s, (const double*)cores[k0], (const double*)cores[k1],
+               (int)dims[k0], R[k0], R[k0 + 1], R[k1 + 1], (double*)table);
+    else
+      launch_k(chain2_kernel<float>, grid, 256, 0, s, (const float*)cores[k0], (const float*)cores[k1],
+               (int)dims[k0], R[k0], R[k0 + 1], R[k1 + 1], (float*)table);
+    return cudaGetLastError();
+  }
   ChainArgs ca;
   for (int k = 0; k < STR_MAXN; ++k) { ca.core[k] = k < N ? cores[k] : nullptr; ca.dim[k] = k < N ? dims[k] : 1; }
   for (int k = 0; k <= STR_MAXN; ++k) ca.R[k] = k <= N ? R[k] : 1;

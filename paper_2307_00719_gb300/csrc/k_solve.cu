@@ -626,7 +626,8 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
   float* Qh = Wm + nn;                      // n x n
   float* Ql = Qh + nn;                      // n x n
   double* pd = (double*)(Ql + nn);          // n: right-hand side (FP64)
-  float* vf = (float*)(pd + n);             // n: FP32 vector of the current product
+  double* pd4 = pd + n;                     // 4 x n: per-part sums of the split partials
+  float* vf = (float*)(pd4 + 4 * n);        // n: FP32 vector of the current product
   float* red = vf + n;                      // 4 x n partial sums (x2 for pairs)
   __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x, c = tid & 63, part = tid >> 6;
@@ -644,26 +645,35 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
   bool staged = false;
   const int k0 = part * ((n + 3) / 4), k1 = min(n, k0 + (n + 3) / 4);
   for (int64_t r = blockIdx.x; r < a.rows; r += gridDim.x) {
-    // right-hand side: base + partials summed in split order (or P), by part 0
+    // right-hand side: base + split partials (or P).  Part q sums the splits
+    // q, q + 4, ... in order; the four sums are added in part order.
+    if (c < n) {
+      if (a.ps.part) {
+        double acc = 0.0;
+        const float* pp = a.ps.part + r * n + c;
+        const int64_t st = a.rows * n;
+        for (int s0 = part; s0 < a.ps.splits; s0 += 32) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = (s0 + 4 * u < a.ps.splits) ? pp[(int64_t)(s0 + 4 * u) * st] : 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (s0 + 4 * u < a.ps.splits) acc += (double)v[u];
+        }
+        pd4[part * n + c] = acc;
+      } else if (part == 0) {
+        pd4[c] = a.P[r * n + c];
+      }
+    }
+    __syncthreads();
     if (part == 0 && c < n) {
       double pc;
       if (a.ps.part) {
         pc = a.ps.base ? a.ps.base[r * n + c] : 0.0;
-        double acc = 0.0;
-        const float* pp = a.ps.part + r * n + c;
-        const int64_t st = a.rows * n;
-        for (int s0 = 0; s0 < a.ps.splits; s0 += 8) {
-          float v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = (s0 + u < a.ps.splits) ? pp[(int64_t)(s0 + u) * st] : 0.f;
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (s0 + u < a.ps.splits) acc += (double)v[u];
-        }
-        pc += acc;
+        pc += ((pd4[c] + pd4[n + c]) + pd4[2 * n + c]) + pd4[3 * n + c];
         a.ps.pout[r * n + c] = pc;
       } else {
-        pc = a.P[r * n + c];
+        pc = pd4[c];
       }
       pd[c] = pc;
       vf[c] = (float)pc;
@@ -748,7 +758,7 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
   }
 }
 
-size_t apply_df_smem(int n) { return (size_t)3 * n * n * 4 + (size_t)n * 8 + (size_t)n * 4 + (size_t)8 * n * 4; }
+size_t apply_df_smem(int n) { return (size_t)3 * n * n * 4 + (size_t)5 * n * 8 + (size_t)n * 4 + (size_t)8 * n * 4; }
 
 // Q (FP64) -> FP32 pair (hi, lo)
 __global__ void split_pair_kernel(const double* __restrict__ Q, int64_t count, float* __restrict__ hi,

@@ -462,6 +462,7 @@ __global__ void transpose01_kernel(const T* __restrict__ in, T* __restrict__ out
 // Groups are combined in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
 constexpr int S2_CH = 32;       // combinations per chunk
+constexpr int S2_STAGES = 4;    // chunks in the shared-memory ring (S2_STAGES - 1 in flight)
 constexpr int S2_THREADS = 256;
 
 __device__ __forceinline__ void s2_issue(const Stage2Args& a, int form, int64_t in, int64_t qa, int nq,
@@ -524,10 +525,10 @@ __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
   const int PO = X * Yd;                   // outputs of one product
   const int G = max(1, S2_THREADS / PO);   // combination groups
   const int ystr = (RRk + 3) & ~3, tstr = (tsz + 3) & ~3;
-  // buffer b: Y rows at s2 + b * S2_CH * ystr, tables at s2 + 2 S2_CH ystr + b S2_CH tstr
+  // ring slot b: Y rows at s2 + b S2_CH ystr, tables at s2 + S2_STAGES S2_CH ystr + b S2_CH tstr
   float* const sY0 = s2;
-  float* const sT0 = s2 + 2 * S2_CH * ystr;
-  float* sRed = s2 + 2 * S2_CH * (ystr + tstr);   // G x PO, then PO (segment sums)
+  float* const sT0 = s2 + S2_STAGES * S2_CH * ystr;
+  float* sRed = s2 + S2_STAGES * S2_CH * (ystr + tstr);   // G x PO, then PO (segment sums)
   const bool vec = (RRk % 4 == 0) && (tsz % 4 == 0) && ((((uintptr_t)a.Y) & 15) == 0) &&
                    (form == 2 || ((((uintptr_t)(form == 0 ? a.TB : a.TA)) & 15) == 0));
   const int tid = threadIdx.x;
@@ -545,22 +546,34 @@ __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
     if (segA) e = min(e, (qa / a.Jlo + 1) * a.Jlo);
     return e;
   };
-  int64_t qa = q0;
-  if (qa < q1) {
-    s2_issue(a, form, in, qa, (int)(chunk_end(qa) - qa), ystr, tstr, tsz, sY0, sT0, vec);
+  // prologue: the first S2_STAGES - 1 chunks in flight
+  int64_t iq = q0;
+#pragma unroll
+  for (int st = 0; st < S2_STAGES - 1; ++st) {
+    if (iq < q1) {
+      const int64_t ie = chunk_end(iq);
+      s2_issue(a, form, in, iq, (int)(ie - iq), ystr, tstr, tsz, sY0 + st * S2_CH * ystr, sT0 + st * S2_CH * tstr, vec);
+      iq = ie;
+    }
+    cp_async_commit();
   }
-  cp_async_commit();
-  int buf = 0;
+  int64_t qa = q0;
+  int ci = 0;
   while (qa < q1) {
     const int64_t qe = chunk_end(qa);
     const int nq = (int)(qe - qa);
-    const int64_t qn = qe;
-    if (qn < q1) {
-      s2_issue(a, form, in, qn, (int)(chunk_end(qn) - qn), ystr, tstr, tsz, sY0 + (buf ^ 1) * S2_CH * ystr,
-               sT0 + (buf ^ 1) * S2_CH * tstr, vec);
+    const int buf = ci % S2_STAGES;
+    {  // chunk ci + S2_STAGES - 1 into the slot of chunk ci - 1 (consumed, barrier passed)
+      const int sl = (ci + S2_STAGES - 1) % S2_STAGES;
+      if (iq < q1) {
+        const int64_t ie = chunk_end(iq);
+        s2_issue(a, form, in, iq, (int)(ie - iq), ystr, tstr, tsz, sY0 + sl * S2_CH * ystr, sT0 + sl * S2_CH * tstr,
+                 vec);
+        iq = ie;
+      }
+      cp_async_commit();
     }
-    cp_async_commit();
-    cp_async_wait_1();
+    cp_async_wait_n<S2_STAGES - 1>();   // chunk ci has landed
     __syncthreads();
     if (act) {
       const float* Yb = sY0 + buf * S2_CH * ystr;
@@ -593,8 +606,8 @@ __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
         }
       }
     }
-    __syncthreads();   // buffer `buf` is refilled by the next iteration's issue
-    buf ^= 1;
+    __syncthreads();   // slot `buf` is refilled by the next iteration's issue
+    ++ci;
     qa = qe;
     const bool seg_end = segA && (qa >= q1 || (qa % a.Jlo) == 0);
     if (seg_end) {
@@ -644,7 +657,7 @@ size_t stage2_smem_bytes(const Stage2Args& a) {
   else { PO = a.Rk * a.Rn; }
   const int G = std::max(1, S2_THREADS / PO);
   const int ystr = (RRk + 3) & ~3, tstr = (tsz + 3) & ~3;
-  return sizeof(float) * ((size_t)2 * S2_CH * (ystr + tstr) + (size_t)G * PO + PO);
+  return sizeof(float) * ((size_t)S2_STAGES * S2_CH * (ystr + tstr) + (size_t)G * PO + PO);
 }
 
 // ---------------------------------------------------------------------------
