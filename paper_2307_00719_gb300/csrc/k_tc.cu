@@ -507,9 +507,31 @@ __device__ __forceinline__ float s2_dot(const float* L, const float* M) {
   return v;
 }
 
+// 2 x 2 register block of a product with compile-time R (multiple of 4):
+// acc[a + 2b] += sum_e L[(x0 + a) + R e] M[e + R (y0 + b)];  L at x0 (even), M at R y0
+template <int R>
+__device__ __forceinline__ void s2_dot22(const float* L, const float* M, float (&acc)[4]) {
+  float v00 = 0.f, v10 = 0.f, v01 = 0.f, v11 = 0.f;
+#pragma unroll
+  for (int e = 0; e < R; e += 4) {
+    const float4 m0 = *(const float4*)(M + e);
+    const float4 m1 = *(const float4*)(M + R + e);
+    const float mm0[4] = {m0.x, m0.y, m0.z, m0.w}, mm1[4] = {m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 l = *(const float2*)(L + R * (e + u));
+      v00 = fmaf(l.x, mm0[u], v00);
+      v10 = fmaf(l.y, mm0[u], v10);
+      v01 = fmaf(l.x, mm1[u], v01);
+      v11 = fmaf(l.y, mm1[u], v11);
+    }
+  }
+  acc[0] += v00; acc[1] += v10; acc[2] += v01; acc[3] += v11;
+}
+
 // RT > 0: all four ranks equal RT (compile-time strides); RT = 0: any ranks
 template <int RT>
-__global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
+__global__ void __launch_bounds__(S2_THREADS, 3) stage2_kernel(Stage2Args a) {
   PDL_ENTRY();
   extern __shared__ __align__(16) float s2[];
   const int Rk = a.Rk, Rk1 = a.Rk1, Rn = a.Rn, Rn1 = a.Rn1;
@@ -532,13 +554,26 @@ __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
   const bool vec = (RRk % 4 == 0) && (tsz % 4 == 0) && ((((uintptr_t)a.Y) & 15) == 0) &&
                    (form == 2 || ((((uintptr_t)(form == 0 ? a.TB : a.TA)) & 15) == 0));
   const int tid = threadIdx.x;
-  const int g = tid / PO, o = tid - g * PO;
-  const bool act = g < G;
-  const int x = act ? o % X : 0, y = act ? o / X : 0;
+  // RT = 0: one product entry o = (x, y) per thread, G groups of PO threads.
+  // RT > 0: a 2 x 2 block of entries per thread (x0..x0+1, y0..y0+1), RT^2/4
+  // threads per combination, GR groups.
+  constexpr int TPC = RT > 0 ? RT * RT / 4 : 1;
+  const int GG = RT > 0 ? S2_THREADS / TPC : G;
+  const int g = RT > 0 ? tid / TPC : tid / PO;
+  const int o = RT > 0 ? 0 : tid - g * PO;
+  const bool act = g < GG;
+  const int tt = RT > 0 ? tid - g * TPC : 0;
+  const int x = RT > 0 ? 2 * (tt % (RT / 2)) : (act ? o % X : 0);
+  const int y = RT > 0 ? 2 * (tt / (RT / 2)) : (act ? o / X : 0);
+  constexpr int NV = RT > 0 ? 4 : 1;
+  // product entries held: (x + (v & 1), y + (v >> 1)) for RT > 0, else (x, y)
+  auto oidx = [&](int v) { return RT > 0 ? (x + (v & 1)) + X * (y + (v >> 1)) : o; };
   const int64_t in = blockIdx.x;
   const int64_t ncomb = a.Jlo * a.Jhi;
   const int64_t q0 = (int64_t)blockIdx.y * a.per, q1 = min(ncomb, q0 + a.per);
-  float acc = 0.f;      // product sums (per group)
+  float acc4[NV];       // product sums (per group)
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc4[v] = 0.f;
   float outv = 0.f;     // A-multiplied segment sums (threads tid < OUTP)
   // chunk boundaries: never cross an i_hi run when segA
   auto chunk_end = [&](int64_t qa) {
@@ -579,7 +614,13 @@ __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
       const float* Yb = sY0 + buf * S2_CH * ystr;
       const float* Tb = sT0 + buf * S2_CH * tstr;
       if (form == 2) {
-        for (int j = g; j < nq; j += G) acc += Yb[j * ystr + x + Rk * y];
+        for (int j = g; j < nq; j += GG) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const int xx = RT > 0 ? x + (v & 1) : x, yy = RT > 0 ? y + (v >> 1) : y;
+            acc4[v] += Yb[j * ystr + xx + Rk * yy];
+          }
+        }
       } else {
         // product entry (x, y) = sum_e L[x + X e] M[e + inner y]:
         // form YB: L = Y_q, M = B;  form AY: L = A, M = Y_q
@@ -587,21 +628,14 @@ __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
         const float* Lb = (form == 0 ? Yb : Tb) + x;
         const float* Mb = (form == 0 ? Tb : Yb) + inner * y;
         if constexpr (RT > 0) {
-          int j = g;
-          for (; j + G < nq; j += 2 * G) {
-            const float v0 = s2_dot<RT>(Lb + j * lstr, Mb + j * mstr);
-            const float v1 = s2_dot<RT>(Lb + (j + G) * lstr, Mb + (j + G) * mstr);
-            acc += v0;
-            acc += v1;
-          }
-          if (j < nq) acc += s2_dot<RT>(Lb + j * lstr, Mb + j * mstr);
+          for (int j = g; j < nq; j += GG) s2_dot22<RT>(Lb + j * lstr, Mb + j * mstr, acc4);
         } else {
-          for (int j = g; j < nq; j += G) {
+          for (int j = g; j < nq; j += GG) {
             const float* lq = Lb + j * lstr;
             const float* mq = Mb + j * mstr;
             float v = 0.f;
             for (int e = 0; e < inner; ++e) v = fmaf(lq[X * e], mq[e], v);
-            acc += v;
+            acc4[0] += v;
           }
         }
       }
@@ -612,13 +646,15 @@ __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
     const bool seg_end = segA && (qa >= q1 || (qa % a.Jlo) == 0);
     if (seg_end) {
       // S = sum over groups (fixed order), then out += A(i_hi) S
-      if (act) sRed[g * PO + o] = acc;
-      acc = 0.f;
+      if (act) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { sRed[g * PO + oidx(v)] = acc4[v]; acc4[v] = 0.f; }
+      }
       __syncthreads();
-      float* sS = sRed + G * PO;
+      float* sS = sRed + GG * PO;
       for (int e = tid; e < PO; e += S2_THREADS) {
         float v = 0.f;
-        for (int gg = 0; gg < G; ++gg) v += sRed[gg * PO + e];
+        for (int gg = 0; gg < GG; ++gg) v += sRed[gg * PO + e];
         sS[e] = v;
       }
       __syncthreads();
@@ -639,11 +675,14 @@ __global__ void __launch_bounds__(S2_THREADS) stage2_kernel(Stage2Args a) {
     for (int e = tid; e < OUTP; e += S2_THREADS) dst[e] = outv;   // tid < OUTP <= 256: one each
     return;
   }
-  if (act) sRed[g * PO + o] = acc;
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sRed[g * PO + oidx(v)] = acc4[v];
+  }
   __syncthreads();
   for (int e = tid; e < PO; e += S2_THREADS) {
     float v = 0.f;
-    for (int gg = 0; gg < G; ++gg) v += sRed[gg * PO + e];
+    for (int gg = 0; gg < GG; ++gg) v += sRed[gg * PO + e];
     const int xx = e % X, yy = e / X;
     dst[yy + Rn * xx] = v;
   }
@@ -655,7 +694,8 @@ size_t stage2_smem_bytes(const Stage2Args& a) {
   if (a.TB) { tsz = a.Rk1 * a.Rn; PO = a.Rk * a.Rn; }
   else if (a.TA) { tsz = a.Rn1 * a.Rk; PO = a.Rn1 * a.Rn; }
   else { PO = a.Rk * a.Rn; }
-  const int G = std::max(1, S2_THREADS / PO);
+  // groups: S2_THREADS / PO (one entry per thread) or S2_THREADS / (PO / 4) (2 x 2 blocks)
+  const int G = std::max(1, S2_THREADS / std::max(1, PO / 4));
   const int ystr = (RRk + 3) & ~3, tstr = (tsz + 3) & ~3;
   return sizeof(float) * ((size_t)S2_STAGES * S2_CH * (ystr + tstr) + (size_t)G * PO + PO);
 }
