@@ -31,6 +31,10 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "STR/rSTR tensor entries/s per update, % roofline, rel. fit err vs FP64"
+# DRAM bytes (read + write) of one stage-1 launch on the order-4 workload, from the
+# ncu capture summarised in profiles/ncu_str_order4_update_kernels.md; set to None
+# whenever the stage-1 kernel changes until it is captured again
+STAGE1_DRAM_BYTES = 10546944
 W2 = synth.WORKLOADS["order4"]
 W3 = synth.WORKLOADS["rand3"]
 WORKLOAD_DESC = ("order4: 64x64x64xT, T=400, TR-ranks all 8, Gaussian cores, SNR 30 dB, "
@@ -230,7 +234,9 @@ def main_ours(a):
     RRk = W2.ranks[0] * W2.ranks[1]
     roofline = {"kernel": "stage1_tc_persist_kernel (tcgen05 kind::tf32, 3-term split, TMA-fed)",
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_hbm, "unit": "GB/s",
-                "frac": round(achieved / peak_hbm, 4), "traffic": None,
+                "frac": round(achieved / peak_hbm, 4), "traffic": STAGE1_DRAM_BYTES,
+                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch, ncu --set full "
+                                "on this workload (profiles/ncu_str_order4_update_kernels.md)",
                 "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured",
                 "algorithmic_per_launch": {"bytes": slab_bytes, "flop": 2.0 * E * RRk,
                                            "note": "one read of the 64^3 x 10 FP32 slab; 2 E R_1 R_2 flop"},
