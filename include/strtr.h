@@ -154,10 +154,17 @@ str_status rstr_update(str_ctx* ctx, const str_tensor* X_new, str_sketch type, i
                        uint64_t seed, void* stream);
 
 /*
- * str_update_batch -- updates `count` independent contexts with one slab each;
- * the per-phase kernels of all contexts run as single batched launches.
+ * str_update_batch -- updates `count` independent contexts with one slab each.
  * randomized = 0: str_update semantics; 1: rstr_update with each context's own
  * sketch settings.  On error no context is changed (sync mode).
+ * On a non-default stream (randomized = 0) every context's update runs as one
+ * branch, forked from `stream` and joined back to it, so the updates run
+ * concurrently; a batch that recurs (same contexts, slab shapes and buffer
+ * parities) is captured once into a CUDA graph and replayed.  Slabs are staged
+ * at each context's own device address (a device-to-device copy).  On the
+ * legacy default stream, or with randomized = 1, the updates run one after
+ * another on `stream`.  Results are bit-identical to one str_update (or
+ * rstr_update) per context.
  */
 str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X_new, int count,
                             int randomized, void* stream);

@@ -111,6 +111,13 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("griddepcontrol.launch_dependents;" :::);   \
   } while (0)
 
+bool str_pdl_enabled();
+// A stream that waited on an event since its last kernel launches its next
+// kernel without programmatic serialisation, so the event dependency is a plain
+// one (programmatic overlap applies only to kernel-to-kernel order).
+void str_mark_cross_wait(cudaStream_t s);
+bool str_take_cross_wait(cudaStream_t s);
+
 template <typename... KArgs, typename... Args>
 static inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                                    Args... args) {
@@ -124,7 +131,8 @@ static inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   // the legacy default stream keeps its plain serialisation
-  cfg.numAttrs = (s == nullptr || s == cudaStreamLegacy) ? 0 : 1;
+  const bool waited = str_take_cross_wait(s);
+  cfg.numAttrs = (s == nullptr || s == cudaStreamLegacy || !str_pdl_enabled() || waited) ? 0 : 1;
   return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
 }
 

@@ -10,6 +10,7 @@
 // by flipping the committed index of every mode it updated, so a failed step
 // (sync mode) leaves the committed state untouched.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <cstdio>
@@ -21,6 +22,32 @@
 #include "kernels.cuh"
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_next_uid{1};
+static uint64_t next_uid() { return g_next_uid.fetch_add(1); }
+namespace {
+thread_local cudaStream_t g_cross_wait[16];
+thread_local int g_cross_n = 0;
+}
+void str_mark_cross_wait(cudaStream_t s) {
+  for (int i = 0; i < g_cross_n; ++i)
+    if (g_cross_wait[i] == s) return;
+  if (g_cross_n < 16) g_cross_wait[g_cross_n++] = s;
+  else g_cross_wait[15] = s;
+}
+bool str_take_cross_wait(cudaStream_t s) {
+  for (int i = 0; i < g_cross_n; ++i)
+    if (g_cross_wait[i] == s) {
+      g_cross_wait[i] = g_cross_wait[--g_cross_n];
+      return true;
+    }
+  return false;
+}
+// cudaStreamWaitEvent that also marks the stream (see str_mark_cross_wait)
+static cudaError_t wait_event(cudaStream_t s, cudaEvent_t e) {
+  str_mark_cross_wait(s);
+  return cudaStreamWaitEvent(s, e, 0);
+}
+bool str_pdl_enabled() { return true; }
 
 void str_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   g_last_error = std::string(cudaGetErrorString(e)) + " in " + what + " (" + file + ":" +
@@ -98,6 +125,10 @@ struct str_ctx {
   std::vector<cudaEvent_t> pool;
   int64_t prof_launch[STR_K_CLASSES] = {};
   double prof_ms[STR_K_CLASSES] = {};
+  // identity for batch-graph caching (never reused) and the batch branch stream
+  uint64_t uid = 0;
+  cudaStream_t bstream = nullptr;
+  cudaEvent_t ev_bfork = nullptr, ev_bjoin = nullptr;
   // second stream for the Q-side branch of an update (created on first use)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -382,16 +413,16 @@ str_status fork_side(str_ctx* c, cudaStream_t s) {
     STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   }
   STR_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
-  STR_CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  STR_CUDA_TRY(wait_event(c->side, c->ev_fork));
   return STR_OK;
 }
 
 str_status join_side(str_ctx* c, cudaStream_t s) {
   STR_CUDA_TRY(cudaEventRecord(c->ev_join, c->side));
-  STR_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
+  STR_CUDA_TRY(wait_event(s, c->ev_join));
   if (c->side2_used) {
     STR_CUDA_TRY(cudaEventRecord(c->ev_join2, c->side2));
-    STR_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join2, 0));
+    STR_CUDA_TRY(wait_event(s, c->ev_join2));
     c->side2_used = false;
   }
   return STR_OK;
@@ -408,7 +439,7 @@ str_status fork_side2(str_ctx* c, cudaStream_t from = nullptr) {
     STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
   }
   STR_CUDA_TRY(cudaEventRecord(c->ev_fork2, from ? from : c->side));
-  STR_CUDA_TRY(cudaStreamWaitEvent(c->side2, c->ev_fork2, 0));
+  STR_CUDA_TRY(wait_event(c->side2, c->ev_fork2));
   c->side2_used = true;
   return STR_OK;
 }
@@ -729,6 +760,7 @@ str_status ctx_create(str_ctx** out, int N, const int64_t* dims, const int* rank
   if (o.sketch != STR_SKETCH_NONE && (o.sketch < 0 || o.sketch > 2 || o.m < 1)) return STR_ERR_INVALID_ARG;
   TRY(validate_shape(N, dims, ranks));
   str_ctx* c = new str_ctx();
+  c->uid = next_uid();
   cudaGetDevice(&c->dev);
   c->N = N;
   for (int k = 0; k < N - 1; ++k) c->I[k] = dims[k];
@@ -1422,6 +1454,82 @@ str_status rstr_update(str_ctx* c, const str_tensor* X, str_sketch type, int64_t
   return finish_step(c, s, tn);
 }
 
+// ---------------------------------------------------------------------------
+// batched updates: one CUDA graph per (contexts, slab shapes, buffer parities,
+// buffer generations) whose branches -- one per context, each the two-branch
+// update of str_step -- run concurrently
+// ---------------------------------------------------------------------------
+struct BatchGraph {
+  int dev;
+  std::vector<uint64_t> uids;
+  std::vector<int64_t> tns;
+  std::vector<int> xtypes, parity;
+  std::vector<uint64_t> gens;
+  cudaGraphExec_t exec;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch;
+// batch keys met once (capture happens when a key comes back): a batch whose
+// slab shapes change every step runs as plain concurrent branches
+std::vector<uint64_t> g_batch_seen;
+
+void forget_batch_graphs(uint64_t uid) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batch.size();) {
+    if (std::find(g_batch[i].uids.begin(), g_batch[i].uids.end(), uid) != g_batch[i].uids.end()) {
+      cudaGraphExecDestroy(g_batch[i].exec);
+      g_batch.erase(g_batch.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+uint64_t batch_key(str_ctx* const* ctxs, const std::vector<int64_t>& tns, const std::vector<SlabView>& v, int count) {
+  uint64_t h = 1469598103934665603ull;   // FNV-1a over the key fields
+  auto mix = [&](uint64_t x) {
+    for (int b = 0; b < 8; ++b) { h ^= (x >> (8 * b)) & 0xff; h *= 1099511628211ull; }
+  };
+  for (int i = 0; i < count; ++i) {
+    mix(ctxs[i]->uid);
+    mix((uint64_t)tns[i]);
+    mix((uint64_t)v[i].xtype);
+    mix((uint64_t)ctxs[i]->cur[0]);
+    mix(ctxs[i]->gen);
+  }
+  return h;
+}
+
+// true when the key was met before; records it otherwise (bounded list)
+bool seen_before(uint64_t key) {
+  if (std::find(g_batch_seen.begin(), g_batch_seen.end(), key) != g_batch_seen.end()) return true;
+  if (g_batch_seen.size() >= 256) g_batch_seen.erase(g_batch_seen.begin());
+  g_batch_seen.push_back(key);
+  return false;
+}
+
+str_status ensure_bstream(str_ctx* c) {
+  if (c->bstream) return STR_OK;
+  STR_CUDA_TRY(cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking));
+  STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_bfork, cudaEventDisableTiming));
+  STR_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_bjoin, cudaEventDisableTiming));
+  return STR_OK;
+}
+
+// every context's step on its own branch stream: all forked from the same point
+// of s, all joined back to s after the last one is enqueued
+str_status batch_steps(str_ctx* const* ctxs, std::vector<SlabView>& v, int count, cudaStream_t s) {
+  for (int i = 0; i < count; ++i) STR_CUDA_TRY(cudaEventRecord(ctxs[i]->ev_bfork, s));
+  for (int i = 0; i < count; ++i) {
+    str_ctx* c = ctxs[i];
+    STR_CUDA_TRY(wait_event(c->bstream, c->ev_bfork));
+    TRY(str_step(c, v[i], c->bstream));
+    STR_CUDA_TRY(cudaEventRecord(c->ev_bjoin, c->bstream));
+  }
+  for (int i = 0; i < count; ++i) STR_CUDA_TRY(wait_event(s, ctxs[i]->ev_bjoin));
+  return STR_OK;
+}
+
 str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, int count, int randomized,
                             void* stream) {
   if (!ctxs || !X || count < 0) return STR_ERR_INVALID_ARG;
@@ -1436,17 +1544,134 @@ str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, in
   }
   str_status st = STR_OK;
   int done = 0;
-  for (int i = 0; i < count && st == STR_OK; ++i) {
-    str_ctx* c = ctxs[i];
-    c->launches = 0;
-    SlabView v;
-    st = take_slab(c, X[i], &v, s);
-    if (st != STR_OK) break;
-    tns[i] = v.dim[c->N - 1];
-    if (c->t_rows + tns[i] > c->opt.t_capacity) { st = STR_ERR_CAPACITY; break; }
-    st = randomized ? rstr_step(c, v, s) : str_step(c, v, s);
-    if (st == STR_OK && !randomized) st = append_rows(c, tns[i], s);
-    done = i + 1;
+  bool concurrent = !randomized && count > 0 && s != nullptr && s != cudaStreamLegacy;
+  for (int i = 0; i < count; ++i)
+    if (ctxs[i]->opt.profile) concurrent = false;
+  if (!concurrent) {
+    for (int i = 0; i < count && st == STR_OK; ++i) {
+      str_ctx* c = ctxs[i];
+      c->launches = 0;
+      SlabView v;
+      st = take_slab(c, X[i], &v, s);
+      if (st != STR_OK) break;
+      tns[i] = v.dim[c->N - 1];
+      if (c->t_rows + tns[i] > c->opt.t_capacity) { st = STR_ERR_CAPACITY; break; }
+      st = randomized ? rstr_step(c, v, s) : str_step(c, v, s);
+      if (st == STR_OK && !randomized) st = append_rows(c, tns[i], s);
+      done = i + 1;
+    }
+  } else {
+    // slabs staged at each context's fixed address, then every update as one
+    // branch of a captured batch graph (plain concurrent branches until every
+    // context has run its slab shape once)
+    std::vector<SlabView> v(count);
+    bool graphs = true, warm = true;
+    for (int i = 0; i < count && st == STR_OK; ++i) {
+      str_ctx* c = ctxs[i];
+      c->launches = 0;
+      st = take_slab(c, X[i], &v[i], s);
+      if (st != STR_OK) break;
+      tns[i] = v[i].dim[c->N - 1];
+      if (c->t_rows + tns[i] > c->opt.t_capacity) { st = STR_ERR_CAPACITY; break; }
+      st = ensure_bstream(c);
+      if (st != STR_OK) break;
+      int64_t cnt = 1;
+      for (int k = 0; k < c->N; ++k) cnt *= v[i].dim[k];
+      if (v[i].X != c->xstage.p) {
+        st = grow(c, c->xstage, (size_t)cnt * dsize(X[i]->dtype));
+        if (st != STR_OK) break;
+        if (cudaMemcpyAsync(c->xstage.p, v[i].X, (size_t)cnt * dsize(X[i]->dtype), cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess) { st = STR_ERR_CUDA; break; }
+        v[i].X = c->xstage.p;
+      }
+      if (!c->opt.graphs) graphs = false;
+      const std::pair<int64_t, int> shape(tns[i], v[i].xtype);
+      if (std::find(c->warm.begin(), c->warm.end(), shape) == c->warm.end()) warm = false;
+    }
+    if (st == STR_OK) {
+      done = count;
+      BatchGraph* hit = nullptr;
+      std::unique_lock<std::mutex> lk(g_batch_mu);
+      if (graphs && warm) {
+        for (auto& g : g_batch) {
+          if ((int)g.uids.size() != count) continue;
+          bool same = true;
+          for (int i = 0; i < count && same; ++i) {
+            const str_ctx* c = ctxs[i];
+            same = g.uids[i] == c->uid && g.tns[i] == tns[i] && g.xtypes[i] == v[i].xtype &&
+                   g.parity[i] == c->cur[0] && g.gens[i] == c->gen && g.dev == c->dev;
+          }
+          if (same) { hit = &g; break; }
+        }
+      }
+      if (hit) {
+        if (cudaGraphLaunch(hit->exec, s) != cudaSuccess) st = STR_ERR_CUDA;
+        for (int i = 0; i < count; ++i)
+          for (int k = 0; k < ctxs[i]->N - 1; ++k) { ctxs[i]->upd[k] = 1; ctxs[i]->core_ver[k]++; }
+      } else if (graphs && warm && !seen_before(batch_key(ctxs, tns, v, count))) {
+        lk.unlock();
+        st = batch_steps(ctxs, v, count, s);
+      } else if (graphs && warm) {
+        std::vector<uint64_t> gen0(count);
+        for (int i = 0; i < count; ++i) gen0[i] = ctxs[i]->gen;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = STR_ERR_CUDA;
+        if (st == STR_OK) {
+          st = batch_steps(ctxs, v, count, s);
+          const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+          bool moved = false;
+          for (int i = 0; i < count; ++i) moved = moved || ctxs[i]->gen != gen0[i];
+          if (st == STR_OK && (ce != cudaSuccess || moved)) {
+            // a buffer grew during capture: nothing recorded ran; run the branches directly
+            if (graph) cudaGraphDestroy(graph);
+            graph = nullptr;
+            cudaGetLastError();
+            for (int i = 0; i < count; ++i) {
+              for (int k = 0; k < STR_MAXN; ++k) ctxs[i]->upd[k] = 0;
+              ctxs[i]->y_slab[0] = ctxs[i]->y_slab[1] = nullptr;
+              ctxs[i]->tc_xt_src = nullptr;
+            }
+            st = batch_steps(ctxs, v, count, s);
+          } else if (st == STR_OK) {
+            cudaGraphExec_t exec = nullptr;
+            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+              st = from_cuda(ie, "cudaGraphInstantiate(batch)");
+            } else {
+              BatchGraph g;
+              g.dev = ctxs[0]->dev;
+              for (int i = 0; i < count; ++i) {
+                const str_ctx* c = ctxs[i];
+                g.uids.push_back(c->uid);
+                g.tns.push_back(tns[i]);
+                g.xtypes.push_back(v[i].xtype);
+                g.parity.push_back(c->cur[0]);
+                g.gens.push_back(c->gen);
+              }
+              g.exec = exec;
+              if (g_batch.size() >= 64) {   // bounded cache: drop the oldest graph
+                cudaGraphExecDestroy(g_batch.front().exec);
+                g_batch.erase(g_batch.begin());
+              }
+              g_batch.push_back(g);
+              if (cudaGraphLaunch(exec, s) != cudaSuccess) st = STR_ERR_CUDA;
+            }
+          } else if (graph) {
+            cudaGraphDestroy(graph);
+          }
+        }
+      } else {
+        lk.unlock();
+        st = batch_steps(ctxs, v, count, s);
+        for (int i = 0; i < count && st == STR_OK; ++i) {
+          const std::pair<int64_t, int> shape(tns[i], v[i].xtype);
+          if (std::find(ctxs[i]->warm.begin(), ctxs[i]->warm.end(), shape) == ctxs[i]->warm.end())
+            ctxs[i]->warm.push_back(shape);
+        }
+      }
+    }
+    for (int i = 0; i < done && st == STR_OK; ++i) st = append_rows(ctxs[i], tns[i], s);
   }
   bool any_fail = st != STR_OK;
   if (!any_fail) {
@@ -1750,6 +1975,10 @@ void str_destroy(str_ctx* c) {
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& e : c->pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : c->pool) cudaEventDestroy(e);
+  forget_batch_graphs(c->uid);
+  if (c->ev_bfork) cudaEventDestroy(c->ev_bfork);
+  if (c->ev_bjoin) cudaEventDestroy(c->ev_bjoin);
+  if (c->bstream) cudaStreamDestroy(c->bstream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->side) cudaStreamDestroy(c->side);

@@ -32,6 +32,39 @@ def test_batch_equals_individual_updates():
             assert np.array_equal(a.core(n), b.core(n))
 
 
+def test_batch_graph_on_a_stream_equals_individual_updates():
+    """On a non-default stream the batch runs every context's update as one
+    branch of a captured graph (plain branches on the first step of a shape,
+    capture on the next one per buffer parity, replays after): still
+    bit-identical to updating each context on its own."""
+    import torch
+    p = lib()
+    specs = synth.uneven_streams(count=5, steps=1, seed=8, dim_range=(8, 40), rank_range=(2, 5),
+                                 tnew_range=(1, 6), t_init=6)
+    steps = 6
+    made = []
+    for i, s in enumerate(specs):
+        tn = s.t_news[0]
+        T = s.t_init + steps * tn
+        G, X = problem(s.dims, T, s.ranks, 300 + i)
+        init = perturbed_init(G, s.t_init, i)
+        a = p.str_init_cores(init, X0=dev(X[..., :s.t_init]), compute="f32", sweeps=2, t_capacity=T)
+        b = p.str_init_cores(init, X0=dev(X[..., :s.t_init]), compute="f32", sweeps=2, t_capacity=T)
+        made.append((s, tn, X, a, b))
+    st = torch.cuda.Stream()
+    for step in range(steps):
+        slabs = [dev(X[..., s.t_init + step * tn:s.t_init + (step + 1) * tn]) for s, tn, X, _, _ in made]
+        with torch.cuda.stream(st):
+            p.str_update_batch([a for _, _, _, a, _ in made], slabs)
+        st.synchronize()
+        for i, (_, _, _, _, b) in enumerate(made):
+            b.update(slabs[i])
+    for s, tn, X, a, b in made:
+        assert a.time_rows() == b.time_rows() == s.t_init + steps * tn
+        for n in (1, 2, 3):
+            assert np.array_equal(a.core(n), b.core(n))
+
+
 @pytest.mark.parametrize("sketch", ["none", "leverage", "ksrft"])
 def test_checkpoint_resume_is_bit_identical(sketch):
     p = lib()
