@@ -124,6 +124,63 @@ __global__ void __launch_bounds__(256) wgram_kernel(const T* __restrict__ g, con
   if (r < RR && c < RR) part[((int64_t)blockIdx.z * RR + r) * RR + c] = acc;
 }
 
+// Same weighted Gram for FP32 samples without the FP64 pipe: every term
+// w_s g_a g_b is formed as an FP32 pair (g_a g_b exactly by FMA, times the
+// weight carried as an FP32 pair) and summed with error-free transformations
+// (Dekker / Knuth), so the split sum carries about 44 significant bits.
+__device__ __forceinline__ void pair_add(float& sh, float& sl, float ph, float pl) {
+  const float t = sh + ph;
+  const float bb = t - sh;
+  const float e = (sh - (t - bb)) + (ph - bb);
+  sh = t;
+  sl += e + pl;
+}
+
+__global__ void __launch_bounds__(256) wgram_pair_kernel(const float* __restrict__ g, const double* __restrict__ w,
+                                                         int64_t m, int64_t per, int RR, double* __restrict__ part) {
+  PDL_ENTRY();
+  constexpr int CH = 64;
+  __shared__ float sa[CH][16], sb[CH][16];
+  __shared__ float swh[CH], swl[CH];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
+  const int64_t sbeg = (int64_t)blockIdx.z * per, send = min(m, sbeg + per);
+  float sh = 0.f, sl = 0.f;
+  for (int64_t s0 = sbeg; s0 < send; s0 += CH) {
+    const int ns = (send - s0 < CH) ? (int)(send - s0) : CH;
+    for (int e = threadIdx.x; e < CH * 16; e += 256) {
+      const int ss = e >> 4, cc = e & 15;
+      float va = 0.f, vb = 0.f;
+      if (ss < ns) {
+        if (r0 + cc < RR) va = g[(s0 + ss) * RR + r0 + cc];
+        if (c0 + cc < RR) vb = g[(s0 + ss) * RR + c0 + cc];
+      }
+      sa[ss][cc] = va;
+      sb[ss][cc] = vb;
+    }
+    for (int e = threadIdx.x; e < CH; e += 256) {
+      const double wv = (e < ns) ? (w ? w[s0 + e] : 1.0) : 0.0;
+      const float wh = (float)wv;
+      swh[e] = wh;
+      swl[e] = (float)(wv - (double)wh);
+    }
+    __syncthreads();
+    for (int ss = 0; ss < ns; ++ss) {
+      const float a = sa[ss][ty], b = sb[ss][tx];
+      const float ph = a * b;
+      const float pl = fmaf(a, b, -ph);          // a b = ph + pl exactly
+      const float wh = swh[ss], wl = swl[ss];
+      const float th = wh * ph;
+      float tl = fmaf(wh, ph, -th);              // wh ph = th + tl exactly
+      tl = fmaf(wh, pl, fmaf(wl, ph, tl));       // + wh pl + wl ph
+      pair_add(sh, sl, th, tl);
+    }
+    __syncthreads();
+  }
+  const int r = r0 + ty, c = c0 + tx;
+  if (r < RR && c < RR) part[((int64_t)blockIdx.z * RR + r) * RR + c] = (double)sh + (double)sl;
+}
+
 // out = base + sum over sample splits (fixed order), FP64
 cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const double* w, int64_t m, int RR,
                                  const double* base, double* out, double* part, cudaStream_t s) {
@@ -139,7 +196,7 @@ cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const do
     else launch_k(wgram_kernel<double, false>, grid, 256, 0, s, (const double*)gs, w, m, per, RR, part);
   } else {
     if (cplx) launch_k(wgram_kernel<float, true>, grid, 256, 0, s, (const float*)gs, w, m, per, RR, part);
-    else launch_k(wgram_kernel<float, false>, grid, 256, 0, s, (const float*)gs, w, m, per, RR, part);
+    else launch_k(wgram_pair_kernel, grid, 256, 0, s, (const float*)gs, w, m, per, RR, part);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

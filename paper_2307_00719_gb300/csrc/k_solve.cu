@@ -588,9 +588,9 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Refined solve for n <= 64 (even), one row of P per CTA at a time, 256
-// threads: thread (c, part) owns column c and the quarter part of every inner
-// sum.  W32 and Q = Qh + Ql (an FP32 pair carrying Q to about 2^-48) are
+// Refined solve for n <= 128 (even), one row of P per CTA at a time, 256
+// threads: thread (c, part) owns column c (and c + 64) and the quarter part of
+// every inner sum.  W32 and Q = Qh + Ql (an FP32 pair carrying Q to about 2^-48) are
 // staged by bulk copies; the right-hand side is formed from the split
 // partials as in solve_refine_kernel.
 //   g  = p W32                           (FP32)
@@ -618,7 +618,9 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+template <int CPT>
 __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
+  // CPT columns per thread: c = (tid & 63) + 64 u, u < CPT (n <= 64 CPT)
   PDL_ENTRY();
   extern __shared__ __align__(16) unsigned char sma[];
   const int n = a.n, nn = n * n;
@@ -630,7 +632,7 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
   float* vf = (float*)(pd4 + 4 * n);        // n: FP32 vector of the current product
   float* red = vf + n;                      // 4 x n partial sums (x2 for pairs)
   __shared__ __align__(8) uint64_t bar;
-  const int tid = threadIdx.x, c = tid & 63, part = tid >> 6;
+  const int tid = threadIdx.x, c0 = tid & 63, part = tid >> 6;
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -644,10 +646,24 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
   }
   bool staged = false;
   const int k0 = part * ((n + 3) / 4), k1 = min(n, k0 + (n + 3) / 4);
+  // sum_{k in this part} v[k] W[k][c]
+  auto part_dot = [&](int c) {
+    float s0 = 0.f, s1 = 0.f;
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+      s0 = fmaf(vf[k], Wm[k * n + c], s0);
+      s1 = fmaf(vf[k + 1], Wm[(k + 1) * n + c], s1);
+    }
+    if (k < k1) s0 = fmaf(vf[k], Wm[k * n + c], s0);
+    return s0 + s1;
+  };
   for (int64_t r = blockIdx.x; r < a.rows; r += gridDim.x) {
     // right-hand side: base + split partials (or P).  Part q sums the splits
     // q, q + 4, ... in order; the four sums are added in part order.
-    if (c < n) {
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      const int c = c0 + 64 * u;
+      if (c >= n) continue;
       if (a.ps.part) {
         double acc = 0.0;
         const float* pp = a.ps.part + r * n + c;
@@ -655,10 +671,10 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
         for (int s0 = part; s0 < a.ps.splits; s0 += 32) {
           float v[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = (s0 + 4 * u < a.ps.splits) ? pp[(int64_t)(s0 + 4 * u) * st] : 0.f;
+          for (int w = 0; w < 8; ++w) v[w] = (s0 + 4 * w < a.ps.splits) ? pp[(int64_t)(s0 + 4 * w) * st] : 0.f;
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (s0 + 4 * u < a.ps.splits) acc += (double)v[u];
+          for (int w = 0; w < 8; ++w)
+            if (s0 + 4 * w < a.ps.splits) acc += (double)v[w];
         }
         pd4[part * n + c] = acc;
       } else if (part == 0) {
@@ -666,17 +682,22 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
       }
     }
     __syncthreads();
-    if (part == 0 && c < n) {
-      double pc;
-      if (a.ps.part) {
-        pc = a.ps.base ? a.ps.base[r * n + c] : 0.0;
-        pc += ((pd4[c] + pd4[n + c]) + pd4[2 * n + c]) + pd4[3 * n + c];
-        a.ps.pout[r * n + c] = pc;
-      } else {
-        pc = pd4[c];
+    if (part == 0) {
+#pragma unroll
+      for (int u = 0; u < CPT; ++u) {
+        const int c = c0 + 64 * u;
+        if (c >= n) continue;
+        double pc;
+        if (a.ps.part) {
+          pc = a.ps.base ? a.ps.base[r * n + c] : 0.0;
+          pc += ((pd4[c] + pd4[n + c]) + pd4[2 * n + c]) + pd4[3 * n + c];
+          a.ps.pout[r * n + c] = pc;
+        } else {
+          pc = pd4[c];
+        }
+        pd[c] = pc;
+        vf[c] = (float)pc;
       }
-      pd[c] = pc;
-      vf[c] = (float)pc;
     }
     if (!staged) {
       const bool ok = mbar_wait(&bar, 0, 2000000000ull);
@@ -689,25 +710,28 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
       __syncthreads();
     }
     // g = p W32
-    float g = 0.f;
-    if (c < n) {
-      float s0 = 0.f, s1 = 0.f;
-      int k = k0;
-      for (; k + 1 < k1; k += 2) {
-        s0 = fmaf(vf[k], Wm[k * n + c], s0);
-        s1 = fmaf(vf[k + 1], Wm[(k + 1) * n + c], s1);
-      }
-      if (k < k1) s0 = fmaf(vf[k], Wm[k * n + c], s0);
-      red[part * n + c] = s0 + s1;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      const int c = c0 + 64 * u;
+      if (c < n) red[part * n + c] = part_dot(c);
     }
     __syncthreads();
-    if (part == 0 && c < n) {
-      g = (red[c] + red[n + c]) + (red[2 * n + c] + red[3 * n + c]);
-      vf[c] = g;                 // g, read by every part below
+    float g[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      const int c = c0 + 64 * u;
+      g[u] = 0.f;
+      if (part == 0 && c < n) {
+        g[u] = (red[c] + red[n + c]) + (red[2 * n + c] + red[3 * n + c]);
+        vf[c] = g[u];            // g, read by every part below
+      }
     }
     __syncthreads();
     // s = g Q in pair arithmetic over this part's k
-    if (c < n) {
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      const int c = c0 + 64 * u;
+      if (c >= n) continue;
       float sh = 0.f, sl = 0.f;
       for (int k = k0; k < k1; ++k) {
         const float gk = vf[k], qh = Qh[k * n + c], ql = Ql[k * n + c];
@@ -723,33 +747,42 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
       red[4 * n + part * n + c] = sl;
     }
     __syncthreads();
-    float rfl = 0.f;
-    if (part == 0 && c < n) {
-      double s = 0.0;
+    float rfl[CPT];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) s += (double)red[q * n + c] + (double)red[4 * n + q * n + c];
-      rfl = (float)(pd[c] - s);
+    for (int u = 0; u < CPT; ++u) {
+      const int c = c0 + 64 * u;
+      rfl[u] = 0.f;
+      if (part == 0 && c < n) {
+        double sm = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sm += (double)red[q * n + c] + (double)red[4 * n + q * n + c];
+        rfl[u] = (float)(pd[c] - sm);
+      }
     }
     __syncthreads();
-    if (part == 0 && c < n) vf[c] = rfl;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      const int c = c0 + 64 * u;
+      if (part == 0 && c < n) vf[c] = rfl[u];
+    }
     __syncthreads();
     // g += r W32
-    if (c < n) {
-      float s0 = 0.f, s1 = 0.f;
-      int k = k0;
-      for (; k + 1 < k1; k += 2) {
-        s0 = fmaf(vf[k], Wm[k * n + c], s0);
-        s1 = fmaf(vf[k + 1], Wm[(k + 1) * n + c], s1);
-      }
-      if (k < k1) s0 = fmaf(vf[k], Wm[k * n + c], s0);
-      red[part * n + c] = s0 + s1;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      const int c = c0 + 64 * u;
+      if (c < n) red[part * n + c] = part_dot(c);
     }
     __syncthreads();
-    if (part == 0 && c < n) {
-      const float d = (red[c] + red[n + c]) + (red[2 * n + c] + red[3 * n + c]);
-      const double gv = (double)g + (double)d;
-      if (a.out64) a.out64[r * n + c] = gv;
-      if (a.out32) a.out32[r * n + c] = (float)gv;
+    if (part == 0) {
+#pragma unroll
+      for (int u = 0; u < CPT; ++u) {
+        const int c = c0 + 64 * u;
+        if (c >= n) continue;
+        const float d = (red[c] + red[n + c]) + (red[2 * n + c] + red[3 * n + c]);
+        const double gv = (double)g[u] + (double)d;
+        if (a.out64) a.out64[r * n + c] = gv;
+        if (a.out32) a.out32[r * n + c] = (float)gv;
+      }
     }
     __syncthreads();
   }
@@ -779,21 +812,22 @@ cudaError_t launch_split_pair(const double* Q, int64_t count, float* hi, float* 
   return cudaGetLastError();
 }
 
-bool apply_df_supported(int n) { return n >= 2 && n <= 64 && (n % 2) == 0; }
+bool apply_df_supported(int n) { return n >= 2 && n <= 128 && (n % 2) == 0; }
 
 cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, int n, const double* P, int64_t rows,
                             double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
   if (!apply_df_supported(n)) return cudaErrorInvalidValue;
   const size_t sm = apply_df_smem(n);
-  cudaError_t e = cudaFuncSetAttribute(apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto kern = n <= 64 ? apply_df_kernel<1> : apply_df_kernel<2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   ApplyDF a;
   a.W = W32; a.Qh = Qh; a.Ql = Ql; a.n = n; a.rows = rows; a.P = P;
   if (ps) a.ps = *ps;
   a.out64 = out64; a.out32 = out32; a.status = status;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 4));
-  launch_k(apply_df_kernel, (unsigned)blocks, 256, sm, s, a);
+  launch_k(kern, (unsigned)blocks, 256, sm, s, a);
   return cudaGetLastError();
 }
 
