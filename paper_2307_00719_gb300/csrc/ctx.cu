@@ -484,11 +484,76 @@ struct SlabView {
 str_status mttkrp_tc(str_ctx* c, const SlabView& v, int n, const void* const* cores, const double* G64k,
                      const double* base, double* out, cudaStream_t s, bool* used, PartialSum* defer);
 
+// Sampled MTTKRP (rSTR) on the tensor cores: rows of G_S and the weighted,
+// split GEMM operand; the gathered fibres; a split-K tcgen05 GEMM; the split
+// sum (here or deferred to the solve).  Returns without work (used = false)
+// when the slab type or sizes do not suit the tensor-core path.
+str_status mttkrp_sampled_tc(str_ctx* c, const SlabView& v, int n, const void* const* cores, const int32_t* idxs,
+                             bool lev, const double* const* pk, double wscale, const double* base, double* out,
+                             void* gs, double* ws, cudaStream_t s, bool* used, PartialSum* defer) {
+  *used = false;
+  if (v.xtype != XT_F32 && v.xtype != XT_BF16) return STR_OK;
+  const int RR = c->RR(n);
+  const int64_t In = v.dim[n];
+  const int64_t m = c->opt.m;
+  if (RR > 160 || In < 32 || m < 32) return STR_OK;
+  const int Npad = ((RR + 15) / 16) * 16;
+  const int Kpad = (int)(((m + 31) / 32) * 32);
+  const size_t es = v.xtype == XT_BF16 ? 2 : 4;
+  if (!tc_supported(Kpad, v.xtype, nullptr)) return STR_OK;
+  MttkrpArgs a;
+  a.X = v.X;
+  a.xtype = v.xtype;
+  a.N = c->N;
+  a.n = n;
+  for (int k = 0; k < c->N; ++k) { a.dim[k] = v.dim[k]; a.core[k] = cores[k]; }
+  for (int k = 0; k <= c->N; ++k) a.R[k] = c->R[k];
+  a.compute = 1;
+  a.nfib = m;
+  a.idxs = idxs;
+  a.m = m;
+  a.leverage = lev ? 1 : 0;
+  if (lev) for (int k = 0; k < c->N; ++k) a.p[k] = pk[k];
+  a.wscale = wscale;
+  a.gs_out = gs;
+  a.ws_out = ws;
+  TRY(grow(c, c->tc_bhi, (size_t)Npad * Kpad * 4));
+  TRY(grow(c, c->tc_blo, (size_t)Npad * Kpad * 4));
+  TRY(grow(c, c->tc_xt, (size_t)In * Kpad * es));
+  STR_CUDA_TRY(cudaMemsetAsync(c->tc_bhi.p, 0, (size_t)Npad * Kpad * 4, s));
+  STR_CUDA_TRY(cudaMemsetAsync(c->tc_blo.p, 0, (size_t)Npad * Kpad * 4, s));
+  LCHK(c, STR_K_SKETCH, launch_sampled_rows(a, Kpad, (float*)c->tc_bhi.p, (float*)c->tc_blo.p, s));
+  LCHK(c, STR_K_SKETCH, launch_gather_fibres(a, Kpad, c->tc_xt.p, s));
+  c->tc_xt_src = nullptr;   // the buffer no longer holds the transposed slab
+  const int mt = (int)((In + 127) / 128);
+  const int want = std::max(1, std::min(Kpad / 32, (2 * 152 + mt - 1) / mt));
+  const int splits = gemm_tc_splitk_count(Kpad, want);
+  TRY(grow(c, c->tc_part, (size_t)splits * In * RR * 4));
+  LCHK(c, STR_K_MTTKRP, launch_gemm_tc_splitk(c->tc_xt.p, v.xtype, In, Kpad, (const float*)c->tc_bhi.p,
+                                               (const float*)c->tc_blo.p, RR, Npad, splits, (float*)c->tc_part.p,
+                                               c->d_status, s));
+  if (defer) {
+    defer->part = (const float*)c->tc_part.p;
+    defer->splits = splits;
+    defer->base = base;
+    defer->pout = out;
+  } else {
+    LCHK(c, STR_K_REDUCE, launch_reduce_partials(c->tc_part.p, 1, 0, splits, In * RR, base, 1.0, out, s));
+  }
+  *used = true;
+  return STR_OK;
+}
+
 str_status mttkrp_into(str_ctx* c, const SlabView& v, int n, const void* const* cores, bool sampled,
                        const int32_t* idxs, bool lev, const double* const* pk, double wscale,
                        bool cplx, const double* base, double* out, void* gs, double* ws,
                        cudaStream_t s, PartialSum* defer = nullptr) {
   if (defer) *defer = PartialSum();
+  if (sampled && !cplx && c->compute == 1 && c->opt.mttkrp_path == 0) {
+    bool used = false;
+    TRY(mttkrp_sampled_tc(c, v, n, cores, idxs, lev, pk, wscale, base, out, gs, ws, s, &used, defer));
+    if (used) return STR_OK;
+  }
   if (!sampled && !cplx && c->compute == 1 && c->opt.mttkrp_path == 0) {
     const int kc = (n == 0) ? 1 : 0;
     bool used = false;

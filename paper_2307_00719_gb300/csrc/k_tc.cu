@@ -116,7 +116,9 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_kernel(const __grid_constant
                                                            const float* __restrict__ Bhi,
                                                            const float* __restrict__ Blo, int M,
                                                            int Kpad, int N, int Npad, uint32_t tmem_cols,
-                                                           float* __restrict__ Y, int* status) {
+                                                           float* __restrict__ Y, int* status, int cps) {
+  // cps > 0: split K -- CTA (x, y) takes the K chunks [y cps, (y + 1) cps) and
+  // writes its partial product to Y + y M N
   PDL_ENTRY();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -146,7 +148,10 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_kernel(const __grid_constant
   uint32_t ph_tma = 0, ph_mma = 0;
   bool failed = false;
   const int nchunks = Kpad / 32;
-  for (int c = 0; c < nchunks && !failed; ++c) {
+  const int cb = cps > 0 ? (int)blockIdx.y * cps : 0;
+  const int ce = cps > 0 ? min(nchunks, cb + cps) : nchunks;
+  if (cps > 0) Y += (size_t)blockIdx.y * (size_t)M * N;
+  for (int c = cb; c < ce && !failed; ++c) {
     if (tid == 0) {
       mbar_expect_tx(&bars[0], box_bytes);
       tma_load_2d(sAraw, &tmA, &bars[0], c * 32, m0);
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_kernel(const __grid_constant
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t adv = (uint64_t)(kk * 32) >> 4;   // 8 TF32 = 32 bytes along K
-        const int step = c * 4 + kk;
+        const int step = (c - cb) * 4 + kk;
         const uint32_t dhi = tmem + (uint32_t)((step & 1) * Npad);
         const uint32_t dx = tmem + (uint32_t)(2 * Npad);
         mma_tf32(dhi, ah + adv, bh + adv, idesc, step >= 2 ? 1u : 0u);
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(128, 1) stage1_tc_kernel(const __grid_constant
   tc_fence_after();
   if (!failed) {
     const int row = m0 + 32 * warp + lane;
-    const bool two = nchunks * 4 >= 2;   // the second hi*hi accumulator was written
+    const bool two = (ce - cb) * 4 >= 2;   // the second hi*hi accumulator was written
     for (int col = 0; col < Npad; col += 8) {
       const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col;
       uint32_t v0[8], v1[8], vx[8];
@@ -701,6 +706,94 @@ size_t stage2_smem_bytes(const Stage2Args& a) {
 }
 
 // ---------------------------------------------------------------------------
+// Sampled MTTKRP on the tensor cores (rSTR, Alg. 5 with the sampled subchain of
+// Alg. 3):  P_n += X_S[n] diag(w) G^{!=n}_S[2].
+//   sampled_rows_kernel: row s of G_S -- the chain G_{n+1}(i_{n+1}) ...
+//     G_{n-1}(i_{n-1}) of the sampled slices (column a + R_n b) -- and its
+//     weight w_s; also the GEMM operand B = diag(w) G_S, transposed and split
+//     into TF32 hi / lo terms.
+//   gather_fibres_kernel: A = X_S[n], row i_n, column s = the mode-n fibre of
+//     the slab at the sampled indices (K = samples contiguous, TMA-loadable).
+// The product then runs as a split-K tcgen05 GEMM (launch_gemm_tc_splitk).
+// ---------------------------------------------------------------------------
+__global__ void sampled_rows_kernel(MttkrpArgs a, int Kpad, float* __restrict__ Bhi, float* __restrict__ Blo) {
+  PDL_ENTRY();
+  const int N = a.N, n = a.n;
+  const int Ra = a.R[n], Rb = a.R[n + 1];
+  const int RR = Ra * Rb;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.m * Rb; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = e / Rb;
+    const int r = (int)(e - f * Rb);
+    double w = a.wscale;
+    float v[STR_MAXR], t[STR_MAXR];
+    int cols = 0;
+    for (int q = 0; q < N - 1; ++q) {
+      const int k = (n + 1 + q) % N;
+      const int i = a.idxs[(int64_t)k * a.m + f];
+      if (a.leverage) w /= a.p[k][i];
+      const int Rk = a.R[k], Rk1 = a.R[k + 1];
+      const float* g = (const float*)a.core[k] + (int64_t)i * Rk * Rk1;
+      if (q == 0) {
+#pragma unroll
+        for (int c = 0; c < STR_MAXR; ++c) v[c] = c < Rk1 ? g[r + Rk * c] : 0.f;
+      } else {
+#pragma unroll
+        for (int c = 0; c < STR_MAXR; ++c) {
+          float sum = 0.f;
+          if (c < Rk1)
+            for (int x = 0; x < cols; ++x) sum = fmaf(v[x], g[x + Rk * c], sum);
+          t[c] = sum;
+        }
+#pragma unroll
+        for (int c = 0; c < STR_MAXR; ++c) v[c] = t[c];
+      }
+      cols = Rk1;
+    }
+    // v[c], c < R_n: entry (b = r, a = c) of S_f -> column c + Ra r
+    float* gs = (float*)a.gs_out;
+    for (int c = 0; c < Ra; ++c) {
+      const int col = c + Ra * r;
+      if (gs) gs[f * RR + col] = v[c];
+      const double val = w * (double)v[c];
+      const float hi = tf32_rn((float)val);
+      Bhi[(int64_t)col * Kpad + f] = hi;
+      Blo[(int64_t)col * Kpad + f] = tf32_rn((float)(val - (double)hi));
+    }
+    if (r == 0 && a.ws_out) a.ws_out[f] = w;
+  }
+}
+
+// A[row][s] = X(mode-n fibre at the sampled indices of s, position row); 0 for s >= m
+template <typename XT>
+__global__ void gather_fibres_kernel(MttkrpArgs a, int Kpad, XT* __restrict__ A) {
+  PDL_ENTRY();
+  __shared__ int64_t sbase[32];
+  const int N = a.N, n = a.n;
+  const int64_t In = a.dim[n];
+  int64_t stride[STR_MAXN];
+  int64_t st = 1;
+  for (int k = 0; k < N; ++k) { stride[k] = st; st *= a.dim[k]; }
+  const int f = blockIdx.x * 32 + threadIdx.x;
+  if (threadIdx.y == 0) {
+    int64_t off = -1;
+    if (f < a.m) {
+      off = 0;
+      for (int k = 0; k < N; ++k)
+        if (k != n) off += (int64_t)a.idxs[(int64_t)k * a.m + f] * stride[k];
+    }
+    sbase[threadIdx.x] = off;
+  }
+  __syncthreads();
+  const int64_t off = sbase[threadIdx.x];
+  const XT* X = (const XT*)a.X;
+  for (int64_t row = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; row < In; row += (int64_t)gridDim.y * blockDim.y) {
+    XT v = (XT)0.f;
+    if (off >= 0) v = X[off + row * stride[n]];
+    if (f < Kpad) A[row * Kpad + f] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // tensor maps (driver entry point resolved once through the runtime)
 // ---------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -801,12 +894,76 @@ cudaError_t launch_stage1_tc(const void* Xa, int xtype, int64_t M, int K, const 
   if (bf16) {
     cudaError_t e = cudaFuncSetAttribute(stage1_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    launch_k(stage1_tc_kernel<true>, grid, 128, sm, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+    launch_k(stage1_tc_kernel<true>, grid, 128, sm, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status, 0);
   } else {
     cudaError_t e = cudaFuncSetAttribute(stage1_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    launch_k(stage1_tc_kernel<false>, grid, 128, sm, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status);
+    launch_k(stage1_tc_kernel<false>, grid, 128, sm, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status, 0);
   }
+  return cudaGetLastError();
+}
+
+// Y_part[y] = A[:, K_y] B[K_y, :] on the tensor cores: A row-major [M][Kpad]
+// (FP32 or BF16, K contiguous), B given as the split pair (Bhi, Blo) [Npad][Kpad];
+// the K chunks are divided over `splits` CTAs per 128-row tile (split K),
+// partial products in Y [splits][M][N]
+cudaError_t launch_gemm_tc_splitk(const void* A, int xtype, int64_t M, int Kpad, const float* Bhi,
+                                  const float* Blo, int N, int Npad, int splits, float* Y, int* status,
+                                  cudaStream_t s) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  const bool bf16 = xtype == XT_BF16;
+  const int es = bf16 ? 2 : 4;
+  if (Kpad % 32 != 0 || ((uintptr_t)A & 15) != 0 || splits < 1) return cudaErrorInvalidValue;
+  uint32_t cols = 32;
+  while ((int)cols < 3 * Npad) cols <<= 1;
+  if (cols > 512) return cudaErrorInvalidValue;
+  const int nch = Kpad / 32;
+  const int cps = (nch + splits - 1) / splits;
+  const int ns = (nch + cps - 1) / cps;   // every split has at least one chunk
+  CUtensorMap tm;
+  cuuint64_t gdim[2] = {(cuuint64_t)Kpad, (cuuint64_t)M};
+  cuuint64_t gstride[1] = {(cuuint64_t)Kpad * es};
+  cuuint32_t box[2] = {32, 128};
+  cuuint32_t estr[2] = {1, 1};
+  if (enc(&tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(A),
+          gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const size_t sm = stage1_smem_bytes(Npad);
+  dim3 grid((unsigned)((M + 127) / 128), (unsigned)ns);
+  if (bf16) {
+    cudaError_t e = cudaFuncSetAttribute(stage1_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    launch_k(stage1_tc_kernel<true>, grid, 128, sm, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status, cps);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(stage1_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    launch_k(stage1_tc_kernel<false>, grid, 128, sm, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols, Y, status, cps);
+  }
+  return cudaGetLastError();
+}
+
+int gemm_tc_splitk_count(int Kpad, int splits) {
+  const int nch = Kpad / 32;
+  const int cps = (nch + splits - 1) / splits;
+  return (nch + cps - 1) / cps;
+}
+
+cudaError_t launch_sampled_rows(const MttkrpArgs& a, int Kpad, float* Bhi, float* Blo, cudaStream_t s) {
+  const int64_t total = a.m * a.R[a.n + 1];
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, 152 * 8));
+  launch_k(sampled_rows_kernel, blocks, 128, 0, s, a, Kpad, Bhi, Blo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_fibres(const MttkrpArgs& a, int Kpad, void* A, cudaStream_t s) {
+  const int64_t In = a.dim[a.n];
+  dim3 block(32, 8);
+  dim3 grid((unsigned)(Kpad / 32), (unsigned)std::max<int64_t>(1, std::min<int64_t>((In + 7) / 8, 64)));
+  if (a.xtype == XT_BF16) launch_k(gather_fibres_kernel<__nv_bfloat16>, grid, block, 0, s, a, Kpad, (__nv_bfloat16*)A);
+  else if (a.xtype == XT_F32) launch_k(gather_fibres_kernel<float>, grid, block, 0, s, a, Kpad, (float*)A);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -169,5 +169,14 @@ cudaError_t launch_transpose01(const void* in, void* out, int xtype, int d0, int
 cudaError_t launch_stage1_tc(const void* Xa, int xtype, int64_t M, int K, const float* Bhi,
                              const float* Blo, int Kpad, int N, int Npad, float* Y, int* status,
                              cudaStream_t s);
+// sampled MTTKRP on the tensor cores: rows of G_S (+ weights, + split GEMM operand
+// B^T [Npad][Kpad], zero-filled by the caller), the gathered fibres A [I_n][Kpad],
+// and the split-K GEMM (partials [splits][M][N])
+cudaError_t launch_sampled_rows(const MttkrpArgs& a, int Kpad, float* Bhi, float* Blo, cudaStream_t s);
+cudaError_t launch_gather_fibres(const MttkrpArgs& a, int Kpad, void* A, cudaStream_t s);
+cudaError_t launch_gemm_tc_splitk(const void* A, int xtype, int64_t M, int Kpad, const float* Bhi,
+                                  const float* Blo, int N, int Npad, int splits, float* Y, int* status,
+                                  cudaStream_t s);
+int gemm_tc_splitk_count(int Kpad, int splits);
 int stage2_plan_splits(int64_t dn, int64_t ncomb, int64_t* per);
 cudaError_t launch_stage2(const Stage2Args& a, cudaStream_t s);
