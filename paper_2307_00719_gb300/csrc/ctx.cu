@@ -137,7 +137,7 @@ struct str_ctx {
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   bool side2_used = false;
   DevBuf mbuf[2];
-  DevBuf qf, qlo, fcount, ring2, ring3;
+  DevBuf qf, qlo, fcount, ring2, ring3, levx;
   const double* qsplit_of = nullptr;   // the Q whose FP32 pair (qf, qlo) is current   // FP32 copy of Q and the last-CTA counter of the fused ring GEMM + factor
 
   int RR(int n) const { return R[n] * R[n + 1]; }
@@ -457,6 +457,21 @@ str_status leverage(str_ctx* c, const double* G, int64_t I, int Ra, int Rb, doub
   TRY(grow(c, c->lfac, (size_t)RR * RR * 8));
   TRY(grow(c, c->invd, (size_t)RR * 8));
   LCHK(c, STR_K_GRAM, launch_core_gram(G, I, Ra, Rb, (double*)c->gram.p, nullptr, s));
+  if (c->compute == 1 && apply_df_supported(RR)) {
+    // FP32 slab arithmetic: x_i = g_i M^{-1} by the FP32 inverse with one
+    // refinement step whose residual is FP64-accurate (pair arithmetic), then
+    // l_i = g_i . x_i in FP64
+    TRY(grow(c, c->qf, (size_t)RR * RR * 4));
+    TRY(grow(c, c->qlo, (size_t)RR * RR * 4));
+    TRY(grow(c, c->levx, (size_t)I * RR * 8));
+    LCHK(c, STR_K_FACTOR, launch_factor_mixed((double*)c->gram.p, RR, (float*)c->lfac.p, c->d_status, nullptr, s));
+    LCHK(c, STR_K_SOLVE, launch_split_pair((double*)c->gram.p, (int64_t)RR * RR, (float*)c->qf.p, (float*)c->qlo.p, s));
+    c->qsplit_of = (const double*)c->gram.p;
+    LCHK(c, STR_K_SOLVE, launch_apply_df((const float*)c->lfac.p, (const float*)c->qf.p, (const float*)c->qlo.p, RR,
+                                         G, I, (double*)c->levx.p, nullptr, nullptr, c->d_status, s));
+    LCHK(c, STR_K_SOLVE, launch_leverage_dot(G, (const double*)c->levx.p, I, RR, p_out, s));
+    return STR_OK;
+  }
   LCHK(c, STR_K_FACTOR, launch_chol_factor((double*)c->gram.p, RR, (double*)c->lfac.p, (double*)c->invd.p, c->d_status, nullptr, s));
   LCHK(c, STR_K_SOLVE, launch_chol_solve((double*)c->lfac.p, (double*)c->invd.p, RR, G, I, nullptr, nullptr, p_out, s));
   return STR_OK;
@@ -532,7 +547,8 @@ str_status mttkrp_sampled_tc(str_ctx* c, const SlabView& v, int n, const void* c
   LCHK(c, STR_K_MTTKRP, launch_gemm_tc_splitk(c->tc_xt.p, v.xtype, In, Kpad, (const float*)c->tc_bhi.p,
                                                (const float*)c->tc_blo.p, RR, Npad, splits, (float*)c->tc_part.p,
                                                c->d_status, s));
-  if (defer) {
+  // many splits: a separate parallel reduction is cheaper than summing them in the solve
+  if (defer && splits <= 16) {
     defer->part = (const float*)c->tc_part.p;
     defer->splits = splits;
     defer->base = base;
@@ -1278,14 +1294,17 @@ str_status rstr_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
     TRY(gather_idx());
     pks(pk);
     const double wsn = sketch_wscale(c, n, v.dim);
+    PartialSum psn;   // the sampled MTTKRP's split partials, summed inside the solve
     if (ks) {
       TRY(mttkrp_into(c, sv, n, cores, true, idxcat, false, pk, wsn, true, nullptr, (double*)c->mtmp.p, c->gs.p, (double*)c->ws.p, s));
       LCHK(c, STR_K_DFT, launch_unmix_rows((double*)c->mtmp.p, c->I[n], RR, (const double*)c->sgn[n].p, c->P[n][c->cur[n]], c->P[n][w], s));
     } else {
-      TRY(mttkrp_into(c, sv, n, cores, true, idxcat, lev, pk, wsn, false, c->P[n][c->cur[n]], c->P[n][w], c->gs.p, (double*)c->ws.p, s));
+      TRY(mttkrp_into(c, sv, n, cores, true, idxcat, lev, pk, wsn, false, c->P[n][c->cur[n]], c->P[n][w], c->gs.p, (double*)c->ws.p, s, &psn));
     }
     LCHK(c, STR_K_SKETCH, launch_weighted_gram(c->gs.p, c->compute, ks ? 1 : 0, (double*)c->ws.p, m, RR, c->Q[n][c->cur[n]], c->Q[n][w], (double*)c->wg_part.p, s));
-    TRY(solve_rows(c, c->Q[n][w], RR, c->P[n][w], c->I[n], c->G64[n][w], c->compute == 1 ? c->G32[n][w] : nullptr, s));
+    TRY(factor_q(c, c->Q[n][w], RR, s));
+    TRY(apply_q(c, c->Q[n][w], RR, c->P[n][w], c->I[n], c->G64[n][w], c->compute == 1 ? c->G32[n][w] : nullptr, s,
+                &psn));
     c->upd[n] = 1;
     c->core_ver[n]++;
     if (levdraw) {

@@ -831,6 +831,29 @@ cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, 
   return cudaGetLastError();
 }
 
+// leverage scores from the solved rows: p_i = (g_i . x_i) / n with x_i = g_i M^{-1}
+// (FP64 dot per row, one warp per row)
+__global__ void leverage_dot_kernel(const double* __restrict__ G, const double* __restrict__ Xs, int64_t rows,
+                                    int n, double* __restrict__ p) {
+  PDL_ENTRY();
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double sum = 0.0;
+    for (int c = lane; c < n; c += 32) sum = fma(G[r * n + c], Xs[r * n + c], sum);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) p[r] = sum / n;
+  }
+}
+
+cudaError_t launch_leverage_dot(const double* G, const double* X, int64_t rows, int n, double* p, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, 152 * 8));
+  launch_k(leverage_dot_kernel, blocks, 256, 0, s, G, X, rows, n, p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_factor_mixed(const double* Q, int n, float* W32, int* status, double* pivot_ratio,
                                 cudaStream_t s) {
   return launch_sweep<float>(Q, n, W32, status, pivot_ratio, s);

@@ -92,6 +92,7 @@ cudaError_t launch_apply_mixed(const float* W32, const double* Q, int n, const d
 bool apply_df_supported(int n);
 cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, int n, const double* P, int64_t rows,
                             double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s);
+cudaError_t launch_leverage_dot(const double* G, const double* X, int64_t rows, int n, double* p, cudaStream_t s);
 cudaError_t launch_split_pair(const double* Q, int64_t count, float* hi, float* lo, cudaStream_t s);
 
 cudaError_t launch_solve_mixed(const double* Q, int n, const double* P, int64_t rows, int iters,
