@@ -34,7 +34,7 @@ METRIC = "STR/rSTR tensor entries/s per update, % roofline, rel. fit err vs FP64
 # DRAM bytes (read + write) of one stage-1 launch on the order-4 workload, from the
 # ncu capture summarised in profiles/ncu_str_order4_update_kernels.md; set to None
 # whenever the stage-1 kernel changes until it is captured again
-STAGE1_DRAM_BYTES = 10546944
+STAGE1_DRAM_BYTES = None
 W2 = synth.WORKLOADS["order4"]
 W3 = synth.WORKLOADS["rand3"]
 WORKLOAD_DESC = ("order4: 64x64x64xT, T=400, TR-ranks all 8, Gaussian cores, SNR 30 dB, "
@@ -233,7 +233,7 @@ def main_ours(a):
     tot = sum(k_ms.values())
     c_avg_ms = k_ms["contract"] / max(1, k_n["contract"])
     RRk = W2.ranks[0] * W2.ranks[1]
-    roofline = {"kernel": "stage1_tc_persist_kernel (tcgen05 kind::tf32, 3-term split, TMA-fed)",
+    roofline = {"kernel": "stage1_ws_kernel (tcgen05 kind::tf32, 3-term split, TMA-fed, warp-specialised)",
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_hbm, "unit": "GB/s",
                 "frac": round(achieved / peak_hbm, 4), "traffic": STAGE1_DRAM_BYTES,
                 "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch, ncu --set full "

@@ -12,27 +12,54 @@
 #include "ptx.cuh"
 
 // ---------------------------------------------------------------------------
-// core Gram: one thread per (c, c') pair with c <= c'; writes both halves
+// core Gram: one (c, c') pair with c <= c' per group of 4 threads (each sums
+// every 4th row; the partial sums are added in a fixed order); the rows of G
+// are staged in shared memory in chunks (cp.async), so the FMA chains read
+// shared memory.  Writes both halves.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) core_gram_kernel(const double* __restrict__ G, int64_t I, int Ra,
                                                         int Rb, double* __restrict__ M,
-                                                        double* __restrict__ E) {
+                                                        double* __restrict__ E, int chunk) {
   PDL_ENTRY();
-  // 64 pairs per CTA, 4 threads per pair each summing every 4th row; the four
-  // partial sums are added in a fixed order
+  extern __shared__ __align__(16) double sg[];   // chunk x RR
   __shared__ double red[4][64];
   const int RR = Ra * Rb;
   const int64_t npairs = (int64_t)RR * (RR + 1) / 2;
   const int p = threadIdx.x & 63, q = threadIdx.x >> 6;
   const int64_t t = (int64_t)blockIdx.x * 64 + p;
   int c = 0, cp = 0;
-  double s = 0.0;
   if (t < npairs) {
-    // decode t -> (c, c') with c <= c'  (row-wise over the upper triangle)
-    int64_t rem = t;
-    while (rem >= RR - c) { rem -= RR - c; ++c; }
-    cp = c + (int)rem;
-    for (int64_t i = q; i < I; i += 4) s = fma(G[i * RR + c], G[i * RR + cp], s);
+    // row c of the upper triangle starts at c RR - c (c - 1) / 2
+    const double b2 = 2.0 * RR + 1.0;
+    c = (int)floor((b2 - sqrt(b2 * b2 - 8.0 * (double)t)) * 0.5);
+    if (c < 0) c = 0;
+    while (c > 0 && (int64_t)c * RR - (int64_t)c * (c - 1) / 2 > t) --c;
+    while ((int64_t)(c + 1) * RR - (int64_t)(c + 1) * c / 2 <= t) ++c;
+    cp = c + (int)(t - ((int64_t)c * RR - (int64_t)c * (c - 1) / 2));
+  }
+  double s = 0.0;
+  const bool vec = ((RR & 1) == 0) && ((((uintptr_t)G) & 15) == 0);
+  for (int64_t i0 = 0; i0 < I; i0 += chunk) {
+    const int nr = (int)min((int64_t)chunk, I - i0);
+    const int64_t cnt = (int64_t)nr * RR;
+    if (vec) {
+      for (int64_t e = 2 * threadIdx.x; e < cnt; e += 2 * blockDim.x) cp_async16(&sg[e], &G[i0 * RR + e]);
+    } else {
+      for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) cp_async8(&sg[e], &G[i0 * RR + e]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (t < npairs) {
+      double s0 = 0.0, s1 = 0.0;
+      int i = q;
+      for (; i + 4 < nr; i += 8) {
+        s0 = fma(sg[i * RR + c], sg[i * RR + cp], s0);
+        s1 = fma(sg[(i + 4) * RR + c], sg[(i + 4) * RR + cp], s1);
+      }
+      if (i < nr) s0 = fma(sg[i * RR + c], sg[i * RR + cp], s0);
+      s += s0 + s1;
+    }
+    __syncthreads();
   }
   red[q][p] = s;
   __syncthreads();
@@ -53,7 +80,11 @@ cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double*
   const int RR = Ra * Rb;
   const int64_t npairs = (int64_t)RR * (RR + 1) / 2;
   const int64_t blocks = std::max<int64_t>(1, (npairs + 63) / 64);
-  launch_k(core_gram_kernel, (unsigned)blocks, 256, 0, s, G, I, Ra, Rb, M, E);
+  // rows per staged chunk: at most 44 KB of dynamic shared memory (with the
+  // kernel's static 2 KB, under the default 48 KB limit)
+  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(I, (44 * 1024) / (8 * (int64_t)RR)));
+  const size_t sm = (size_t)chunk * RR * 8;
+  launch_k(core_gram_kernel, (unsigned)blocks, 256, sm, s, G, I, Ra, Rb, M, E, chunk);
   return cudaGetLastError();
 }
 

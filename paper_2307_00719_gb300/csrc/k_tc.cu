@@ -411,6 +411,222 @@ size_t stage1_persist_smem_bytes(int Npad, int nch, bool bf16) {
 }
 
 // ---------------------------------------------------------------------------
+// stage 1, warp-specialised persistent form (192 threads):
+//   warp 0       TMA producer: X tiles into a ring of SA slots
+//   warp 1       MMA issuer (one thread): 3-term TF32 products into one of two
+//                TMEM accumulator sets, then commits that free the X slot and
+//                the X_lo slot and publish the accumulator
+//   warps 2-5    workers: X_lo = rn(X - trunc(X)) (BF16: the widened X) into
+//                one of two slots, then the epilogue of the previous tile
+//                (TMEM lanes 32 (warp % 4) .. + 31) while the MMA of the next
+//                tile runs
+// mbarriers: fullA/emptyA per X slot, fullLo/emptyLo per X_lo slot,
+// accFull/accEmpty per accumulator set, bReady for the resident B operand.
+// Every wait is bounded (2 s); a role whose wait times out stops and records
+// DEV_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+template <bool SRC_BF16, int SA>
+__global__ void __launch_bounds__(192, 1) stage1_ws_kernel(
+    const __grid_constant__ CUtensorMap tmA, const float* __restrict__ Bhi, const float* __restrict__ Blo,
+    int M, int Kpad, int N, int Npad, uint32_t tmem_cols, float* __restrict__ Y, int* status) {
+  PDL_ENTRY();
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int nch = Kpad / 32;
+  const size_t bchunk = (size_t)Npad * 128;
+  constexpr uint32_t kRaw = SRC_BF16 ? 8192u : 16384u;   // one X chunk in the ring
+  unsigned char* sBhi = smem;                            // nch x Npad x 128 B
+  unsigned char* sBlo = sBhi + nch * bchunk;
+  unsigned char* sA = sBlo + nch * bchunk;               // SA slots x nch x kRaw
+  unsigned char* sLo = sA + (size_t)SA * nch * kRaw;     // 2 slots x nch x 16 KB
+  uint64_t* bars = (uint64_t*)(sLo + (size_t)2 * nch * 16384);
+  uint64_t* fullA = bars;
+  uint64_t* emptyA = bars + SA;
+  uint64_t* fullLo = bars + 2 * SA;
+  uint64_t* emptyLo = fullLo + 2;
+  uint64_t* accFull = emptyLo + 2;
+  uint64_t* accEmpty = accFull + 2;
+  uint64_t* bReady = accEmpty + 2;
+  uint32_t* tslot = (uint32_t*)(bReady + 1);
+  int* s_fail = (int*)(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = (M + 127) / 128;
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp == 1) tmem_alloc(tslot, tmem_cols);
+  if (tid == 0) {
+    for (int i = 0; i < SA; ++i) { mbar_init(&fullA[i], 1); mbar_init(&emptyA[i], 1); }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&fullLo[i], 4);
+      mbar_init(&emptyLo[i], 1);
+      mbar_init(&accFull[i], 1);
+      mbar_init(&accEmpty[i], 4);
+    }
+    mbar_init(bReady, 128);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  bool failed = false;
+
+  if (warp == 0) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      for (int j = 0; j < my_tiles; ++j) {
+        const int a = j % SA, ua = j / SA;
+        if (!mbar_wait(&emptyA[a], (ua & 1) ^ 1, kWaitNs)) { failed = true; break; }
+        const int t = blockIdx.x + j * gridDim.x;
+        mbar_expect_tx(&fullA[a], kRaw * nch);
+        for (int c = 0; c < nch; ++c)
+          tma_load_2d(sA + ((size_t)a * nch + c) * kRaw, &tmA, &fullA[a], c * 32, t * 128);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Npad >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+      if (!mbar_wait(bReady, 0, kWaitNs)) failed = true;
+      for (int j = 0; j < my_tiles && !failed; ++j) {
+        const int a = j % SA, l = j & 1, ul = j >> 1;
+        if (!mbar_wait(&fullLo[l], ul & 1, kWaitNs)) { failed = true; break; }
+        if (!mbar_wait(&accEmpty[l], (ul & 1) ^ 1, kWaitNs)) { failed = true; break; }
+        tc_fence_after();
+        const uint32_t base = tmem + (uint32_t)(l * 3 * Npad);
+        for (int c = 0; c < nch; ++c) {
+          const unsigned char* ahp = SRC_BF16 ? sLo + ((size_t)l * nch + c) * 16384 : sA + ((size_t)a * nch + c) * kRaw;
+          const uint64_t ah = desc_sw128(ahp);
+          const uint64_t al = desc_sw128(sLo + ((size_t)l * nch + c) * 16384);
+          const uint64_t bh = desc_sw128(sBhi + c * bchunk), bl = desc_sw128(sBlo + c * bchunk);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+            const int step = c * 4 + kk;
+            const uint32_t dhi = base + (uint32_t)((step & 1) * Npad);
+            const uint32_t dx = base + (uint32_t)(2 * Npad);
+            mma_tf32(dhi, ah + adv, bh + adv, idesc, step >= 2 ? 1u : 0u);
+            mma_tf32(dx, ah + adv, bl + adv, idesc, step >= 1 ? 1u : 0u);
+            if (!SRC_BF16) mma_tf32(dx, al + adv, bh + adv, idesc, 1u);
+          }
+        }
+        mma_commit(&accFull[l]);
+        mma_commit(&emptyA[a]);
+        mma_commit(&emptyLo[l]);
+      }
+      // the last products complete before TMEM is released
+      if (!failed && my_tiles > 0) {
+        const int jl = my_tiles - 1;
+        if (!mbar_wait(&accFull[jl & 1], (jl >> 1) & 1, kWaitNs)) failed = true;
+      }
+    }
+  } else {
+    // ---- workers: B staging, X_lo, epilogue ----
+    const int wt = tid - 64;                 // 0..127
+    const int q = warp & 3;                  // TMEM lane quadrant of this warp
+    for (int c = 0; c < nch; ++c)
+      for (int r = wt >> 3; r < Npad; r += 16) {
+        const int jx = wt & 7;
+        cp_async16(sBhi + c * bchunk + sw128_off(r, jx), Bhi + (size_t)r * Kpad + c * 32 + jx * 4);
+        cp_async16(sBlo + c * bchunk + sw128_off(r, jx), Blo + (size_t)r * Kpad + c * 32 + jx * 4);
+      }
+    cp_async_wait_all();
+    fence_proxy_async();
+    mbar_arrive(bReady);
+    const bool vec = (N & 3) == 0;
+    for (int j = 0; j <= my_tiles && !failed; ++j) {
+      if (j < my_tiles) {
+        const int a = j % SA, ua = j / SA, l = j & 1, ul = j >> 1;
+        if (!mbar_wait(&fullA[a], ua & 1, kWaitNs)) { failed = true; break; }
+        if (!mbar_wait(&emptyLo[l], (ul & 1) ^ 1, kWaitNs)) { failed = true; break; }
+        const unsigned char* araw = sA + (size_t)a * nch * kRaw;
+        unsigned char* lo = sLo + (size_t)l * nch * 16384;
+        if (!SRC_BF16) {
+          for (int e = wt; e < nch * 1024; e += 128 * 4) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (e + 128 * u < nch * 1024) v[u] = *(const float4*)(araw + (size_t)(e + 128 * u) * 16);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (e + 128 * u >= nch * 1024) continue;
+              const float4 x = v[u];
+              const float4 h = make_float4(__uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u),
+                                           __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u),
+                                           __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u),
+                                           __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u));
+              *(float4*)(lo + (size_t)(e + 128 * u) * 16) =
+                  make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
+            }
+          }
+        } else {
+          for (int c = 0; c < nch; ++c) {
+            const unsigned char* raw = araw + (size_t)c * kRaw;
+            unsigned char* ah = lo + (size_t)c * 16384;
+            for (int p = 0; p < 8; ++p) {
+              const int r = p * 16 + (wt >> 3);
+              const int jx = wt & 7;
+              const __nv_bfloat162* qv = (const __nv_bfloat162*)(raw + r * 64 + jx * 8);
+              const float2 x0 = __bfloat1622float2(qv[0]), x1 = __bfloat1622float2(qv[1]);
+              *(float4*)(ah + sw128_off(r, jx)) = make_float4(x0.x, x0.y, x1.x, x1.y);
+            }
+          }
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&fullLo[l]);
+      }
+      if (j >= 1) {
+        const int jp = j - 1, r = jp & 1, ur = jp >> 1;
+        if (!mbar_wait(&accFull[r], ur & 1, kWaitNs)) { failed = true; break; }
+        tc_fence_after();
+        const int t = blockIdx.x + jp * gridDim.x;
+        const int row = t * 128 + 32 * q + lane;
+        const uint32_t abase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(r * 3 * Npad);
+        for (int col = 0; col < Npad; col += 16) {
+          uint32_t v0[16], v1[16], vx[16];
+          tmem_ld_x16_nw(abase + (uint32_t)col, v0);
+          tmem_ld_x16_nw(abase + (uint32_t)(Npad + col), v1);
+          tmem_ld_x16_nw(abase + (uint32_t)(2 * Npad + col), vx);
+          tmem_wait_ld();
+          if (row < M) {
+            float y[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+              y[u] = (__uint_as_float(v0[u]) + __uint_as_float(vx[u])) + __uint_as_float(v1[u]);
+            float* yrow = Y + (size_t)row * N + col;
+            if (vec && col + 16 <= N) {
+#pragma unroll
+              for (int u = 0; u < 16; u += 4) *(float4*)(yrow + u) = make_float4(y[u], y[u + 1], y[u + 2], y[u + 3]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 16; ++u)
+                if (col + u < N) yrow[u] = y[u];
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accEmpty[r]);
+      }
+    }
+  }
+  if (failed) *s_fail = 1;
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *s_fail) atomicOr(status, DEV_ERR_TIMEOUT);
+  if (warp == 1) tmem_dealloc(tmem, tmem_cols);
+}
+
+size_t stage1_ws_smem_bytes(int Npad, int nch, bool bf16, int sa) {
+  const size_t b = (size_t)2 * nch * Npad * 128;
+  const size_t raw = (size_t)sa * nch * (bf16 ? 8192 : 16384);
+  return 1024 + b + raw + (size_t)2 * nch * 16384 + 256;
+}
+
+// ---------------------------------------------------------------------------
 // operand prep: B^T split, [Npad][Kpad], zero padded
 // ---------------------------------------------------------------------------
 __global__ void prep_b_kernel(const double* __restrict__ G, int K, int N, int Kpad, int Npad,
@@ -872,6 +1088,26 @@ cudaError_t launch_stage1_tc(const void* Xa, int xtype, int64_t M, int K, const 
   };
   CUtensorMap tm;
   if (encode(&tm, persist && !bf16) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  // warp-specialised persistent kernel when its rings fit (3 X slots, else 2)
+  // and two accumulator sets of 3 Npad TMEM columns each fit in 512 columns
+  const size_t ws3 = stage1_ws_smem_bytes(Npad, nch, bf16, 3), ws2 = stage1_ws_smem_bytes(Npad, nch, bf16, 2);
+  uint32_t cols_ws = 32;
+  while ((int)cols_ws < 6 * Npad) cols_ws <<= 1;
+  if (persist && ws2 <= 225 * 1024 && cols_ws <= 512) {
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (M + 127) / 128;
+    const unsigned gridp = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, sms));
+    const bool three = ws3 <= 225 * 1024;
+    const size_t smw = three ? ws3 : ws2;
+    auto kern = bf16 ? (three ? stage1_ws_kernel<true, 3> : stage1_ws_kernel<true, 2>)
+                     : (three ? stage1_ws_kernel<false, 3> : stage1_ws_kernel<false, 2>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
+    if (e != cudaSuccess) return e;
+    launch_k(kern, gridp, 192, smw, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols_ws, Y, status);
+    return cudaGetLastError();
+  }
   if (persist) {
     int sms = 152;
     int dev = 0;
