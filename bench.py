@@ -52,6 +52,7 @@ def args_parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU arm")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-streams row")
+    ap.add_argument("--no-loss", action="store_true", help="skip the masked-loss row")
     return ap.parse_args()
 
 
@@ -314,6 +315,8 @@ def main_ours(a):
         out["rstr"] = rstr_rows(p, torch, flush, rank)
     if not a.no_batch:
         out["batch"] = batch_rows(p, torch, flush, rank)
+    if not a.no_loss:
+        out["loss"] = loss_rows(p, torch, flush, rank, peak_hbm)
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     if rank == 0 and world == 1 and not a.no_cpu:
         out["cpu_baseline"] = cpu_baseline(X, cores0)
@@ -424,6 +427,52 @@ def batch_rows(p, torch, flush, rank, steps=4, warmup=6, count=256):
             "workload": (f"{count} independent order-3 streams, spatial dims uniform in [16,128], TR-ranks "
                          "in {2..12}, 1-16 new slices per step (fixed per stream), BF16 slabs, FP32 slab-side "
                          "arithmetic, 1 sweep; one str_update_batch per step vs one str_update per stream")}
+
+
+def loss_rows(p, torch, flush, rank, peak_hbm, steps=3, warmup=3):
+    """Masked TR fit loss and its backward on the 32x32x32x32x100 FP32 tensor
+    (TR-ranks 6, 30% of the entries hidden, mask as packed bits): one forward
+    (loss) and one backward (gradients of all five cores) per step.  The tensor
+    is the TR tensor of Gaussian cores (no noise), made on the device by the
+    library's reconstruction."""
+    W = synth.WORKLOADS["masked5"]
+    dims = tuple(W.dims) + (W.T,)
+    seed = W.seed + 1000 * rank
+    G = synth.gaussian_cores(dims, W.ranks, seed)
+    truth = p.str_init_cores(G, X0=None, t_capacity=W.T)
+    X = p.paper_layout(truth.reconstruct(0, W.T, dtype=torch.float32))
+    truth.close()
+    bits = torch.from_numpy(synth.pack_mask_bits(synth.bernoulli_keep_mask(dims, 0.3, seed))
+                            .view(np.int32)).cuda()
+    cores = [torch.from_numpy(a).to("cuda", torch.float32) for a in p.cores_to_abi(G)]
+    E = int(np.prod(dims))
+
+    def timed(fn):
+        stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for j in range(steps):
+                flush.zero_()
+                evs[j][0].record(stream)
+                fn()
+                evs[j][1].record(stream)
+            torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+    ms_f = timed(lambda: p.tr_masked_loss_fwd(cores, X, bits))
+    ms_b = timed(lambda: p.tr_masked_loss_bwd(cores, X, bits, 1.0))
+    loss = float(p.tr_masked_loss_fwd(cores, X, bits).item())
+    in_bytes = E * 4 + bits.numel() * 4
+    return {"value": E / ((ms_f + ms_b) / 1e3), "unit": "entries/s", "ms_fwd": ms_f, "ms_bwd": ms_b,
+            "fwd_read_gbs": in_bytes / (ms_f / 1e3) / 1e9, "fwd_frac_of_measured_hbm": in_bytes / (ms_f / 1e3) / 1e9 / peak_hbm,
+            "t_bound_fused_fwd_bwd_ms": in_bytes / (peak_hbm * 1e9) * 1e3, "loss": loss,
+            "workload": ("masked5: 32x32x32x32x100 FP32 (104.9 M entries, 419 MB), TR-ranks all 6, Bernoulli(0.3) "
+                         "hidden entries as packed mask bits; one tr_masked_loss_fwd + one tr_masked_loss_bwd "
+                         "(all 5 core gradients) per step")}
 
 
 # ---------------------------------------------------------------------------

@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <mutex>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "kernels.cuh"
@@ -24,23 +25,20 @@
 static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_next_uid{1};
 static uint64_t next_uid() { return g_next_uid.fetch_add(1); }
+// streams that waited on an event since their last kernel launch: every mark is
+// kept until that stream's next launch takes it (a lost mark would let a kernel
+// overlap, through programmatic serialisation, work it must wait for in full)
 namespace {
-thread_local cudaStream_t g_cross_wait[16];
-thread_local int g_cross_n = 0;
+std::mutex g_cross_mu;
+std::unordered_set<cudaStream_t> g_cross_wait;
 }
 void str_mark_cross_wait(cudaStream_t s) {
-  for (int i = 0; i < g_cross_n; ++i)
-    if (g_cross_wait[i] == s) return;
-  if (g_cross_n < 16) g_cross_wait[g_cross_n++] = s;
-  else g_cross_wait[15] = s;
+  std::lock_guard<std::mutex> lk(g_cross_mu);
+  g_cross_wait.insert(s);
 }
 bool str_take_cross_wait(cudaStream_t s) {
-  for (int i = 0; i < g_cross_n; ++i)
-    if (g_cross_wait[i] == s) {
-      g_cross_wait[i] = g_cross_wait[--g_cross_n];
-      return true;
-    }
-  return false;
+  std::lock_guard<std::mutex> lk(g_cross_mu);
+  return g_cross_wait.erase(s) > 0;
 }
 // cudaStreamWaitEvent that also marks the stream (see str_mark_cross_wait)
 static cudaError_t wait_event(cudaStream_t s, cudaEvent_t e) {
@@ -138,6 +136,7 @@ struct str_ctx {
   bool side2_used = false;
   DevBuf mbuf[2];
   DevBuf qf, qlo, fcount, ring2, ring3, levx;
+  bool fcount_dirty = false;     // fcount allocated but not yet cleared on a stream
   const double* qsplit_of = nullptr;   // the Q whose FP32 pair (qf, qlo) is current   // FP32 copy of Q and the last-CTA counter of the fused ring GEMM + factor
 
   int RR(int n) const { return R[n] * R[n + 1]; }
@@ -187,14 +186,39 @@ cudaEvent_t ev_get(str_ctx* c) {
     LCHK(ctx, cls, expr);           \
   } while (0)
 
+// New buffers are zeroed before any stream can use them: the zeroing runs on
+// the legacy stream, which does not order the non-blocking streams the library
+// works on, so it is waited for.  Inside one of the library's own graph captures
+// (which a new buffer makes run again directly) the zeroing is deferred to
+// zero_pending(), called before that direct run.
+thread_local bool g_in_capture = false;
+thread_local std::vector<std::pair<void*, size_t>> g_zero_pending;
+
+str_status zero_now(void* p, size_t bytes) {
+  if (cudaMemset(p, 0, bytes) != cudaSuccess || cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
+    cudaGetLastError();
+    return STR_ERR_CUDA;
+  }
+  return STR_OK;
+}
+
+str_status zero_pending() {
+  str_status st = STR_OK;
+  for (auto& z : g_zero_pending)
+    if (st == STR_OK) st = zero_now(z.first, z.second);
+  g_zero_pending.clear();
+  return st;
+}
+
 str_status dalloc(str_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) { *p = nullptr; cudaGetLastError(); return from_cuda(e, "cudaMalloc"); }
-  cudaMemset(*p, 0, bytes);
   c->owned.push_back(*p);
   c->bytes += bytes;
+  if (g_in_capture) g_zero_pending.emplace_back(*p, bytes);
+  else TRY(zero_now(*p, bytes));
   return STR_OK;
 }
 
@@ -210,6 +234,8 @@ str_status grow(str_ctx* c, DevBuf& b, size_t bytes) {
   if (b.p) {
     auto it = std::find(c->owned.begin(), c->owned.end(), b.p);
     if (it != c->owned.end()) c->owned.erase(it);
+    for (auto z = g_zero_pending.begin(); z != g_zero_pending.end();)
+      z = z->first == b.p ? g_zero_pending.erase(z) : z + 1;
     cudaFree(b.p);
     c->bytes -= b.cap;
   }
@@ -349,7 +375,20 @@ str_status ring_last_factor(str_ctx* c, int n, const double* M, const double* EN
   TRY(grow(c, c->invd, (size_t)RRn * 8));
   TRY(grow(c, c->qf, (size_t)RRn * RRn * 4));
   TRY(grow(c, c->qlo, (size_t)RRn * RRn * 4));
+  // the last-CTA counter must start at zero (each launch leaves it at zero again):
+  // a new buffer is cleared on the stream that runs the kernel, outside any capture
+  // (a buffer grown during a capture makes the capture run again directly)
+  const void* fc_old = c->fcount.p;
   TRY(grow(c, c->fcount, 16));
+  if (c->fcount.p != fc_old) c->fcount_dirty = true;
+  if (c->fcount_dirty) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    STR_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      STR_CUDA_TRY(cudaMemsetAsync(c->fcount.p, 0, 16, s));
+      c->fcount_dirty = false;
+    }
+  }
   LCHK(c, STR_K_FACTOR, launch_gemm64_factor(M, El, Qout, c->R[f0] * c->R[f0], c->R[kl] * c->R[kl],
                                              c->R[kl + 1] * c->R[kl + 1], c->R[n], c->R[n + 1], base,
                                              (float*)c->qf.p, (float*)c->qlo.p, (float*)c->lfac.p,
@@ -876,6 +915,9 @@ str_status ctx_create(str_ctx** out, int N, const int64_t* dims, const int* rank
   if (cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess) return fail(STR_ERR_OOM);
   if (cudaMallocHost(&c->h_sums, 4 * sizeof(double)) != cudaSuccess) return fail(STR_ERR_OOM);
   *c->h_status = 0;
+  // dalloc zeroes on the legacy stream, which does not order the non-blocking
+  // streams the updates run on: finish the zeroing before any of them starts
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(STR_ERR_CUDA);
   *out = c;
   return STR_OK;
 }
@@ -1186,9 +1228,15 @@ str_status str_step_graph(str_ctx* c, SlabView& v, int64_t count, size_t es, cud
   }
   const uint64_t gen0 = c->gen;
   STR_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  g_in_capture = true;
   str_status st = str_step(c, v, s);
   cudaGraph_t graph = nullptr;
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  g_in_capture = false;
+  {
+    const str_status zs = zero_pending();
+    if (st == STR_OK) st = zs;
+  }
   if (st != STR_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   if (ce != cudaSuccess || c->gen != gen0) {
     // nothing recorded was executed: forget the capture's host-side bookkeeping
@@ -1408,6 +1456,7 @@ str_status str_init_cores(str_ctx** out, int N, const int64_t* dims, const int* 
   str_ctx* c = nullptr;
   TRY(ctx_create(&c, N, dims, ranks, opt, t_init));
   cudaStream_t s = (cudaStream_t)stream;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
   str_status st = upload_cores(c, cores, s);
   if (st == STR_OK && X0) {
     SlabView v;
@@ -1439,6 +1488,7 @@ str_status str_init(str_ctx** out, const str_tensor* X0, const int* ranks, const
   str_ctx* c = nullptr;
   TRY(ctx_create(&c, N, X0->dims, ranks, &o, t_init));
   cudaStream_t s = (cudaStream_t)stream;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
   str_status st = upload_cores(c, guess, s);
   SlabView v;
   if (st == STR_OK) st = take_slab(c, X0, &v, s);
@@ -1495,6 +1545,7 @@ str_status str_init(str_ctx** out, const str_tensor* X0, const int* ranks, const
 str_status str_update(str_ctx* c, const str_tensor* X, void* stream) {
   if (!c) return STR_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
   TRY(precheck(c, s));
   c->launches = 0;
   SlabView v;
@@ -1524,6 +1575,7 @@ str_status rstr_update(str_ctx* c, const str_tensor* X, str_sketch type, int64_t
   if (c->opt.sketch == STR_SKETCH_NONE || type != c->opt.sketch || m != c->opt.m || seed != c->opt.seed)
     return STR_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
   TRY(precheck(c, s));
   c->launches = 0;
   SlabView v;
@@ -1618,6 +1670,7 @@ str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, in
                             void* stream) {
   if (!ctxs || !X || count < 0) return STR_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
   // enqueue every context's step with status checks deferred, then commit all or none
   std::vector<int64_t> tns(count);
   for (int i = 0; i < count; ++i) {
@@ -1701,8 +1754,14 @@ str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, in
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = STR_ERR_CUDA;
         if (st == STR_OK) {
+          g_in_capture = true;
           st = batch_steps(ctxs, v, count, s);
           const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+          g_in_capture = false;
+          {
+            const str_status zs = zero_pending();
+            if (st == STR_OK) st = zs;
+          }
           bool moved = false;
           for (int i = 0; i < count; ++i) moved = moved || ctxs[i]->gen != gen0[i];
           if (st == STR_OK && (ce != cudaSuccess || moved)) {
@@ -1793,6 +1852,7 @@ str_status tr_fit_error(const str_ctx* cc, const str_tensor* X, int64_t t0, doub
   if (!cc || !X || !rel_err || !X->data || !X->dims) return STR_ERR_INVALID_ARG;
   str_ctx* c = const_cast<str_ctx*>(cc);
   cudaStream_t s = (cudaStream_t)stream;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
   if (X->order != c->N) return STR_ERR_SHAPE;
   for (int k = 0; k < c->N - 1; ++k) if (X->dims[k] != c->I[k]) return STR_ERR_SHAPE;
   const int64_t t = X->dims[c->N - 1];
@@ -1941,6 +2001,7 @@ str_status str_load(str_ctx** out, const void* buf, size_t len, void* stream) {
   c->I[N - 1] = h.I[N - 1];
   if (save_size(c, &h2) > len) { str_destroy(c); return STR_ERR_INVALID_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
   const char* p = (const char*)buf + sizeof(SaveHeader);
   str_status st = STR_OK;
   auto h2d = [&](void* dst, size_t bytes) {
@@ -1969,7 +2030,8 @@ str_status str_load(str_ctx** out, const void* buf, size_t len, void* stream) {
   }
   c->step = h.step;
   c->last_tn = h.last_tn;
-  if (st == STR_OK) st = from_cuda(cudaStreamSynchronize(s), "sync");
+  // the uploads ran on the legacy stream: complete them before any other stream reads
+  if (st == STR_OK) st = from_cuda(cudaDeviceSynchronize(), "sync");
   if (st != STR_OK) { str_destroy(c); return st; }
   *out = c;
   return STR_OK;
@@ -2062,13 +2124,13 @@ void str_destroy(str_ctx* c) {
   forget_batch_graphs(c->uid);
   if (c->ev_bfork) cudaEventDestroy(c->ev_bfork);
   if (c->ev_bjoin) cudaEventDestroy(c->ev_bjoin);
-  if (c->bstream) cudaStreamDestroy(c->bstream);
+  if (c->bstream) { str_take_cross_wait(c->bstream); cudaStreamDestroy(c->bstream); }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
-  if (c->side) cudaStreamDestroy(c->side);
+  if (c->side) { str_take_cross_wait(c->side); cudaStreamDestroy(c->side); }
   if (c->ev_fork2) cudaEventDestroy(c->ev_fork2);
   if (c->ev_join2) cudaEventDestroy(c->ev_join2);
-  if (c->side2) cudaStreamDestroy(c->side2);
+  if (c->side2) { str_take_cross_wait(c->side2); cudaStreamDestroy(c->side2); }
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_sums) cudaFreeHost(c->h_sums);
   delete c;
@@ -2092,6 +2154,109 @@ static str_status loss_setup(int N, const int64_t* dims, const int* ranks, str_d
   return STR_OK;
 }
 
+// Split of the modes into a prefix 1..k and a suffix k+1..N for the fused loss
+// pass (1 <= k <= N-2, K = R_1 R_{k+1} <= 64): the one with the least work in the
+// reduced MTTKRPs of the backward (a prefix of one core needs none).  0 = none.
+static int loss_split(int N, const int64_t* dims, const int* R) {
+  int best_k = 0;
+  double best = 1e300;
+  for (int k = 1; k <= N - 2; ++k) {
+    const int K = R[0] * R[k];
+    if (K > 64) continue;
+    double rows = 1, cols = 1;
+    for (int j = 0; j < k; ++j) rows *= (double)dims[j];
+    for (int j = k; j < N; ++j) cols *= (double)dims[j];
+    const double cost = ((k > 1 ? k * rows : 0.0) + (N - k) * cols + rows + cols) * K;
+    if (cost < best) { best = cost; best_k = k; }
+  }
+  return best_k;
+}
+
+// Backward by one fused pass over X: Z (prefix side) and W (suffix side), then
+// the gradient of each core as the MTTKRP of Z or W over a reduced trace
+// problem in which a unit core stands for the other side's product:
+//   prefix modes: tensor Z(i_1..i_k, c), cores G_1..G_k, U;
+//   suffix modes: tensor W(c, i_{k+1}..i_N), cores V, G_{k+1}..G_N.
+static str_status loss_bwd_fused(int N, const int64_t* dims, const str_ctx& t, const LossPlan& pl,
+                                 const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
+                                 double grad_scale, void* const* grad_cores_dev, int64_t rows, int64_t cols,
+                                 int kp, int K, size_t es, cudaStream_t s) {
+  const int xt = es == 8 ? XT_F64 : XT_F32;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const int64_t nbl = (int64_t)pl.nrg * pl.ncg;
+  size_t off[7];
+  off[0] = 0;                                                          // loss partials
+  off[1] = off[0] + al((size_t)nbl * 8);                              // Zpart
+  off[2] = off[1] + al((size_t)pl.ncg * rows * K * es);                // Wpart (nrg > 1)
+  off[3] = off[2] + (pl.nrg > 1 ? al((size_t)pl.nrg * cols * K * es) : 0);  // Zt
+  off[4] = off[3] + al((size_t)rows * K * es);                         // W
+  off[5] = off[4] + al((size_t)cols * K * es);                         // U, V
+  off[6] = off[5] + 2 * al((size_t)K * K * es);
+  // the reduced MTTKRPs: arguments and the largest partial buffer, before any launch
+  std::vector<MttkrpArgs> args;
+  size_t part_bytes = 0;
+  for (int n = 0; n < N; ++n) {
+    if (n < kp && kp == 1) { args.emplace_back(); continue; }
+    MttkrpArgs a;
+    a.xtype = xt;
+    a.compute = t.compute;
+    if (n < kp) {
+      a.N = kp + 1;
+      a.n = n;
+      for (int k = 0; k < kp; ++k) { a.dim[k] = dims[k]; a.core[k] = cores_dev[k]; a.R[k] = t.R[k]; }
+      a.dim[kp] = K;
+      a.R[kp] = t.R[kp];
+      a.R[kp + 1] = t.R[0];
+    } else {
+      a.N = N - kp + 1;
+      a.n = n - kp + 1;
+      a.dim[0] = K;
+      a.R[0] = t.R[0];
+      for (int k = kp; k < N; ++k) { a.dim[k - kp + 1] = dims[k]; a.core[k - kp + 1] = cores_dev[k]; a.R[k - kp + 1] = t.R[k]; }
+      a.R[N - kp + 1] = t.R[0];
+    }
+    int64_t J = 1;
+    for (int k = 0; k < a.N; ++k) if (k != a.n) J *= a.dim[k];
+    a.nfib = J;
+    // small reduced problems: at least 64 fibres per split, about two CTAs per SM
+    const int64_t gx = (a.dim[a.n] + 63) / 64;
+    const int64_t per = std::max<int64_t>(64, (J * gx + 303) / 304);
+    a.fib_per_split = per;
+    a.splits = (int)((J + per - 1) / per);
+    part_bytes = std::max(part_bytes, (size_t)a.splits * a.dim[a.n] * a.R[a.n] * a.R[a.n + 1] * es);
+    args.push_back(a);
+  }
+  TRY(ws_grow(3, off[6]));
+  TRY(ws_grow(2, part_bytes + 64));
+  char* b3 = (char*)g_loss_ws[3].p;
+  void* Zpart = b3 + off[1];
+  void* Zt = b3 + off[3];
+  void* W = b3 + off[4];
+  void* Wpart = pl.nrg > 1 ? (void*)(b3 + off[2]) : W;
+  void* U = b3 + off[5];
+  void* V = b3 + off[5] + al((size_t)K * K * es);
+  STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, 0, kp - 1, 0, 0, g_loss_ws[0].p, s));
+  STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, kp, N - 1, 0, 1, g_loss_ws[1].p, s));
+  STR_CUDA_TRY(launch_loss_pass(g_loss_ws[0].p, g_loss_ws[1].p, t.compute, rows, cols, K, X_dev, mask_bits, pl, true,
+                                (double*)(b3 + off[0]), Zpart, Wpart, s));
+  STR_CUDA_TRY(launch_loss_reduce(Zpart, pl.ncg, rows, Wpart, pl.nrg, cols, K, t.compute, Zt, W, s));
+  STR_CUDA_TRY(launch_unit_cores(t.R[0], t.R[kp], t.compute, U, V, s));
+  for (int n = 0; n < N; ++n) {
+    if (n < kp && kp == 1) {
+      STR_CUDA_TRY(launch_prefix1_grad(Zt, dims[0], K, grad_scale, t.compute, grad_cores_dev[0], s));
+      continue;
+    }
+    MttkrpArgs a = args[n];
+    if (n < kp) { a.X = Zt; a.core[kp] = U; }
+    else { a.X = W; a.core[0] = V; }
+    a.partial = g_loss_ws[2].p;
+    STR_CUDA_TRY(launch_mttkrp(a, s));
+    STR_CUDA_TRY(launch_reduce_partials_to(a.partial, t.compute, a.splits, a.dim[a.n] * a.R[a.n] * a.R[a.n + 1],
+                                           -grad_scale, grad_cores_dev[n], xt, s));
+  }
+  return STR_OK;
+}
+
 str_status tr_masked_loss_fwd(int N, const int64_t* dims, const int* ranks, str_dtype dtype,
                               const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
                               double* loss_dev, void* stream) {
@@ -2100,7 +2265,9 @@ str_status tr_masked_loss_fwd(int N, const int64_t* dims, const int* ranks, str_
   if (!loss_dev) return STR_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_ws_mu);
   cudaStream_t s = (cudaStream_t)stream;
-  const int kp = N / 2;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
+  const int ks = loss_split(N, dims, t.R);
+  const int kp = ks > 0 ? ks : N / 2;
   int64_t rows = 1, cols = 1;
   for (int k = 0; k < kp; ++k) rows *= dims[k];
   for (int k = kp; k < N; ++k) cols *= dims[k];
@@ -2108,6 +2275,20 @@ str_status tr_masked_loss_fwd(int N, const int64_t* dims, const int* ranks, str_
   const size_t es = dtype == STR_F64 ? 8 : 4;
   TRY(ws_grow(0, (size_t)rows * K * es));
   TRY(ws_grow(1, (size_t)cols * K * es));
+  LossPlan pl;
+  if (ks > 0 && loss_pass_plan(t.compute, rows, cols, K, false, &pl)) {
+    // one fused pass over X: per-CTA partial sums of r^2, summed in a fixed order
+    const int64_t nbl = (int64_t)pl.nrg * pl.ncg;
+    TRY(ws_grow(2, (size_t)nbl * 8 + 64));
+    STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, 0, kp - 1, 0, 0, g_loss_ws[0].p, s));
+    STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, kp, N - 1, 0, 1, g_loss_ws[1].p, s));
+    double* part = (double*)g_loss_ws[2].p;
+    STR_CUDA_TRY(launch_loss_pass(g_loss_ws[0].p, g_loss_ws[1].p, t.compute, rows, cols, K, X_dev, mask_bits, pl,
+                                  false, part, nullptr, nullptr, s));
+    STR_CUDA_TRY(launch_sum_blocks(part, nbl, 1, part + nbl, 0.5, s));
+    STR_CUDA_TRY(cudaMemcpyAsync(loss_dev, part + nbl, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return STR_OK;
+  }
   TRY(ws_grow(2, (size_t)recon_blocks(rows, cols) * 16 + 64));
   STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, 0, kp - 1, 0, 0, g_loss_ws[0].p, s));
   STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, kp, N - 1, 0, 1, g_loss_ws[1].p, s));
@@ -2128,7 +2309,9 @@ str_status tr_masked_loss_bwd(int N, const int64_t* dims, const int* ranks, str_
   for (int k = 0; k < N; ++k) if (!grad_cores_dev[k]) return STR_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_ws_mu);
   cudaStream_t s = (cudaStream_t)stream;
-  const int kp = N / 2;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
+  const int ks = loss_split(N, dims, t.R);
+  const int kp = ks > 0 ? ks : N / 2;
   int64_t rows = 1, cols = 1, count = 1;
   for (int k = 0; k < kp; ++k) rows *= dims[k];
   for (int k = kp; k < N; ++k) cols *= dims[k];
@@ -2137,6 +2320,10 @@ str_status tr_masked_loss_bwd(int N, const int64_t* dims, const int* ranks, str_
   const size_t es = dtype == STR_F64 ? 8 : 4;
   TRY(ws_grow(0, (size_t)rows * K * es));
   TRY(ws_grow(1, (size_t)cols * K * es));
+  LossPlan pl;
+  if (ks > 0 && loss_pass_plan(t.compute, rows, cols, K, true, &pl)) return loss_bwd_fused(N, dims, t, pl, cores_dev, X_dev,
+                                                                                mask_bits, grad_scale, grad_cores_dev,
+                                                                                rows, cols, kp, K, es, s);
   TRY(ws_grow(3, (size_t)count * es));
   STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, 0, kp - 1, 0, 0, g_loss_ws[0].p, s));
   STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, kp, N - 1, 0, 1, g_loss_ws[1].p, s));

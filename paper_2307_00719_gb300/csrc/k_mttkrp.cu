@@ -416,9 +416,36 @@ __global__ void reduce_to_kernel(const T* partial, int splits, int64_t count, do
   }
 }
 
+// many splits: one warp per output, lane l sums the splits l, l + 32, ... and the
+// 32 lane sums are combined by a fixed butterfly (same order on every run)
+template <typename T, typename O>
+__global__ void reduce_to_warp_kernel(const T* partial, int splits, int64_t count, double scale, O* out) {
+  PDL_ENTRY();
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < count;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double s = 0.0;
+    for (int k = lane; k < splits; k += 32) s += (double)partial[(int64_t)k * count + i];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = (O)(scale * s);
+  }
+}
+
 cudaError_t launch_reduce_partials_to(const void* partial, int compute, int splits, int64_t count,
                                       double scale, void* out, int out_type, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (splits >= 64) {
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count * 32 + 255) / 256, 152 * 16));
+#define STR_RW(T, O) launch_k(reduce_to_warp_kernel<T, O>, g, 256, 0, s, (const T*)partial, splits, count, scale, (O*)out)
+    if (compute == 2) {
+      if (out_type == XT_F64) STR_RW(double, double); else STR_RW(double, float);
+    } else {
+      if (out_type == XT_F64) STR_RW(float, double); else STR_RW(float, float);
+    }
+#undef STR_RW
+    return cudaGetLastError();
+  }
   if (compute == 2) {
     if (out_type == XT_F64) launch_k(reduce_to_kernel<double, double>, grid_for(count), 256, 0, s, (const double*)partial, splits, count, scale, (double*)out);
     else launch_k(reduce_to_kernel<double, float>, grid_for(count), 256, 0, s, (const double*)partial, splits, count, scale, (float*)out);

@@ -145,6 +145,26 @@ cudaError_t launch_recon(const void* Lm, const void* Rm, int compute, int64_t ro
 cudaError_t launch_sum_blocks(const double* block_sums, int64_t nblocks, int width, double* out,
                               double scale, cudaStream_t s);
 int recon_blocks(int64_t rows, int64_t cols);
+// fused masked-loss pass (one read of X): loss partials [nrg][ncg]; with bwd also
+// Zpart [ncg][rows][K] (sum over columns of r Rm) and Wpart [nrg][cols][K] (sum
+// over rows of r Lm); K <= 64
+struct LossPlan {
+  int RG = 64, nrg = 1, ncg = 1;
+  int64_t cb_per = 1;
+  size_t smem = 0;
+};
+bool loss_pass_plan(int compute, int64_t rows, int64_t cols, int K, bool bwd, LossPlan* pl);
+cudaError_t launch_loss_pass(const void* Lm, const void* Rm, int compute, int64_t rows, int64_t cols, int K,
+                             const void* X, const uint32_t* mask, const LossPlan& pl, bool bwd,
+                             double* loss_part, void* Zpart, void* Wpart, cudaStream_t s);
+// Zt[c][row] = sum of the column-group partials; W = sum of the row-group partials
+// (skipped when nrg == 1: the pass wrote W itself)
+cudaError_t launch_loss_reduce(const void* Zpart, int ncg, int64_t rows, const void* Wpart, int nrg, int64_t cols,
+                               int K, int compute, void* Zt, void* W, cudaStream_t s);
+// unit cores U, V (K x K each, core layout) of the reduced trace problems
+cudaError_t launch_unit_cores(int R1, int Rk, int compute, void* U, void* V, cudaStream_t s);
+cudaError_t launch_prefix1_grad(const void* Zt, int64_t I, int K, double scale, int compute, void* grad,
+                                cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // tensor-core dense MTTKRP (k_tc.cu): stage 1 Y = X x_k G_k on tcgen05,

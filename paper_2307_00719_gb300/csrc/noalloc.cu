@@ -104,6 +104,7 @@ extern "C" str_status tr_masked_loss_fwd_noalloc(int N, const int64_t* dims, con
   double* blocks = (double*)(b + off_blocks);
   double* sums = (double*)(b + off_sums);
   cudaStream_t s = (cudaStream_t)stream;
+  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
   STR_CUDA_TRY(launch_chain_table(cores_dev, compute, R, N, dims, 0, kp - 1, 0, 0, prefix, s));
   STR_CUDA_TRY(launch_chain_table(cores_dev, compute, R, N, dims, kp, N - 1, 0, 1, suffix, s));
   int64_t nbo = 0;

@@ -61,3 +61,33 @@ def test_autograd_function():
     gref = masked_loss_grad(X, G, mask)
     for n in range(4):
         assert rel(_abi_to_paper(cores[n].grad, 0, 0), 2.0 * gref[n]) <= 1e-12
+
+
+# Shapes for the fused loss pass: ragged 64-row / 64-column tiles, a prefix of one
+# core (order 3 and order 4), a two-core prefix of 1600 rows over 9 columns (many
+# row groups, one column block), and a mid-size order-5 tensor.
+@pytest.mark.parametrize("dims,ranks", [
+    ((70, 9, 13), (2, 3, 4)),
+    ((31, 33, 5, 7), (3, 2, 4, 3)),
+    ((40, 40, 3, 3), (2, 8, 2, 2)),
+    ((16, 16, 16, 16, 12), (4, 4, 4, 4, 4)),
+])
+@pytest.mark.parametrize("dtype_name,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_masked_loss_tiles_and_groups(dims, ranks, dtype_name, tol):
+    import torch
+    p = lib()
+    dt = torch.float64 if dtype_name == "f64" else torch.float32
+    G = synth.gaussian_cores(dims, ranks, 11)
+    X = synth.gaussian_tensor(dims, 12)
+    mask = synth.bernoulli_keep_mask(dims, 0.3, 13)
+    bits = torch.from_numpy(synth.pack_mask_bits(mask).view(np.int32)).cuda()
+    cores = _abi_cores(G, dt)
+    Xd = dev(X, dt)
+    for mb, mk in ((bits, mask), (None, None)):
+        loss = p.tr_masked_loss_fwd(cores, Xd, mb).item()
+        ref = masked_loss(X, G, mk)
+        assert abs(loss - ref) <= tol * ref
+        grads = p.tr_masked_loss_bwd(cores, Xd, mb, 0.5)
+        gref = masked_loss_grad(X, G, mk)
+        for n in range(len(dims)):
+            assert rel(_abi_to_paper(grads[n], 0, 0), 0.5 * gref[n]) <= tol * 10, n
