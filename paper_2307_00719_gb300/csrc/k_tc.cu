@@ -411,22 +411,23 @@ size_t stage1_persist_smem_bytes(int Npad, int nch, bool bf16) {
 }
 
 // ---------------------------------------------------------------------------
-// stage 1, warp-specialised persistent form (192 threads):
+// stage 1, warp-specialised persistent form (320 threads):
 //   warp 0       TMA producer: X tiles into a ring of SA slots
 //   warp 1       MMA issuer (one thread): 3-term TF32 products into one of two
 //                TMEM accumulator sets, then commits that free the X slot and
 //                the X_lo slot and publish the accumulator
-//   warps 2-5    workers: X_lo = rn(X - trunc(X)) (BF16: the widened X) into
-//                one of two slots, then the epilogue of the previous tile
-//                (TMEM lanes 32 (warp % 4) .. + 31) while the MMA of the next
-//                tile runs
+//   warps 2-9    workers, two warpgroups: X_lo = rn(X - trunc(X)) (BF16: the
+//                widened X) into one of two slots, shared by both groups, then
+//                the epilogue of the previous tile (TMEM lanes 32 (warp % 4) ..
+//                + 31; the groups take alternate 16-column chunks) while the
+//                MMA of the next tile runs
 // mbarriers: fullA/emptyA per X slot, fullLo/emptyLo per X_lo slot,
 // accFull/accEmpty per accumulator set, bReady for the resident B operand.
 // Every wait is bounded (2 s); a role whose wait times out stops and records
 // DEV_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------
 template <bool SRC_BF16, int SA>
-__global__ void __launch_bounds__(192, 1) stage1_ws_kernel(
+__global__ void __launch_bounds__(320, 1) stage1_ws_kernel(
     const __grid_constant__ CUtensorMap tmA, const float* __restrict__ Bhi, const float* __restrict__ Blo,
     int M, int Kpad, int N, int Npad, uint32_t tmem_cols, float* __restrict__ Y, int* status) {
   PDL_ENTRY();
@@ -449,6 +450,7 @@ __global__ void __launch_bounds__(192, 1) stage1_ws_kernel(
   uint64_t* bReady = accEmpty + 2;
   uint32_t* tslot = (uint32_t*)(bReady + 1);
   int* s_fail = (int*)(tslot + 1);
+  float* sEpi = (float*)((unsigned char*)bars + 256);   // 8 warps x 32 rows x 17: epilogue staging
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = (M + 127) / 128;
   const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -457,12 +459,12 @@ __global__ void __launch_bounds__(192, 1) stage1_ws_kernel(
   if (tid == 0) {
     for (int i = 0; i < SA; ++i) { mbar_init(&fullA[i], 1); mbar_init(&emptyA[i], 1); }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&fullLo[i], 4);
+      mbar_init(&fullLo[i], 8);
       mbar_init(&emptyLo[i], 1);
       mbar_init(&accFull[i], 1);
-      mbar_init(&accEmpty[i], 4);
+      mbar_init(&accEmpty[i], 8);
     }
-    mbar_init(bReady, 128);
+    mbar_init(bReady, 256);
     *s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -524,10 +526,11 @@ __global__ void __launch_bounds__(192, 1) stage1_ws_kernel(
     }
   } else {
     // ---- workers: B staging, X_lo, epilogue ----
-    const int wt = tid - 64;                 // 0..127
+    const int wt = tid - 64;                 // 0..255
     const int q = warp & 3;                  // TMEM lane quadrant of this warp
+    const int wg = (warp - 2) >> 2;          // worker group: epilogue chunks wg, wg + 2, ..
     for (int c = 0; c < nch; ++c)
-      for (int r = wt >> 3; r < Npad; r += 16) {
+      for (int r = wt >> 3; r < Npad; r += 32) {
         const int jx = wt & 7;
         cp_async16(sBhi + c * bchunk + sw128_off(r, jx), Bhi + (size_t)r * Kpad + c * 32 + jx * 4);
         cp_async16(sBlo + c * bchunk + sw128_off(r, jx), Blo + (size_t)r * Kpad + c * 32 + jx * 4);
@@ -544,20 +547,20 @@ __global__ void __launch_bounds__(192, 1) stage1_ws_kernel(
         const unsigned char* araw = sA + (size_t)a * nch * kRaw;
         unsigned char* lo = sLo + (size_t)l * nch * 16384;
         if (!SRC_BF16) {
-          for (int e = wt; e < nch * 1024; e += 128 * 4) {
+          for (int e = wt; e < nch * 1024; e += 256 * 4) {
             float4 v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-              if (e + 128 * u < nch * 1024) v[u] = *(const float4*)(araw + (size_t)(e + 128 * u) * 16);
+              if (e + 256 * u < nch * 1024) v[u] = *(const float4*)(araw + (size_t)(e + 256 * u) * 16);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              if (e + 128 * u >= nch * 1024) continue;
+              if (e + 256 * u >= nch * 1024) continue;
               const float4 x = v[u];
               const float4 h = make_float4(__uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u),
                                            __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u),
                                            __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u),
                                            __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u));
-              *(float4*)(lo + (size_t)(e + 128 * u) * 16) =
+              *(float4*)(lo + (size_t)(e + 256 * u) * 16) =
                   make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
             }
           }
@@ -565,8 +568,8 @@ __global__ void __launch_bounds__(192, 1) stage1_ws_kernel(
           for (int c = 0; c < nch; ++c) {
             const unsigned char* raw = araw + (size_t)c * kRaw;
             unsigned char* ah = lo + (size_t)c * 16384;
-            for (int p = 0; p < 8; ++p) {
-              const int r = p * 16 + (wt >> 3);
+            for (int p = 0; p < 4; ++p) {
+              const int r = p * 32 + (wt >> 3);
               const int jx = wt & 7;
               const __nv_bfloat162* qv = (const __nv_bfloat162*)(raw + r * 64 + jx * 8);
               const float2 x0 = __bfloat1622float2(qv[0]), x1 = __bfloat1622float2(qv[1]);
@@ -583,28 +586,46 @@ __global__ void __launch_bounds__(192, 1) stage1_ws_kernel(
         if (!mbar_wait(&accFull[r], ur & 1, kWaitNs)) { failed = true; break; }
         tc_fence_after();
         const int t = blockIdx.x + jp * gridDim.x;
-        const int row = t * 128 + 32 * q + lane;
+        const int row0 = t * 128 + 32 * q;        // first row of this warp's 32
         const uint32_t abase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(r * 3 * Npad);
-        for (int col = 0; col < Npad; col += 16) {
+        float* se = sEpi + (warp - 2) * (32 * 17);
+        for (int col = 16 * wg; col < Npad; col += 32) {
           uint32_t v0[16], v1[16], vx[16];
           tmem_ld_x16_nw(abase + (uint32_t)col, v0);
           tmem_ld_x16_nw(abase + (uint32_t)(Npad + col), v1);
           tmem_ld_x16_nw(abase + (uint32_t)(2 * Npad + col), vx);
           tmem_wait_ld();
-          if (row < M) {
-            float y[16];
+          float y[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u)
-              y[u] = (__uint_as_float(v0[u]) + __uint_as_float(vx[u])) + __uint_as_float(v1[u]);
-            float* yrow = Y + (size_t)row * N + col;
-            if (vec && col + 16 <= N) {
+          for (int u = 0; u < 16; ++u)
+            y[u] = (__uint_as_float(v0[u]) + __uint_as_float(vx[u])) + __uint_as_float(v1[u]);
+          if (vec) {
+            // rows of 16-byte multiples: the lane's row, four floats per store
+            const int row = row0 + lane;
+            if (row < M) {
+              float* yrow = Y + (size_t)row * N + col;
+              if (col + 16 <= N) {
 #pragma unroll
-              for (int u = 0; u < 16; u += 4) *(float4*)(yrow + u) = make_float4(y[u], y[u + 1], y[u + 2], y[u + 3]);
-            } else {
+                for (int u = 0; u < 16; u += 4) *(float4*)(yrow + u) = make_float4(y[u], y[u + 1], y[u + 2], y[u + 3]);
+              } else {
 #pragma unroll
-              for (int u = 0; u < 16; ++u)
-                if (col + u < N) yrow[u] = y[u];
+                for (int u = 0; u < 16; ++u)
+                  if (col + u < N) yrow[u] = y[u];
+              }
             }
+          } else {
+            // other widths: through shared memory, so that each store writes two
+            // rows' 16 consecutive columns
+#pragma unroll
+            for (int u = 0; u < 16; ++u) se[lane * 17 + u] = y[u];
+            __syncwarp();
+            const int cc = lane & 15;
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+              const int rr = 2 * i + (lane >> 4);
+              if (row0 + rr < M && col + cc < N) Y[(size_t)(row0 + rr) * N + col + cc] = se[rr * 17 + cc];
+            }
+            __syncwarp();
           }
         }
         tc_fence_before();
@@ -623,7 +644,7 @@ __global__ void __launch_bounds__(192, 1) stage1_ws_kernel(
 size_t stage1_ws_smem_bytes(int Npad, int nch, bool bf16, int sa) {
   const size_t b = (size_t)2 * nch * Npad * 128;
   const size_t raw = (size_t)sa * nch * (bf16 ? 8192 : 16384);
-  return 1024 + b + raw + (size_t)2 * nch * 16384 + 256;
+  return 1024 + b + raw + (size_t)2 * nch * 16384 + 256 + 8 * 32 * 17 * 4;
 }
 
 // ---------------------------------------------------------------------------
@@ -1105,7 +1126,7 @@ cudaError_t launch_stage1_tc(const void* Xa, int xtype, int64_t M, int K, const 
                      : (three ? stage1_ws_kernel<false, 3> : stage1_ws_kernel<false, 2>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
     if (e != cudaSuccess) return e;
-    launch_k(kern, gridp, 192, smw, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols_ws, Y, status);
+    launch_k(kern, gridp, 320, smw, s, tm, Bhi, Blo, (int)M, Kpad, N, Npad, cols_ws, Y, status);
     return cudaGetLastError();
   }
   if (persist) {
