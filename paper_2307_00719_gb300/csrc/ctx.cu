@@ -764,7 +764,7 @@ str_status mttkrp_tc(str_ctx* c, const SlabView& v, int n, const void* const* co
     TRY(chain_table_c(c, cores, dims, b0, b1, &a.TB, s));
   }
   int64_t per = 1;
-  a.splits = stage2_plan_splits(a.dn, a.Jlo * a.Jhi, &per);
+  a.splits = stage2_plan_splits(a, &per);
   a.per = per;
   const int OUTP = a.Rn * a.Rn1;
   TRY(grow(c, c->tc_part, (size_t)a.splits * a.dn * OUTP * 4));

@@ -930,6 +930,133 @@ __global__ void __launch_bounds__(S2_THREADS, 3) stage2_kernel(Stage2Args a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// stage 2 for small equal ranks R (R^2 <= 49), warp-synchronous: each warp takes
+// batches of 32 consecutive combinations, copies their Y rows (and B rows when
+// B follows i_lo) into its own shared-memory slice with coalesced loads, then
+// lane j forms combination j's whole R x R product in registers
+//   O = [A(i_hi)] . Y_q . [B]        (each factor present as in stage2_kernel)
+// and accumulates it.  No block-wide barrier until the final fixed-order sum.
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(128) stage2_warp_kernel(Stage2Args a) {
+  PDL_ENTRY();
+  constexpr int PO = R * R;
+  constexpr int PS = PO | 1;                  // odd per-combination stride: lane reads are conflict-free
+  constexpr int NW = 4;
+  extern __shared__ __align__(16) float s2w[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* sY = s2w + warp * (2 * 32 * PS);
+  float* sB = sY + 32 * PS;
+  __shared__ float red[NW][PO];
+  const bool hasA = a.TA != nullptr, hasB = a.TB != nullptr;
+  const bool b_lo = hasB && a.k == 0;         // B follows i_lo (else i_hi)
+  const int64_t in = blockIdx.x;
+  const int64_t ncomb = a.Jlo * a.Jhi;
+  const int64_t q0 = (int64_t)blockIdx.y * a.per, q1 = min(ncomb, q0 + a.per);
+  float acc[PO];
+#pragma unroll
+  for (int u = 0; u < PO; ++u) acc[u] = 0.f;
+  for (int64_t qb = q0 + 32 * warp; qb < q1; qb += 32 * NW) {
+    const int nq = (int)min((int64_t)32, q1 - qb);
+    const int64_t hi0 = qb / a.Jlo, lo0 = qb - hi0 * a.Jlo;
+    const bool one_seg = lo0 + nq <= a.Jlo;   // warp-uniform: rows of the batch are consecutive
+    const int64_t q = qb + lane;
+    const int64_t ihi = q / a.Jlo, ilo = q - ihi * a.Jlo;
+    __syncwarp();
+    if (one_seg) {
+      const float* ys = a.Y + (lo0 + a.Jlo * (in + a.dn * hi0)) * PO;
+      for (int f = lane; f < nq * PO; f += 32) {
+        const int j = f / PO, u = f - j * PO;
+        sY[j * PS + u] = __ldg(ys + f);
+      }
+      if (b_lo) {
+        const float* bs = a.TB + lo0 * PO;
+        for (int f = lane; f < nq * PO; f += 32) {
+          const int j = f / PO, u = f - j * PO;
+          sB[j * PS + u] = __ldg(bs + f);
+        }
+      }
+    } else if (lane < nq) {
+      const float* ys = a.Y + (ilo + a.Jlo * (in + a.dn * ihi)) * PO;
+#pragma unroll
+      for (int u = 0; u < PO; ++u) sY[lane * PS + u] = __ldg(ys + u);
+      if (b_lo) {
+#pragma unroll
+        for (int u = 0; u < PO; ++u) sB[lane * PS + u] = __ldg(a.TB + ilo * PO + u);
+      }
+    }
+    __syncwarp();
+    if (lane < nq) {
+      float y[PO];
+#pragma unroll
+      for (int u = 0; u < PO; ++u) y[u] = sY[lane * PS + u];
+      float s[PO];                            // S = Y_q . B   (entry (c, w) at c + R w)
+      if (hasB) {
+        const float* bq = b_lo ? sB + lane * PS : a.TB + ihi * PO;
+#pragma unroll
+        for (int w = 0; w < R; ++w) {
+          float bc[R];
+#pragma unroll
+          for (int e = 0; e < R; ++e) bc[e] = b_lo ? bq[e + R * w] : __ldg(bq + e + R * w);
+#pragma unroll
+          for (int c = 0; c < R; ++c) {
+            float v = 0.f;
+#pragma unroll
+            for (int e = 0; e < R; ++e) v = fmaf(y[c + R * e], bc[e], v);
+            s[c + R * w] = v;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < PO; ++u) s[u] = y[u];
+      }
+      if (hasA) {
+        // O = A(i_hi) S, entry (x, w) accumulated at w + R x
+        const float* aq = a.TA + ihi * PO;
+        float am[PO];
+#pragma unroll
+        for (int u = 0; u < PO; ++u) am[u] = __ldg(aq + u);
+#pragma unroll
+        for (int x = 0; x < R; ++x)
+#pragma unroll
+          for (int w = 0; w < R; ++w) {
+            float v = 0.f;
+#pragma unroll
+            for (int c = 0; c < R; ++c) v = fmaf(am[x + R * c], s[c + R * w], v);
+            acc[w + R * x] += v;
+          }
+      } else {
+#pragma unroll
+        for (int x = 0; x < R; ++x)
+#pragma unroll
+          for (int w = 0; w < R; ++w) acc[w + R * x] += s[x + R * w];
+      }
+    }
+  }
+  // fixed-order sums: butterfly within the warp, then warps in order
+#pragma unroll
+  for (int u = 0; u < PO; ++u) {
+    float v = acc[u];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][u] = v;
+  }
+  __syncthreads();
+  float* dst = a.partial + ((int64_t)blockIdx.y * a.dn + in) * PO;
+  for (int e = threadIdx.x; e < PO; e += blockDim.x) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) v += red[w][e];
+    dst[e] = v;
+  }
+}
+
+static int stage2_warp_rank(const Stage2Args& a) {
+  const bool eq = a.Rk == a.Rk1 && a.Rk == a.Rn && a.Rk == a.Rn1;
+  return eq && a.Rk >= 2 && a.Rk <= 7 && a.Rk != 4 ? a.Rk : 0;
+}
+
 size_t stage2_smem_bytes(const Stage2Args& a) {
   const int RRk = a.Rk * a.Rk1;
   int tsz = 0, PO = 0;
@@ -1224,15 +1351,36 @@ cudaError_t launch_gather_fibres(const MttkrpArgs& a, int Kpad, void* A, cudaStr
   return cudaGetLastError();
 }
 
-int stage2_plan_splits(int64_t dn, int64_t ncomb, int64_t* per) {
-  int64_t splits = std::max<int64_t>(1, (2 * 152 + dn - 1) / dn);
-  splits = std::min<int64_t>(splits, std::max<int64_t>(1, ncomb / 128));
+int stage2_plan_splits(const Stage2Args& a, int64_t* per) {
+  const int64_t dn = a.dn, ncomb = a.Jlo * a.Jhi;
+  int64_t splits;
+  if (stage2_warp_rank(a)) {
+    // warp kernel: about eight CTAs of four warps per SM, at least one batch per warp
+    splits = std::max<int64_t>(1, (8 * 152 + dn - 1) / dn);
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, ncomb / 128));
+  } else {
+    splits = std::max<int64_t>(1, (2 * 152 + dn - 1) / dn);
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, ncomb / 128));
+  }
   int64_t p = (ncomb + splits - 1) / splits;
   *per = std::max<int64_t>(1, p);
   return (int)((ncomb + *per - 1) / *per);
 }
 
 cudaError_t launch_stage2(const Stage2Args& a, cudaStream_t s) {
+  if (const int rw = stage2_warp_rank(a)) {
+    if (a.Jlo * a.Jhi >= ((int64_t)1 << 40)) return cudaErrorInvalidValue;
+    const size_t sm = (size_t)4 * 2 * 32 * ((rw * rw) | 1) * sizeof(float);
+    auto kern = rw == 2 ? stage2_warp_kernel<2> : rw == 3 ? stage2_warp_kernel<3> : rw == 5 ? stage2_warp_kernel<5>
+              : rw == 6 ? stage2_warp_kernel<6> : stage2_warp_kernel<7>;
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)a.dn, (unsigned)a.splits);
+    launch_k(kern, grid, 128, sm, s, a);
+    return cudaGetLastError();
+  }
   const int OUTP = a.Rn * a.Rn1;
   if (OUTP > S2_THREADS || a.Rk * a.Rn > S2_THREADS || a.Rn1 * a.Rn > S2_THREADS ||
       a.Jlo * a.Jhi >= ((int64_t)1 << 31))

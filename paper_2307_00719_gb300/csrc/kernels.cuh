@@ -199,5 +199,5 @@ cudaError_t launch_gemm_tc_splitk(const void* A, int xtype, int64_t M, int Kpad,
                                   const float* Blo, int N, int Npad, int splits, float* Y, int* status,
                                   cudaStream_t s);
 int gemm_tc_splitk_count(int Kpad, int splits);
-int stage2_plan_splits(int64_t dn, int64_t ncomb, int64_t* per);
+int stage2_plan_splits(const Stage2Args& a, int64_t* per);
 cudaError_t launch_stage2(const Stage2Args& a, cudaStream_t s);

@@ -83,11 +83,19 @@ def test_tensor_core_path_every_mode(slab):
     _run((64, 40), 23, (5, 4, 6), 7, 8, compute="f32", slab=slab, seed=10, tol=1e-5)
 
 
-@pytest.mark.parametrize("R", [4, 8])
+@pytest.mark.parametrize("R", [2, 3, 4, 5, 6, 7, 8])
 def test_tensor_core_path_equal_ranks(R):
-    """Equal TR-ranks 4 and 8 take the stage-2 kernel specialised on the rank;
-    the temporal mode's combinations span several chunks and splits."""
+    """Equal TR-ranks take the stage-2 kernels specialised on the rank (2 x 2
+    register blocks for 4 and 8, the warp-per-batch kernel for the others); the
+    temporal mode's combinations span several chunks, batches and splits."""
     _run((16, 24, 8), 21, (R, R, R, R), 9, 6, compute="f32", slab="f32", sweeps=2, seed=11, tol=1e-5)
+
+
+def test_tensor_core_path_order5_segments():
+    """Order 5, equal ranks 5: stage 2 with both chain tables (A . Y . B per
+    combination) where the runs of equal i_hi are 10 and 90 combinations long,
+    so 32-combination batches straddle run boundaries."""
+    _run((12, 10, 9, 7), 14, (5, 5, 5, 5, 5), 6, 4, compute="f32", slab="f32", sweeps=2, seed=12, tol=1e-5)
 
 
 def test_host_slab_matches_device_slab():
