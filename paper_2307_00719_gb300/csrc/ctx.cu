@@ -135,7 +135,7 @@ struct str_ctx {
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   bool side2_used = false;
   DevBuf mbuf[2];
-  DevBuf qf, qlo, fcount, ring2, ring3, levx;
+  DevBuf qf, qlo, fcount, ring2, ring3, levx, chain_scratch;
   bool fcount_dirty = false;     // fcount allocated but not yet cleared on a stream
   const double* qsplit_of = nullptr;   // the Q whose FP32 pair (qf, qlo) is current   // FP32 copy of Q and the last-CTA counter of the fused ring GEMM + factor
 
@@ -672,7 +672,18 @@ str_status chain_table_c(str_ctx* c, const void* const* cores, const int64_t* di
   int64_t J = 1;
   for (int j = k0; j <= k1; ++j) J *= dims[j];
   TRY(grow(c, slot->buf, (size_t)J * c->R[k0] * c->R[k1 + 1] * 4));
-  LCHK(c, STR_K_GRAM, launch_chain_table(cores, 1, c->R, c->N, dims, k0, k1, 0, 0, slot->buf.p, s));
+  if (k1 == k0 + 2 && dims[k0] * dims[k0 + 1] < (1 << 30)) {
+    // three cores as two two-core products: (G_k0 G_k0+1) into a scratch table,
+    // then that table (a core of I_k0 I_k0+1 slices) times G_k1
+    TRY(grow(c, c->chain_scratch, (size_t)dims[k0] * dims[k0 + 1] * c->R[k0] * c->R[k0 + 2] * 4));
+    LCHK(c, STR_K_GRAM, launch_chain_table(cores, 1, c->R, c->N, dims, k0, k0 + 1, 0, 0, c->chain_scratch.p, s));
+    const void* c2[2] = {c->chain_scratch.p, cores[k1]};
+    const int64_t d2[2] = {dims[k0] * dims[k0 + 1], dims[k1]};
+    const int r2[3] = {c->R[k0], c->R[k0 + 2], c->R[k1 + 1]};
+    LCHK(c, STR_K_GRAM, launch_chain_table(c2, 1, r2, 2, d2, 0, 1, 0, 0, slot->buf.p, s));
+  } else {
+    LCHK(c, STR_K_GRAM, launch_chain_table(cores, 1, c->R, c->N, dims, k0, k1, 0, 0, slot->buf.p, s));
+  }
   slot->k0 = k0;
   slot->k1 = k1;
   slot->valid = true;
@@ -695,7 +706,7 @@ str_status ensure_transposed(str_ctx* c, const SlabView& v, cudaStream_t s, bool
   int64_t E = 1;
   for (int j = 0; j < c->N; ++j) E *= v.dim[j];
   const size_t es = v.xtype == XT_BF16 ? 2 : 4;
-  if (((size_t)v.dim[1] * es) % 16 != 0 || E / (v.dim[0] * v.dim[1]) > 65535) return STR_OK;
+  if (((size_t)v.dim[1] * es) % 16 != 0) return STR_OK;
   if (c->tc_xt_src != v.X) {
     TRY(grow(c, c->tc_xt, (size_t)E * es));
     LCHK(c, STR_K_OTHER, launch_transpose01(v.X, c->tc_xt.p, v.xtype, (int)v.dim[0], (int)v.dim[1],

@@ -100,7 +100,8 @@ cudaError_t launch_chain_table(const void* const* cores, int compute, const int*
   for (int k = k0; k <= k1; ++k) J *= dims[k];
   const int64_t total = J * R[k0];
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, 152 * 16));
-  if (k1 == k0 + 1 && !transpose && R[k0] * R[k0 + 1] <= STR_MAXRR && R[k0 + 1] * R[k1 + 1] <= STR_MAXRR) {
+  if (k1 == k0 + 1 && !transpose && R[k0] * R[k0 + 1] <= STR_MAXRR && R[k0 + 1] * R[k1 + 1] <= STR_MAXRR &&
+      dims[k1] <= 65535) {
     dim3 grid((unsigned)((dims[k0] + 15) / 16), (unsigned)dims[k1]);
     if (compute == 2)
       launch_k(chain2_kernel<double>, grid, 256, 0, s, (const double*)cores[k0], (const double*)cores[k1],

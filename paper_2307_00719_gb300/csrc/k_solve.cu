@@ -619,10 +619,10 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Refined solve for n <= 128 (even), one row of P per CTA at a time, 256
+// Refined solve for n <= 128, one row of P per CTA at a time, 256
 // threads: thread (c, part) owns column c (and c + 64) and the quarter part of
 // every inner sum.  W32 and Q = Qh + Ql (an FP32 pair carrying Q to about 2^-48) are
-// staged by bulk copies; the right-hand side is formed from the split
+// staged by bulk copies (plain loads for odd n); the right-hand side is formed from the split
 // partials as in solve_refine_kernel.
 //   g  = p W32                           (FP32)
 //   r  = p - g Q                         (double-FP32 arithmetic: exact products
@@ -654,11 +654,11 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
   // CPT columns per thread: c = (tid & 63) + 64 u, u < CPT (n <= 64 CPT)
   PDL_ENTRY();
   extern __shared__ __align__(16) unsigned char sma[];
-  const int n = a.n, nn = n * n;
+  const int n = a.n, nn = n * n, nns = (nn + 3) & ~3;
   float* Wm = (float*)sma;                  // n x n
-  float* Qh = Wm + nn;                      // n x n
-  float* Ql = Qh + nn;                      // n x n
-  double* pd = (double*)(Ql + nn);          // n: right-hand side (FP64)
+  float* Qh = Wm + nns;                     // n x n
+  float* Ql = Qh + nns;                     // n x n
+  double* pd = (double*)(Ql + nns);         // n: right-hand side (FP64)
   double* pd4 = pd + n;                     // 4 x n: per-part sums of the split partials
   float* vf = (float*)(pd4 + 4 * n);        // n: FP32 vector of the current product
   float* red = vf + n;                      // 4 x n partial sums (x2 for pairs)
@@ -669,13 +669,23 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (tid == 0) {
+  // even n: bulk copies (sizes in 16-byte units); odd n: plain loads
+  const bool bulk = (n & 1) == 0;
+  if (bulk && tid == 0) {
     mbar_expect_tx(&bar, 3u * nn * 4u);
     bulk_g2s(Wm, a.W, nn * 4, &bar);
     bulk_g2s(Qh, a.Qh, nn * 4, &bar);
     bulk_g2s(Ql, a.Ql, nn * 4, &bar);
   }
-  bool staged = false;
+  bool staged = !bulk;
+  if (!bulk) {
+    for (int e = tid; e < nn; e += 256) {
+      Wm[e] = a.W[e];
+      Qh[e] = a.Qh[e];
+      Ql[e] = a.Ql[e];
+    }
+    __syncthreads();
+  }
   const int k0 = part * ((n + 3) / 4), k1 = min(n, k0 + (n + 3) / 4);
   // sum_{k in this part} v[k] W[k][c]
   auto part_dot = [&](int c) {
@@ -822,7 +832,9 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
   }
 }
 
-size_t apply_df_smem(int n) { return (size_t)3 * n * n * 4 + (size_t)5 * n * 8 + (size_t)n * 4 + (size_t)8 * n * 4; }
+size_t apply_df_smem(int n) {
+  return (size_t)3 * ((n * n + 3) & ~3) * 4 + (size_t)5 * n * 8 + (size_t)n * 4 + (size_t)8 * n * 4;
+}
 
 // Q (FP64) -> FP32 pair (hi, lo)
 __global__ void split_pair_kernel(const double* __restrict__ Q, int64_t count, float* __restrict__ hi,
@@ -843,7 +855,7 @@ cudaError_t launch_split_pair(const double* Q, int64_t count, float* hi, float* 
   return cudaGetLastError();
 }
 
-bool apply_df_supported(int n) { return n >= 2 && n <= 128 && (n % 2) == 0; }
+bool apply_df_supported(int n) { return n >= 2 && n <= 128; }
 
 cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, int n, const double* P, int64_t rows,
                             double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s) {

@@ -673,19 +673,27 @@ __global__ void prep_b_kernel(const double* __restrict__ G, int K, int N, int Kp
 template <typename T>
 __global__ void transpose01_kernel(const T* __restrict__ in, T* __restrict__ out, int d0, int d1, int64_t rest) {
   PDL_ENTRY();
-  __shared__ T tile[32][33];
-  const int64_t r = blockIdx.z;
+  __shared__ T tile[2][32][33];
   const int i0b = blockIdx.x * 32, i1b = blockIdx.y * 32;
-  const T* src = in + r * (int64_t)d0 * d1;
-  T* dst = out + r * (int64_t)d0 * d1;
-  for (int y = threadIdx.y; y < 32; y += 8) {
-    const int i1 = i1b + y, i0 = i0b + threadIdx.x;
-    if (i0 < d0 && i1 < d1) tile[y][threadIdx.x] = src[(int64_t)i1 * d0 + i0];
-  }
-  __syncthreads();
-  for (int y = threadIdx.y; y < 32; y += 8) {
-    const int i0 = i0b + y, i1 = i1b + threadIdx.x;
-    if (i0 < d0 && i1 < d1) dst[(int64_t)i0 * d1 + i1] = tile[threadIdx.x][y];
+  // several slices r per CTA (double-buffered tile: one barrier per slice)
+  int b = 0;
+  for (int64_t r = blockIdx.z; r < rest; r += gridDim.z, b ^= 1) {
+    const T* src = in + r * (int64_t)d0 * d1;
+    T* dst = out + r * (int64_t)d0 * d1;
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i1 = i1b + threadIdx.y + 8 * u, i0 = i0b + threadIdx.x;
+      v[u] = (i0 < d0 && i1 < d1) ? src[(int64_t)i1 * d0 + i0] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) tile[b][threadIdx.y + 8 * u][threadIdx.x] = v[u];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i0 = i0b + threadIdx.y + 8 * u, i1 = i1b + threadIdx.x;
+      if (i0 < d0 && i1 < d1) dst[(int64_t)i0 * d1 + i1] = tile[b][threadIdx.x][threadIdx.y + 8 * u];
+    }
   }
 }
 
@@ -964,7 +972,29 @@ __global__ void __launch_bounds__(128) stage2_warp_kernel(Stage2Args a) {
     const int64_t q = qb + lane;
     const int64_t ihi = q / a.Jlo, ilo = q - ihi * a.Jlo;
     __syncwarp();
-    if (one_seg) {
+    if (one_seg && nq == 32) {
+      // all loads of the batch issued before the first store
+      const float* ys = a.Y + (lo0 + a.Jlo * (in + a.dn * hi0)) * PO;
+      float v[PO];
+#pragma unroll
+      for (int i = 0; i < PO; ++i) v[i] = __ldg(ys + lane + 32 * i);
+      if (b_lo) {
+        const float* bs = a.TB + lo0 * PO;
+        float w[PO];
+#pragma unroll
+        for (int i = 0; i < PO; ++i) w[i] = __ldg(bs + lane + 32 * i);
+#pragma unroll
+        for (int i = 0; i < PO; ++i) {
+          const int f = lane + 32 * i, j = f / PO;
+          sB[j * PS + f - j * PO] = w[i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < PO; ++i) {
+        const int f = lane + 32 * i, j = f / PO;
+        sY[j * PS + f - j * PO] = v[i];
+      }
+    } else if (one_seg) {
       const float* ys = a.Y + (lo0 + a.Jlo * (in + a.dn * hi0)) * PO;
       for (int f = lane; f < nq * PO; f += 32) {
         const int j = f / PO, u = f - j * PO;
@@ -1201,9 +1231,11 @@ cudaError_t launch_prep_b(const double* G, int K, int N, int Kpad, int Npad, flo
 
 cudaError_t launch_transpose01(const void* in, void* out, int xtype, int d0, int d1, int64_t rest,
                                cudaStream_t s) {
-  dim3 grid((unsigned)ceil_div_i(d0, 32), (unsigned)ceil_div_i(d1, 32), (unsigned)rest);
+  // about 16 CTAs per SM in all, each looping over its share of the slices
+  const int64_t tiles = (int64_t)ceil_div_i(d0, 32) * ceil_div_i(d1, 32);
+  const int64_t zc = std::max<int64_t>(1, std::min<int64_t>(rest, std::min<int64_t>(65535, (152 * 16 + tiles - 1) / tiles)));
+  dim3 grid((unsigned)ceil_div_i(d0, 32), (unsigned)ceil_div_i(d1, 32), (unsigned)zc);
   dim3 block(32, 8);
-  if (rest > 65535) return cudaErrorInvalidValue;
   if (xtype == XT_BF16)
     launch_k(transpose01_kernel<__nv_bfloat16>, grid, block, 0, s, (const __nv_bfloat16*)in, (__nv_bfloat16*)out, d0, d1, rest);
   else
