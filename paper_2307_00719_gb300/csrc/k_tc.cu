@@ -962,9 +962,28 @@ __global__ void __launch_bounds__(128) stage2_warp_kernel(Stage2Args a) {
   const int64_t in = blockIdx.x;
   const int64_t ncomb = a.Jlo * a.Jhi;
   const int64_t q0 = (int64_t)blockIdx.y * a.per, q1 = min(ncomb, q0 + a.per);
-  float acc[PO];
+  float acc[PO], sacc[PO];
 #pragma unroll
-  for (int u = 0; u < PO; ++u) acc[u] = 0.f;
+  for (int u = 0; u < PO; ++u) acc[u] = sacc[u] = 0.f;
+  int64_t cur_hi = -1;
+  // acc[w + R x] += sum_c A(h)[x + R c] sacc[c + R w]; sacc = 0
+  auto flush = [&](int64_t h) {
+    const float* aq = a.TA + h * PO;
+    float am[PO];
+#pragma unroll
+    for (int u = 0; u < PO; ++u) am[u] = __ldg(aq + u);
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+      for (int w = 0; w < R; ++w) {
+        float v = 0.f;
+#pragma unroll
+        for (int c = 0; c < R; ++c) v = fmaf(am[x + R * c], sacc[c + R * w], v);
+        acc[w + R * x] += v;
+      }
+#pragma unroll
+    for (int u = 0; u < PO; ++u) sacc[u] = 0.f;
+  };
   for (int64_t qb = q0 + 32 * warp; qb < q1; qb += 32 * NW) {
     const int nq = (int)min((int64_t)32, q1 - qb);
     const int64_t hi0 = qb / a.Jlo, lo0 = qb - hi0 * a.Jlo;
@@ -985,14 +1004,14 @@ __global__ void __launch_bounds__(128) stage2_warp_kernel(Stage2Args a) {
         for (int i = 0; i < PO; ++i) w[i] = __ldg(bs + lane + 32 * i);
 #pragma unroll
         for (int i = 0; i < PO; ++i) {
-          const int f = lane + 32 * i, j = f / PO;
-          sB[j * PS + f - j * PO] = w[i];
+          const int f = lane + 32 * i;
+          sB[PS == PO ? f : f + f / PO] = w[i];
         }
       }
 #pragma unroll
       for (int i = 0; i < PO; ++i) {
-        const int f = lane + 32 * i, j = f / PO;
-        sY[j * PS + f - j * PO] = v[i];
+        const int f = lane + 32 * i;
+        sY[PS == PO ? f : f + f / PO] = v[i];     // j PS + u with f = j PO + u
       }
     } else if (one_seg) {
       const float* ys = a.Y + (lo0 + a.Jlo * (in + a.dn * hi0)) * PO;
@@ -1042,20 +1061,14 @@ __global__ void __launch_bounds__(128) stage2_warp_kernel(Stage2Args a) {
         for (int u = 0; u < PO; ++u) s[u] = y[u];
       }
       if (hasA) {
-        // O = A(i_hi) S, entry (x, w) accumulated at w + R x
-        const float* aq = a.TA + ihi * PO;
-        float am[PO];
+        // A(i_hi) is applied once per run of equal i_hi seen by this lane:
+        // S is summed over the run, then O = A(i_hi) S_run joins the sums
+        if (ihi != cur_hi) {
+          if (cur_hi >= 0) flush(cur_hi);
+          cur_hi = ihi;
+        }
 #pragma unroll
-        for (int u = 0; u < PO; ++u) am[u] = __ldg(aq + u);
-#pragma unroll
-        for (int x = 0; x < R; ++x)
-#pragma unroll
-          for (int w = 0; w < R; ++w) {
-            float v = 0.f;
-#pragma unroll
-            for (int c = 0; c < R; ++c) v = fmaf(am[x + R * c], s[c + R * w], v);
-            acc[w + R * x] += v;
-          }
+        for (int u = 0; u < PO; ++u) sacc[u] += s[u];
       } else {
 #pragma unroll
         for (int x = 0; x < R; ++x)
@@ -1064,6 +1077,7 @@ __global__ void __launch_bounds__(128) stage2_warp_kernel(Stage2Args a) {
       }
     }
   }
+  if (hasA && cur_hi >= 0) flush(cur_hi);
   // fixed-order sums: butterfly within the warp, then warps in order
 #pragma unroll
   for (int u = 0; u < PO; ++u) {
