@@ -34,7 +34,7 @@ METRIC = "STR/rSTR tensor entries/s per update, % roofline, rel. fit err vs FP64
 # DRAM bytes (read + write) of one stage-1 launch on the order-4 workload, from the
 # ncu capture summarised in profiles/ncu_str_order4_update_kernels.md; set to None
 # whenever the stage-1 kernel changes until it is captured again
-STAGE1_DRAM_BYTES = None
+STAGE1_DRAM_BYTES = 10549760
 W2 = synth.WORKLOADS["order4"]
 W3 = synth.WORKLOADS["rand3"]
 WORKLOAD_DESC = ("order4: 64x64x64xT, T=400, TR-ranks all 8, Gaussian cores, SNR 30 dB, "
