@@ -209,28 +209,33 @@ cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const do
 // Twiddles: cos/sin(2 pi j / L) for j < L, computed once on the host side of
 // the launch in FP64 and indexed by (k * i) mod L.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int FB>
 __global__ void dft_mode_kernel(const void* __restrict__ in, int in_type, T* __restrict__ out,
-                                int64_t L, int64_t inner, int64_t nfib, const double* __restrict__ d,
-                                const double* __restrict__ tw, int FB) {
+                                int L, int64_t inner, int64_t nfib, const double* __restrict__ d,
+                                const double* __restrict__ tw) {
   PDL_ENTRY();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sre = (T*)smraw;                 // L * FB
   T* sim = sre + L * FB;              // L * FB
   T* cs = sim + L * FB;               // L
   T* sn = cs + L;                     // L
-  for (int64_t j = threadIdx.x; j < L; j += blockDim.x) { cs[j] = (T)tw[2 * j]; sn[j] = (T)tw[2 * j + 1]; }
+  __shared__ int64_t fbase[FB];       // offset of element 0 of each staged fibre
+  for (int j = threadIdx.x; j < L; j += blockDim.x) { cs[j] = (T)tw[2 * j]; sn[j] = (T)tw[2 * j + 1]; }
   const T scale = (T)(1.0 / sqrt((double)L));
   for (int64_t fb0 = (int64_t)blockIdx.x * FB; fb0 < nfib; fb0 += (int64_t)gridDim.x * FB) {
     // fibre f: inner index = f % inner, outer = f / inner; element i at
     // outer * L * inner + i * inner + inner_idx
-    for (int64_t e = threadIdx.x; e < L * FB; e += blockDim.x) {
-      const int ff = (int)(e % FB);
-      const int64_t i = e / FB;
-      const int64_t f = fb0 + ff;
+    if (threadIdx.x < FB) {
+      const int64_t f = fb0 + threadIdx.x;
+      fbase[threadIdx.x] = f < nfib ? (f / inner) * (int64_t)L * inner + (f % inner) : -1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < L * FB; e += blockDim.x) {
+      const int ff = e % FB, i = e / FB;
+      const int64_t fo = fbase[ff];
       T re = 0, im = 0;
-      if (f < nfib) {
-        const int64_t o = (f / inner) * L * inner + i * inner + (f % inner);
+      if (fo >= 0) {
+        const int64_t o = fo + (int64_t)i * inner;
         switch (in_type) {
           case XT_BF16: re = (T)__bfloat162float(((const __nv_bfloat16*)in)[o]); break;
           case XT_F32: re = (T)((const float*)in)[o]; break;
@@ -244,13 +249,12 @@ __global__ void dft_mode_kernel(const void* __restrict__ in, int in_type, T* __r
       sim[i * FB + ff] = im;
     }
     __syncthreads();
-    for (int64_t e = threadIdx.x; e < L * FB; e += blockDim.x) {
-      const int ff = (int)(e % FB);
-      const int64_t kk = e / FB;
-      const int64_t f = fb0 + ff;
+    for (int e = threadIdx.x; e < L * FB; e += blockDim.x) {
+      const int ff = e % FB, kk = e / FB;
+      const int64_t fo = fbase[ff];
       T are = 0, aim = 0;
-      int64_t ph = 0;   // (kk * i) mod L
-      for (int64_t i = 0; i < L; ++i) {
+      int ph = 0;   // (kk * i) mod L
+      for (int i = 0; i < L; ++i) {
         const T c = cs[ph], sv = sn[ph];     // F(k,i) = c - i s
         const T xr = sre[i * FB + ff], xi = sim[i * FB + ff];
         are += c * xr + sv * xi;
@@ -258,8 +262,8 @@ __global__ void dft_mode_kernel(const void* __restrict__ in, int in_type, T* __r
         ph += kk;
         if (ph >= L) ph -= L;
       }
-      if (f < nfib) {
-        const int64_t o = (f / inner) * L * inner + kk * inner + (f % inner);
+      if (fo >= 0) {
+        const int64_t o = fo + (int64_t)kk * inner;
         out[2 * o] = are * scale;
         out[2 * o + 1] = aim * scale;
       }
@@ -287,7 +291,14 @@ static const double* twiddles(int64_t L) {
   }
   double* dptr = nullptr;
   if (cudaMalloc(&dptr, 2 * L * sizeof(double)) != cudaSuccess) return nullptr;
-  cudaMemcpy(dptr, h.data(), 2 * L * sizeof(double), cudaMemcpyHostToDevice);
+  // a copy from pageable memory may still be in flight when cudaMemcpy returns, and
+  // the legacy stream does not order the non-blocking streams that read the table
+  if (cudaMemcpy(dptr, h.data(), 2 * L * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dptr);
+    return nullptr;
+  }
   g_tw[key] = dptr;
   return dptr;
 }
@@ -298,29 +309,39 @@ static const double* twiddles(int64_t L) {
 // stages (decimation in time), then either the unitary transform written as
 // complex values, or (inverse, unmixing) base + d_k * Re(result) as FP64.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int FB>
 __global__ void fft_mode_kernel(const void* __restrict__ in, int in_type, void* __restrict__ out,
-                                int out_real, const double* __restrict__ base, int64_t L, int logL,
+                                int out_real, const double* __restrict__ base, int L, int logL,
                                 int64_t inner, int64_t nfib, const double* __restrict__ dpre,
                                 const double* __restrict__ dpost, int inverse,
-                                const double* __restrict__ tw, int FB) {
+                                const double* __restrict__ tw) {
   PDL_ENTRY();
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sre = (T*)smraw;                 // L * FB
-  T* sim = sre + L * FB;              // L * FB
-  T* cs = sim + L * FB;               // L
+  constexpr int FS = FB + 1;           // odd row stride: natural-order rows are conflict-free
+  T* sre = (T*)smraw;                 // L * FS
+  T* sim = sre + L * FS;              // L * FS
+  T* cs = sim + L * FS;               // L
   T* sn = cs + L;                     // L
-  for (int64_t j = threadIdx.x; j < L; j += blockDim.x) { cs[j] = (T)tw[2 * j]; sn[j] = (T)tw[2 * j + 1]; }
+  __shared__ int64_t fbase[FB];       // offset of element 0 of each staged fibre
+  for (int j = threadIdx.x; j < L; j += blockDim.x) { cs[j] = (T)tw[2 * j]; sn[j] = (T)tw[2 * j + 1]; }
   const T scale = (T)(1.0 / sqrt((double)L));
   const T sgn = inverse ? (T)1 : (T)-1;   // exp(sgn * 2 pi i t / L) = cos + sgn * i sin
+  // inner == 1: a fibre is L contiguous elements, threads run along it (coalesced);
+  // otherwise adjacent fibres are adjacent in memory, threads run across them
+  const bool along = inner == 1;
   for (int64_t fb0 = (int64_t)blockIdx.x * FB; fb0 < nfib; fb0 += (int64_t)gridDim.x * FB) {
-    for (int64_t e = threadIdx.x; e < L * FB; e += blockDim.x) {
-      const int ff = (int)(e % FB);
-      const int64_t i = e / FB;
-      const int64_t f = fb0 + ff;
+    if (threadIdx.x < FB) {
+      const int64_t f = fb0 + threadIdx.x;
+      fbase[threadIdx.x] = f < nfib ? (f / inner) * (int64_t)L * inner + (f % inner) : -1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < L * FB; e += blockDim.x) {
+      const int ff = along ? e >> logL : e % FB;
+      const int i = along ? e & (L - 1) : e / FB;
+      const int64_t fo = fbase[ff];
       T re = 0, im = 0;
-      if (f < nfib) {
-        const int64_t o = (f / inner) * L * inner + i * inner + (f % inner);
+      if (fo >= 0) {
+        const int64_t o = fo + (int64_t)i * inner;
         switch (in_type) {
           case XT_BF16: re = (T)__bfloat162float(((const __nv_bfloat16*)in)[o]); break;
           case XT_F32: re = (T)((const float*)in)[o]; break;
@@ -330,38 +351,38 @@ __global__ void fft_mode_kernel(const void* __restrict__ in, int in_type, void* 
         }
         if (dpre) { re *= (T)dpre[i]; im *= (T)dpre[i]; }
       }
-      const int64_t br = (int64_t)(__brev((unsigned)i) >> (32 - logL));
-      sre[br * FB + ff] = re;
-      sim[br * FB + ff] = im;
+      const int br = (int)(__brev((unsigned)i) >> (32 - logL));
+      sre[br * FS + ff] = re;
+      sim[br * FS + ff] = im;
     }
     __syncthreads();
     for (int st = 0; st < logL; ++st) {
-      const int64_t half = (int64_t)1 << st;
-      const int64_t tstep = L >> (st + 1);     // twiddle index stride = L / len
-      for (int64_t e = threadIdx.x; e < (L / 2) * FB; e += blockDim.x) {
-        const int ff = (int)(e % FB);
-        const int64_t b = e / FB;
-        const int64_t g = b >> st, j = b & (half - 1);
-        const int64_t i0 = g * 2 * half + j, i1 = i0 + half;
-        const int64_t t = j * tstep;
+      const int half = 1 << st;
+      const int tstep = L >> (st + 1);     // twiddle index stride = L / len
+      for (int e = threadIdx.x; e < (L / 2) * FB; e += blockDim.x) {
+        const int ff = e % FB;
+        const int b = e / FB;
+        const int g = b >> st, j = b & (half - 1);
+        const int i0 = g * 2 * half + j, i1 = i0 + half;
+        const int t = j * tstep;
         const T wr = cs[t], wi = sgn * sn[t];
-        const T xr = sre[i1 * FB + ff], xi = sim[i1 * FB + ff];
+        const T xr = sre[i1 * FS + ff], xi = sim[i1 * FS + ff];
         const T vr = xr * wr - xi * wi, vi = xr * wi + xi * wr;
-        const T ur = sre[i0 * FB + ff], ui = sim[i0 * FB + ff];
-        sre[i0 * FB + ff] = ur + vr;
-        sim[i0 * FB + ff] = ui + vi;
-        sre[i1 * FB + ff] = ur - vr;
-        sim[i1 * FB + ff] = ui - vi;
+        const T ur = sre[i0 * FS + ff], ui = sim[i0 * FS + ff];
+        sre[i0 * FS + ff] = ur + vr;
+        sim[i0 * FS + ff] = ui + vi;
+        sre[i1 * FS + ff] = ur - vr;
+        sim[i1 * FS + ff] = ui - vi;
       }
       __syncthreads();
     }
-    for (int64_t e = threadIdx.x; e < L * FB; e += blockDim.x) {
-      const int ff = (int)(e % FB);
-      const int64_t kk = e / FB;
-      const int64_t f = fb0 + ff;
-      if (f < nfib) {
-        const int64_t o = (f / inner) * L * inner + kk * inner + (f % inner);
-        T yr = sre[kk * FB + ff] * scale, yi = sim[kk * FB + ff] * scale;
+    for (int e = threadIdx.x; e < L * FB; e += blockDim.x) {
+      const int ff = along ? e >> logL : e % FB;
+      const int kk = along ? e & (L - 1) : e / FB;
+      const int64_t fo = fbase[ff];
+      if (fo >= 0) {
+        const int64_t o = fo + (int64_t)kk * inner;
+        T yr = sre[kk * FS + ff] * scale, yi = sim[kk * FS + ff] * scale;
         if (dpost) { yr *= (T)dpost[kk]; yi *= (T)dpost[kk]; }
         if (out_real) ((double*)out)[o] = (base ? base[o] : 0.0) + (double)yr;
         else { ((T*)out)[2 * o] = yr; ((T*)out)[2 * o + 1] = yi; }
@@ -383,14 +404,28 @@ static cudaError_t launch_fft(const void* in, int in_type, void* out, int out_re
                               int64_t L, int logL, int64_t inner, int64_t nfib, const double* dpre,
                               const double* dpost, int inverse, const double* tw, cudaStream_t s) {
   const int tsize = sizeof(T);
+  // fibres per CTA: up to 16, fewer when there are few fibres (two CTAs per SM at least)
   int FB = 16;
-  while (FB > 1 && (size_t)(2 * L * FB + 2 * L) * tsize > 96 * 1024) FB /= 2;
-  const size_t sm = (size_t)(2 * L * FB + 2 * L) * tsize;
-  cudaError_t e = cudaFuncSetAttribute(fft_mode_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+  while (FB > 1 && (size_t)(2 * L * (FB + 1) + 2 * L) * tsize > 96 * 1024) FB /= 2;
+  while (FB > 1 && (nfib + FB - 1) / FB < 2 * 152) FB /= 2;
+  const size_t sm = (size_t)(2 * L * (FB + 1) + 2 * L) * tsize;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nfib + FB - 1) / FB, 152 * 8));
-  launch_k(fft_mode_kernel<T>, (unsigned)blocks, 256, sm, s, in, in_type, out, out_real, base, L, logL, inner, nfib,
-                                                       dpre, dpost, inverse, tw, FB);
+#define STR_FFT_CASE(F)                                                                                   \
+  do {                                                                                                    \
+    cudaError_t e = cudaFuncSetAttribute(fft_mode_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)sm);                                                        \
+    if (e != cudaSuccess) return e;                                                                       \
+    launch_k(fft_mode_kernel<T, F>, (unsigned)blocks, 256, sm, s, in, in_type, out, out_real, base, (int)L, \
+             logL, inner, nfib, dpre, dpost, inverse, tw);                                                \
+  } while (0)
+  switch (FB) {
+    case 16: STR_FFT_CASE(16); break;
+    case 8: STR_FFT_CASE(8); break;
+    case 4: STR_FFT_CASE(4); break;
+    case 2: STR_FFT_CASE(2); break;
+    default: STR_FFT_CASE(1); break;
+  }
+#undef STR_FFT_CASE
   return cudaGetLastError();
 }
 
@@ -408,18 +443,34 @@ cudaError_t launch_dft_mode(const void* in, int in_type, void* out, int out_cplx
     return launch_fft<float>(in, in_type, out, 0, nullptr, L, logL, inner, nfib, d, nullptr, 0, tw, s);
   }
   const int tsize = out_cplx_compute == 2 ? 8 : 4;
+  if (L > 16384) return cudaErrorInvalidValue;
   int FB = 16;
   while (FB > 1 && (size_t)(2 * L * FB + 2 * L) * tsize > 96 * 1024) FB /= 2;
   const size_t sm = (size_t)(2 * L * FB + 2 * L) * tsize;
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((nfib + FB - 1) / FB, 152 * 8));
-  if (out_cplx_compute == 2) {
-    cudaFuncSetAttribute(dft_mode_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    launch_k(dft_mode_kernel<double>, (unsigned)blocks, 256, sm, s, in, in_type, (double*)out, L, inner, nfib, d, tw, FB);
-  } else {
-    cudaFuncSetAttribute(dft_mode_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    launch_k(dft_mode_kernel<float>, (unsigned)blocks, 256, sm, s, in, in_type, (float*)out, L, inner, nfib, d, tw, FB);
+#define STR_DFT_CASE(T, F)                                                                                \
+  do {                                                                                                    \
+    cudaError_t e = cudaFuncSetAttribute(dft_mode_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)sm);                                                        \
+    if (e != cudaSuccess) return e;                                                                       \
+    launch_k(dft_mode_kernel<T, F>, (unsigned)blocks, 256, sm, s, in, in_type, (T*)out, (int)L, inner, nfib, d, tw); \
+  } while (0)
+#define STR_DFT_FB(T)                    \
+  switch (FB) {                          \
+    case 16: STR_DFT_CASE(T, 16); break; \
+    case 8: STR_DFT_CASE(T, 8); break;   \
+    case 4: STR_DFT_CASE(T, 4); break;   \
+    case 2: STR_DFT_CASE(T, 2); break;   \
+    default: STR_DFT_CASE(T, 1); break;  \
   }
+  if (out_cplx_compute == 2) {
+    STR_DFT_FB(double);
+  } else {
+    STR_DFT_FB(float);
+  }
+#undef STR_DFT_FB
+#undef STR_DFT_CASE
   return cudaGetLastError();
 }
 
