@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) wgram_kernel(const T* __restrict__ g, con
   if (r < RR && c < RR) part[((int64_t)blockIdx.z * RR + r) * RR + c] = acc;
 }
 
-// Same weighted Gram for FP32 samples without the FP64 pipe: every term
+// Same weighted Gram for FP32 samples (real or complex) without the FP64 pipe: every term
 // w_s g_a g_b is formed as an FP32 pair (g_a g_b exactly by FMA, times the
 // weight carried as an FP32 pair) and summed with error-free transformations
 // (Dekker / Knuth), so the split sum carries about 44 significant bits.
@@ -136,11 +136,15 @@ __device__ __forceinline__ void pair_add(float& sh, float& sl, float ph, float p
   sl += e + pl;
 }
 
+// C: complex samples, term w_s Re(g_a conj(g_b)) = w_s (re_a re_b + im_a im_b),
+// both products exact pairs, summed error-free before the weight
+template <bool C>
 __global__ void __launch_bounds__(256) wgram_pair_kernel(const float* __restrict__ g, const double* __restrict__ w,
                                                          int64_t m, int64_t per, int RR, double* __restrict__ part) {
   PDL_ENTRY();
   constexpr int CH = 64;
-  __shared__ float sa[CH][16], sb[CH][16];
+  constexpr int W = C ? 2 : 1;
+  __shared__ float sa[CH][16 * W], sb[CH][16 * W];
   __shared__ float swh[CH], swl[CH];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int r0 = blockIdx.y * 16, c0 = blockIdx.x * 16;
@@ -148,15 +152,16 @@ __global__ void __launch_bounds__(256) wgram_pair_kernel(const float* __restrict
   float sh = 0.f, sl = 0.f;
   for (int64_t s0 = sbeg; s0 < send; s0 += CH) {
     const int ns = (send - s0 < CH) ? (int)(send - s0) : CH;
-    for (int e = threadIdx.x; e < CH * 16; e += 256) {
-      const int ss = e >> 4, cc = e & 15;
+    for (int e = threadIdx.x; e < CH * 16 * W; e += 256) {
+      const int ss = e / (16 * W), x = e % (16 * W);
+      const int cc = x / W, q = x % W;
       float va = 0.f, vb = 0.f;
       if (ss < ns) {
-        if (r0 + cc < RR) va = g[(s0 + ss) * RR + r0 + cc];
-        if (c0 + cc < RR) vb = g[(s0 + ss) * RR + c0 + cc];
+        if (r0 + cc < RR) va = g[((s0 + ss) * RR + r0 + cc) * W + q];
+        if (c0 + cc < RR) vb = g[((s0 + ss) * RR + c0 + cc) * W + q];
       }
-      sa[ss][cc] = va;
-      sb[ss][cc] = vb;
+      sa[ss][x] = va;
+      sb[ss][x] = vb;
     }
     for (int e = threadIdx.x; e < CH; e += 256) {
       const double wv = (e < ns) ? (w ? w[s0 + e] : 1.0) : 0.0;
@@ -166,9 +171,19 @@ __global__ void __launch_bounds__(256) wgram_pair_kernel(const float* __restrict
     }
     __syncthreads();
     for (int ss = 0; ss < ns; ++ss) {
-      const float a = sa[ss][ty], b = sb[ss][tx];
-      const float ph = a * b;
-      const float pl = fmaf(a, b, -ph);          // a b = ph + pl exactly
+      float ph, pl;
+      if (C) {
+        const float ar = sa[ss][2 * ty], ai = sa[ss][2 * ty + 1], br = sb[ss][2 * tx], bi = sb[ss][2 * tx + 1];
+        const float h1 = ar * br, l1 = fmaf(ar, br, -h1);   // exact products
+        const float h2 = ai * bi, l2 = fmaf(ai, bi, -h2);
+        ph = h1 + h2;                                       // two-sum of the high parts
+        const float bb = ph - h1;
+        pl = ((h1 - (ph - bb)) + (h2 - bb)) + (l1 + l2);
+      } else {
+        const float a = sa[ss][ty], b = sb[ss][tx];
+        ph = a * b;
+        pl = fmaf(a, b, -ph);                     // a b = ph + pl exactly
+      }
       const float wh = swh[ss], wl = swl[ss];
       const float th = wh * ph;
       float tl = fmaf(wh, ph, -th);              // wh ph = th + tl exactly
@@ -195,8 +210,8 @@ cudaError_t launch_weighted_gram(const void* gs, int compute, int cplx, const do
     if (cplx) launch_k(wgram_kernel<double, true>, grid, 256, 0, s, (const double*)gs, w, m, per, RR, part);
     else launch_k(wgram_kernel<double, false>, grid, 256, 0, s, (const double*)gs, w, m, per, RR, part);
   } else {
-    if (cplx) launch_k(wgram_kernel<float, true>, grid, 256, 0, s, (const float*)gs, w, m, per, RR, part);
-    else launch_k(wgram_pair_kernel, grid, 256, 0, s, (const float*)gs, w, m, per, RR, part);
+    if (cplx) launch_k(wgram_pair_kernel<true>, grid, 256, 0, s, (const float*)gs, w, m, per, RR, part);
+    else launch_k(wgram_pair_kernel<false>, grid, 256, 0, s, (const float*)gs, w, m, per, RR, part);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
