@@ -135,7 +135,7 @@ struct str_ctx {
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   bool side2_used = false;
   DevBuf mbuf[2];
-  DevBuf qf, qlo, fcount, ring2, ring3, levx, chain_scratch;
+  DevBuf qf, qlo, fcount, ring2, ring3, levx, chain_scratch, tc_bhi2, tc_blo2;
   bool fcount_dirty = false;     // fcount allocated but not yet cleared on a stream
   const double* qsplit_of = nullptr;   // the Q whose FP32 pair (qf, qlo) is current   // FP32 copy of Q and the last-CTA counter of the fused ring GEMM + factor
 
@@ -599,11 +599,75 @@ str_status mttkrp_sampled_tc(str_ctx* c, const SlabView& v, int n, const void* c
   return STR_OK;
 }
 
+// Sampled complex MTTKRP (KSRFT, FP32 slab arithmetic) on the tensor cores: two
+// real split-K GEMMs for Re P and Im P; out = complex FP64 (interleaved).
+str_status mttkrp_sampled_tc_cplx(str_ctx* c, const SlabView& v, int n, const void* const* cores, const int32_t* idxs,
+                                  double wscale, double* out, void* gs, double* ws, cudaStream_t s, bool* used) {
+  *used = false;
+  if (v.xtype != XT_C32) return STR_OK;
+  const int RR = c->RR(n);
+  const int64_t In = v.dim[n];
+  const int64_t m = c->opt.m;
+  if (RR > 160 || In < 32 || m < 32) return STR_OK;
+  const int Npad = ((RR + 15) / 16) * 16;
+  const int Kpad = (int)(((m + 31) / 32) * 32);
+  const int K2 = 2 * Kpad;
+  if (!tc_supported(K2, XT_F32, nullptr)) return STR_OK;
+  MttkrpArgs a;
+  a.X = v.X;
+  a.xtype = v.xtype;
+  a.N = c->N;
+  a.n = n;
+  for (int k = 0; k < c->N; ++k) { a.dim[k] = v.dim[k]; a.core[k] = cores[k]; }
+  for (int k = 0; k <= c->N; ++k) a.R[k] = c->R[k];
+  a.compute = 1;
+  a.cplx = 1;
+  a.nfib = m;
+  a.idxs = idxs;
+  a.m = m;
+  a.wscale = wscale;
+  a.gs_out = gs;
+  a.ws_out = ws;
+  const size_t bsz = (size_t)Npad * K2 * 4;
+  TRY(grow(c, c->tc_bhi, bsz));
+  TRY(grow(c, c->tc_blo, bsz));
+  TRY(grow(c, c->tc_bhi2, bsz));
+  TRY(grow(c, c->tc_blo2, bsz));
+  TRY(grow(c, c->tc_xt, (size_t)In * K2 * 4));
+  STR_CUDA_TRY(cudaMemsetAsync(c->tc_bhi.p, 0, bsz, s));
+  STR_CUDA_TRY(cudaMemsetAsync(c->tc_blo.p, 0, bsz, s));
+  STR_CUDA_TRY(cudaMemsetAsync(c->tc_bhi2.p, 0, bsz, s));
+  STR_CUDA_TRY(cudaMemsetAsync(c->tc_blo2.p, 0, bsz, s));
+  LCHK(c, STR_K_SKETCH, launch_sampled_rows_cplx(a, Kpad, (float*)c->tc_bhi.p, (float*)c->tc_blo.p,
+                                                 (float*)c->tc_bhi2.p, (float*)c->tc_blo2.p, s));
+  LCHK(c, STR_K_SKETCH, launch_gather_fibres_cplx(a, Kpad, (float*)c->tc_xt.p, s));
+  c->tc_xt_src = nullptr;   // the buffer no longer holds the transposed slab
+  const int mt = (int)((In + 127) / 128);
+  const int want = std::max(1, std::min(K2 / 32, (2 * 152 + mt - 1) / mt));
+  const int splits = gemm_tc_splitk_count(K2, want);
+  const size_t psz = (size_t)splits * In * RR;
+  TRY(grow(c, c->tc_part, 2 * psz * 4));
+  float* pre = (float*)c->tc_part.p;
+  float* pim = pre + psz;
+  LCHK(c, STR_K_MTTKRP, launch_gemm_tc_splitk(c->tc_xt.p, XT_F32, In, K2, (const float*)c->tc_bhi.p,
+                                               (const float*)c->tc_blo.p, RR, Npad, splits, pre, c->d_status, s));
+  LCHK(c, STR_K_MTTKRP, launch_gemm_tc_splitk(c->tc_xt.p, XT_F32, In, K2, (const float*)c->tc_bhi2.p,
+                                               (const float*)c->tc_blo2.p, RR, Npad, splits, pim, c->d_status, s));
+  LCHK(c, STR_K_REDUCE, launch_reduce_cplx_pair(pre, pim, splits, In * RR, out, s));
+  *used = true;
+  return STR_OK;
+}
+
 str_status mttkrp_into(str_ctx* c, const SlabView& v, int n, const void* const* cores, bool sampled,
                        const int32_t* idxs, bool lev, const double* const* pk, double wscale,
                        bool cplx, const double* base, double* out, void* gs, double* ws,
                        cudaStream_t s, PartialSum* defer = nullptr) {
   if (defer) *defer = PartialSum();
+  if (sampled && cplx && c->compute == 1 && c->opt.mttkrp_path == 0) {
+    bool used = false;
+    TRY(mttkrp_sampled_tc_cplx(c, v, n, cores, idxs, wscale, out, gs, ws, s, &used));
+    if (used) return STR_OK;
+  }
   if (sampled && !cplx && c->compute == 1 && c->opt.mttkrp_path == 0) {
     bool used = false;
     TRY(mttkrp_sampled_tc(c, v, n, cores, idxs, lev, pk, wscale, base, out, gs, ws, s, &used, defer));

@@ -1201,6 +1201,122 @@ __global__ void gather_fibres_kernel(MttkrpArgs a, int Kpad, XT* __restrict__ A)
   }
 }
 
+// Complex samples (KSRFT, mixed slab and cores in complex FP32): P = X_S diag(w)
+// conj(G_S) as two real GEMMs over K' = 2 Kpad with A = [Re X_S | Im X_S]:
+//   Re P = A [w Re G_S ; w Im G_S],   Im P = A [-w Im G_S ; w Re G_S].
+// sampled_rows_cplx_kernel writes G_S (complex, for the Gram), w and both B
+// operands (transposed [Npad][2 Kpad], split TF32 hi / lo).
+__global__ void sampled_rows_cplx_kernel(MttkrpArgs a, int Kpad, float* __restrict__ Brh, float* __restrict__ Brl,
+                                         float* __restrict__ Bih, float* __restrict__ Bil) {
+  PDL_ENTRY();
+  const int N = a.N, n = a.n;
+  const int Ra = a.R[n], Rb = a.R[n + 1];
+  const int RR = Ra * Rb;
+  const int64_t K2 = 2 * (int64_t)Kpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.m * Rb; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = e / Rb;
+    const int r = (int)(e - f * Rb);
+    const double w = a.wscale;
+    float vr[STR_MAXR], vi[STR_MAXR], tr[STR_MAXR], ti[STR_MAXR];
+    int cols = 0;
+    for (int q = 0; q < N - 1; ++q) {
+      const int k = (n + 1 + q) % N;
+      const int i = a.idxs[(int64_t)k * a.m + f];
+      const int Rk = a.R[k], Rk1 = a.R[k + 1];
+      const float* g = (const float*)a.core[k] + 2 * (int64_t)i * Rk * Rk1;   // interleaved (re, im)
+      if (q == 0) {
+#pragma unroll
+        for (int c = 0; c < STR_MAXR; ++c) {
+          vr[c] = c < Rk1 ? g[2 * (r + Rk * c)] : 0.f;
+          vi[c] = c < Rk1 ? g[2 * (r + Rk * c) + 1] : 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < STR_MAXR; ++c) {
+          float sr = 0.f, si = 0.f;
+          if (c < Rk1)
+            for (int x = 0; x < cols; ++x) {
+              const float gr = g[2 * (x + Rk * c)], gi = g[2 * (x + Rk * c) + 1];
+              sr = fmaf(vr[x], gr, fmaf(-vi[x], gi, sr));
+              si = fmaf(vr[x], gi, fmaf(vi[x], gr, si));
+            }
+          tr[c] = sr;
+          ti[c] = si;
+        }
+#pragma unroll
+        for (int c = 0; c < STR_MAXR; ++c) { vr[c] = tr[c]; vi[c] = ti[c]; }
+      }
+      cols = Rk1;
+    }
+    float* gs = (float*)a.gs_out;
+    for (int c = 0; c < Ra; ++c) {
+      const int col = c + Ra * r;
+      if (gs) { gs[2 * (f * RR + col)] = vr[c]; gs[2 * (f * RR + col) + 1] = vi[c]; }
+      const double re = w * (double)vr[c], im = w * (double)vi[c];
+      const float reh = tf32_rn((float)re), reL = tf32_rn((float)(re - (double)reh));
+      const float imh = tf32_rn((float)im), imL = tf32_rn((float)(im - (double)imh));
+      const int64_t o = (int64_t)col * K2;
+      Brh[o + f] = reh;          Brl[o + f] = reL;
+      Brh[o + Kpad + f] = imh;   Brl[o + Kpad + f] = imL;
+      Bih[o + f] = -imh;         Bil[o + f] = -imL;
+      Bih[o + Kpad + f] = reh;   Bil[o + Kpad + f] = reL;
+    }
+    if (r == 0 && a.ws_out) a.ws_out[f] = w;
+  }
+}
+
+// A[row][s] = Re, A[row][Kpad + s] = Im of the complex mode-n fibre at the
+// sampled indices of s; 0 for s >= m
+__global__ void gather_fibres_cplx_kernel(MttkrpArgs a, int Kpad, float* __restrict__ A) {
+  PDL_ENTRY();
+  __shared__ int64_t sbase[32];
+  const int N = a.N, n = a.n;
+  const int64_t In = a.dim[n];
+  int64_t stride[STR_MAXN];
+  int64_t st = 1;
+  for (int k = 0; k < N; ++k) { stride[k] = st; st *= a.dim[k]; }
+  const int f = blockIdx.x * 32 + threadIdx.x;
+  if (threadIdx.y == 0) {
+    int64_t off = -1;
+    if (f < a.m) {
+      off = 0;
+      for (int k = 0; k < N; ++k)
+        if (k != n) off += (int64_t)a.idxs[(int64_t)k * a.m + f] * stride[k];
+    }
+    sbase[threadIdx.x] = off;
+  }
+  __syncthreads();
+  const int64_t off = sbase[threadIdx.x];
+  const float* X = (const float*)a.X;
+  for (int64_t row = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; row < In; row += (int64_t)gridDim.y * blockDim.y) {
+    float re = 0.f, im = 0.f;
+    if (off >= 0) {
+      const int64_t o = off + row * stride[n];
+      re = X[2 * o];
+      im = X[2 * o + 1];
+    }
+    if (f < Kpad) {
+      A[row * 2 * Kpad + f] = re;
+      A[row * 2 * Kpad + Kpad + f] = im;
+    }
+  }
+}
+
+// out[2 e] = sum_s Pre[s][e], out[2 e + 1] = sum_s Pim[s][e]   (FP64, fixed order)
+__global__ void reduce_cplx_pair_kernel(const float* __restrict__ Pre, const float* __restrict__ Pim, int splits,
+                                        int64_t count, double* __restrict__ out) {
+  PDL_ENTRY();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q < splits; ++q) {
+      sr += (double)Pre[(int64_t)q * count + e];
+      si += (double)Pim[(int64_t)q * count + e];
+    }
+    out[2 * e] = sr;
+    out[2 * e + 1] = si;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // tensor maps (driver entry point resolved once through the runtime)
 // ---------------------------------------------------------------------------
@@ -1384,6 +1500,29 @@ cudaError_t launch_sampled_rows(const MttkrpArgs& a, int Kpad, float* Bhi, float
   const int64_t total = a.m * a.R[a.n + 1];
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, 152 * 8));
   launch_k(sampled_rows_kernel, blocks, 128, 0, s, a, Kpad, Bhi, Blo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sampled_rows_cplx(const MttkrpArgs& a, int Kpad, float* Brh, float* Brl, float* Bih, float* Bil,
+                                     cudaStream_t s) {
+  const int64_t total = a.m * a.R[a.n + 1];
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 127) / 128, 152 * 8));
+  launch_k(sampled_rows_cplx_kernel, blocks, 128, 0, s, a, Kpad, Brh, Brl, Bih, Bil);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_fibres_cplx(const MttkrpArgs& a, int Kpad, float* A, cudaStream_t s) {
+  const int64_t In = a.dim[a.n];
+  dim3 block(32, 8);
+  dim3 grid((unsigned)(Kpad / 32), (unsigned)std::max<int64_t>(1, std::min<int64_t>((In + 7) / 8, 64)));
+  launch_k(gather_fibres_cplx_kernel, grid, block, 0, s, a, Kpad, A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_cplx_pair(const float* Pre, const float* Pim, int splits, int64_t count, double* out,
+                                    cudaStream_t s) {
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 152 * 4));
+  launch_k(reduce_cplx_pair_kernel, blocks, 256, 0, s, Pre, Pim, splits, count, out);
   return cudaGetLastError();
 }
 

@@ -195,6 +195,13 @@ cudaError_t launch_stage1_tc(const void* Xa, int xtype, int64_t M, int K, const 
 // and the split-K GEMM (partials [splits][M][N])
 cudaError_t launch_sampled_rows(const MttkrpArgs& a, int Kpad, float* Bhi, float* Blo, cudaStream_t s);
 cudaError_t launch_gather_fibres(const MttkrpArgs& a, int Kpad, void* A, cudaStream_t s);
+// complex samples (KSRFT): B operands of Re P and Im P, A = [Re X_S | Im X_S] over
+// K' = 2 Kpad, and the pairwise sum of the two split-K partial sets into complex FP64
+cudaError_t launch_sampled_rows_cplx(const MttkrpArgs& a, int Kpad, float* Brh, float* Brl, float* Bih, float* Bil,
+                                     cudaStream_t s);
+cudaError_t launch_gather_fibres_cplx(const MttkrpArgs& a, int Kpad, float* A, cudaStream_t s);
+cudaError_t launch_reduce_cplx_pair(const float* Pre, const float* Pim, int splits, int64_t count, double* out,
+                                    cudaStream_t s);
 cudaError_t launch_gemm_tc_splitk(const void* A, int xtype, int64_t M, int Kpad, const float* Bhi,
                                   const float* Blo, int N, int Npad, int splits, float* Y, int* status,
                                   cudaStream_t s);
