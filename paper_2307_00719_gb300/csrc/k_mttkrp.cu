@@ -318,7 +318,8 @@ int mttkrp_plan_splits(const MttkrpArgs& a, int64_t* fib_per_split) {
   const int BM = a.dim[a.n] <= 16 ? 16 : 64;
   const int gx = ceil_div_i(a.dim[a.n], BM);
   const int target = 2 * 152;
-  int64_t min_chunk = 256;
+  // sampled problems have few fibres (the sketch size): smaller chunks keep the SMs busy
+  int64_t min_chunk = a.idxs ? 32 : 256;
   int64_t splits = std::max<int64_t>(1, target / std::max(1, gx));
   splits = std::min<int64_t>(splits, std::max<int64_t>(1, (a.nfib + min_chunk - 1) / min_chunk));
   int64_t per = (a.nfib + splits - 1) / splits;
