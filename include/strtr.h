@@ -110,8 +110,8 @@ str_status str_default_options(str_options* opt);
  * Computes the initial cores of X0 by TR-ALS-NE (Alg. 2; stops per
  * opt->init_tol / init_max_it, Sec. 4) from the host FP64 initial guess
  * `guess` (N pointers, core n with I_n rows, the temporal one with t_init
- * rows), then P_n = X0_[n] G^{!=n}_[2] and Q_n = (H^{!=n})_<2> (Alg. 4,
- * lines 2-6) or their sketched forms (Alg. 5, lines 2-5, draws at tau = 0).
+ * rows), then P_n = X0_[n] G^{!=n}_[2] and Q_n = (H^{!=n})_<2> (the
+ * initialisation of Alg. 4) or their sketched forms (Alg. 5, draws at tau = 0).
  *   out    : receives the new context (owns all device state); *out = NULL on error
  *   X0     : initial tensor I_1 x .. x I_{N-1} x t_init (device or host)
  *   ranks  : host array R_1..R_N
@@ -124,7 +124,7 @@ str_status str_init(str_ctx** out, const str_tensor* X0, const int* ranks,
 /*
  * str_init_cores -- as str_init, but takes the initial cores as given (host
  * FP64, N pointers in the core layout, the temporal core with t_init rows) and
- * only builds P_n, Q_n from X0 (Alg. 4, lines 2-6; Alg. 5, lines 2-5).
+ * only builds P_n, Q_n from X0 (Alg. 4; Alg. 5).
  * X0 may be NULL: then P_n = 0 and Q_n = 0 (no history) and t_init = the
  * temporal core's row count `t_init`.
  */
@@ -133,7 +133,7 @@ str_status str_init_cores(str_ctx** out, int N, const int64_t* dims, const int* 
                           const str_options* opt, void* stream);
 
 /*
- * str_update -- one time step of STR (Alg. 4, lines 8-19): the temporal core's
+ * str_update -- one time step of STR (Alg. 4): the temporal core's
  * new rows G_N^new = X^new_[N] G^{!=N}_[2] (H^{!=N}_<2>)^dagger are appended,
  * then for n = 1..N-1: P_n += X^new_[n] (G^{!=n}_new)_[2], Q_n += (H^{!=n}_new)_<2>,
  * G_{n(2)} = P_n Q_n^dagger.  With opt.sweeps = s > 1 the step is repeated s

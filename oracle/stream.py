@@ -98,7 +98,7 @@ def str_init(X0: np.ndarray, cores: Sequence[np.ndarray]) -> State:
 
 
 def str_update(st: State, Xnew: np.ndarray, sweeps: int = 1) -> State:
-    """One time step of Alg. 4 (lines 8-19).
+    """One time step of Alg. 4 (its update stage).
 
     Temporal mode: G_N^new = X^new_[N] G^{!=N}_[2] (H^{!=N}_<2>)^dagger, rows appended.
     Spatial modes n = 1..N-1 in order (later modes see the updated cores):
@@ -115,13 +115,13 @@ def str_update(st: State, Xnew: np.ndarray, sweeps: int = 1) -> State:
     cur = list(st.cores)
     GN_new = None
     for _ in range(max(1, sweeps)):
-        # temporal mode (lines 8-11); the subchain uses G_1..G_{N-1} only
+        # temporal mode first; the subchain uses G_1..G_{N-1} only
         A = subchain_unfold(cur, N)
         M = unfold_cyclic(Xnew, N) @ A
         RN, R1 = _rank_pair(cur, N)
         GN_new = core_fold2(solve_pinv(M, A.T @ A), RN, R1)
         cur[N - 1] = GN_new
-        # spatial modes (lines 12-18)
+        # then the spatial modes in order
         for n in range(1, N):
             A = subchain_unfold(cur, n)
             st.P[n - 1] = P_old[n - 1] + unfold_cyclic(Xnew, n) @ A
@@ -151,7 +151,7 @@ def leverage_probs(G: np.ndarray, rcond: float = 1e-12) -> np.ndarray:
 
 
 def sampled_subchain(cores: Sequence[np.ndarray], idxs: np.ndarray, n: int) -> np.ndarray:
-    """Alg. 3 lines 5-8: start from identity slices and take the slices-Hadamard
+    """Alg. 3: start from identity slices and take the slices-Hadamard
     product with G_k(:, idxs(:,k), :) for k = n+1..N, 1..n-1.  Returns the
     sampled subchain's mode-2 unfolding, m x R_n R_{n+1}, column r_n + R_n r_{n+1}."""
     N = len(cores)
@@ -171,7 +171,7 @@ def sampled_subchain(cores: Sequence[np.ndarray], idxs: np.ndarray, n: int) -> n
 
 
 def sampled_fibres(X: np.ndarray, idxs: np.ndarray, n: int) -> np.ndarray:
-    """Alg. 3 line 9: X_S[n](i_n, s) = X(idxs(s,1), .., i_n, .., idxs(s,N)); I_n x m."""
+    """Alg. 3: X_S[n](i_n, s) = X(idxs(s,1), .., i_n, .., idxs(s,N)); I_n x m."""
     N = X.ndim
     m = idxs.shape[0]
     out = np.empty((X.shape[n - 1], m), dtype=X.dtype)
@@ -219,7 +219,7 @@ def dft_mix_core(G: np.ndarray, d: np.ndarray) -> np.ndarray:
 
 
 def dft_unmix(fib: np.ndarray, d: np.ndarray) -> np.ndarray:
-    """D F^* applied along the first axis of the sampled fibres (Alg. 6, line 8)."""
+    """D F^* applied along the first axis of the sampled fibres (Alg. 6)."""
     return d[:, None] * np.fft.ifft(fib, axis=0, norm="ortho")
 
 

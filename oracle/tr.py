@@ -131,7 +131,7 @@ def subchain_unfold(cores: Sequence[np.ndarray], n: int) -> np.ndarray:
 # Gram tensors and the structured Gram (Alg. 2; Proposition subchain_gram)
 # ----------------------------------------------------------------------------
 def gram_Z(G: np.ndarray) -> np.ndarray:
-    """Z = sum_i G(i)^T o G(i)^T, shape (R_{n+1}, R_n, R_{n+1}, R_n) (Alg. 2, line 2)."""
+    """Z = sum_i G(i)^T o G(i)^T, shape (R_{n+1}, R_n, R_{n+1}, R_n) (Alg. 2)."""
     Rn, In, Rn1 = G.shape
     Z = np.zeros((Rn1, Rn, Rn1, Rn))
     for i in range(In):
@@ -147,7 +147,7 @@ def contract_2413(A: np.ndarray, B: np.ndarray) -> np.ndarray:
 
 
 def ring_H(cores: Sequence[np.ndarray], n: int) -> np.ndarray:
-    """H^{!=n} = Z_{n-1} x Z_{n-2} x .. x Z_1 x Z_N x .. x Z_{n+1} (Alg. 2, line 5),
+    """H^{!=n} = Z_{n-1} x Z_{n-2} x .. x Z_1 x Z_N x .. x Z_{n+1} (Alg. 2),
     each x being x_{2,4}^{1,3}; shape (R_n, R_{n+1}, R_n, R_{n+1})."""
     N = len(cores)
     order = [(n - 2 - k) % N for k in range(N - 1)]   # 0-based n-1, .., 1, N, .., n+1
@@ -174,7 +174,7 @@ def gram_explicit(cores: Sequence[np.ndarray], n: int) -> np.ndarray:
 
 
 def mttkrp(X: np.ndarray, cores: Sequence[np.ndarray], n: int) -> np.ndarray:
-    """P = X_[n] G^{!=n}_[2] (Eq. partial; Alg. 2 line 7)."""
+    """P = X_[n] G^{!=n}_[2] (Eq. partial; Alg. 2)."""
     return unfold_cyclic(X, n) @ subchain_unfold(cores, n)
 
 
@@ -182,7 +182,7 @@ def mttkrp(X: np.ndarray, cores: Sequence[np.ndarray], n: int) -> np.ndarray:
 # Solve and error
 # ----------------------------------------------------------------------------
 def solve_pinv(P: np.ndarray, Q: np.ndarray) -> np.ndarray:
-    """G_{n(2)} = P Q^dagger with the symmetric pseudo-inverse (Alg. 4, line 17);
+    """G_{n(2)} = P Q^dagger with the symmetric pseudo-inverse (Alg. 4);
     default cut-off max(dim) * eps relative to the largest eigenvalue."""
     return P @ np.linalg.pinv(Q, hermitian=True)
 

@@ -280,7 +280,7 @@ str_status check_status(str_ctx* c, cudaStream_t s, bool* failed) {
 // ---------------------------------------------------------------------------
 
 // ring product W = E_{k_0} E_{k_1} ... E_{k_{N-2}} (cyclic order n+1..n-1), scattered into
-// Qout = base + (H^{!=n})_<2>  (Alg. 4 lines 8, 16; Prop. subchain_gram)
+// Qout = base + (H^{!=n})_<2>  (Alg. 4; Prop. subchain_gram)
 str_status ring_Q(str_ctx* c, int n, const double* ENew, const double* base, double* Qout,
                   cudaStream_t s) {
   const int N = c->N;
@@ -1028,7 +1028,7 @@ double sketch_wscale(const str_ctx* c, int n, const int64_t* dims) {
   return J / (double)c->opt.m;
 }
 
-// rSTR initialisation stage (Algs. 7-9, lines 2-19): draws at tau = 0, sketched P_n, Q_n
+// rSTR initialisation stage (Algs. 7-9): draws at tau = 0, sketched P_n, Q_n
 str_status rstr_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
   c->qsplit_of = nullptr;
   const int N = c->N;
@@ -1098,7 +1098,7 @@ str_status rstr_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
   return STR_OK;
 }
 
-// exact initialisation (Alg. 4 lines 2-6): P_n = X0_[n] G^{!=n}_[2], Q_n = ring with Z_N of G_N^init
+// exact initialisation (Alg. 4): P_n = X0_[n] G^{!=n}_[2], Q_n = ring with Z_N of G_N^init
 str_status str_init_state(str_ctx* c, const SlabView& v, cudaStream_t s) {
   c->qsplit_of = nullptr;
   const int N = c->N;
@@ -1147,7 +1147,7 @@ str_status precheck(str_ctx* c, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// STR step (Alg. 4 lines 8-19), with sweeps
+// STR step (Alg. 4), with sweeps
 // ---------------------------------------------------------------------------
 str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
   const int N = c->N;
@@ -1265,7 +1265,7 @@ str_status str_step(str_ctx* c, const SlabView& v, cudaStream_t s) {
   return STR_OK;
 }
 
-// append the step's new temporal rows after the committed ones (Alg. 4 line 10)
+// append the step's new temporal rows after the committed ones (Alg. 4)
 str_status append_rows(str_ctx* c, int64_t tn, cudaStream_t s) {
   const int RRN = c->RR(c->N - 1);
   STR_CUDA_TRY(cudaMemcpyAsync(c->GT64 + c->t_rows * RRN, c->gnew64.p, (size_t)tn * RRN * 8, cudaMemcpyDeviceToDevice, s));

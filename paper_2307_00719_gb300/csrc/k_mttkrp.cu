@@ -1,8 +1,8 @@
 // Slab MTTKRP with the TR subchain generated on the fly (never materialised).
 //
-//   P_n increment = X^new_[n] (G^{!=n}_new)_[2]            (Eq. partial, Alg. 4 line 15)
-//   temporal      = X^new_[N] G^{!=N}_[2]                   (Alg. 4 line 9)
-//   sampled       = X_S[n] diag(w) G^{!=n}_S[2]             (Alg. 3, Alg. 5 lines 15-16)
+//   P_n increment = X^new_[n] (G^{!=n}_new)_[2]            (Eq. partial, Alg. 4)
+//   temporal      = X^new_[N] G^{!=N}_[2]                   (Alg. 4)
+//   sampled       = X_S[n] diag(w) G^{!=n}_S[2]             (Alg. 3, Alg. 5)
 //
 // Each CTA owns BM rows of mode n and a contiguous range of fibres (split-K).
 // Per chunk of BK fibres it (1) decodes the fibre multi-indices, (2) forms the

@@ -1,6 +1,6 @@
 // Sketch kernels for rSTR: Philox row draws (Eq. sampDS; Lemma lev_est),
 // random sign flips and unitary DFT mixing (Definition of the KSRFT), the
-// weighted Gram of the sampled subchain (Alg. 5 line 16), and small utilities.
+// weighted Gram of the sampled subchain (Alg. 5), and small utilities.
 #include <algorithm>
 #include <map>
 #include <mutex>

@@ -1,9 +1,9 @@
 // FP64 kernels for the structured Gram and the small normal equations.
 //
 //   core Gram        M = G_{(2)}^T G_{(2)},   transfer form E = sum_i G(i) (x) G(i)
-//                    (the Gram tensor Z of Alg. 2 line 2, with its indices permuted)
+//                    (the Gram tensor Z of Alg. 2, with its indices permuted)
 //   ring             W = E_{n+1} E_{n+2} ... E_{n-1}  gives  (H^{!=n})_<2>   (Prop. subchain_gram)
-//   solve            G_{n(2)} = P_n Q_n^{-1} (Alg. 4 line 17): FP64 LDL^T + substitution, or
+//   solve            G_{n(2)} = P_n Q_n^{-1} (Alg. 4): FP64 LDL^T + substitution, or
 //                    (FP32 path) Q_n^{-1} from an FP32 symmetric sweep + FP64-residual refinement
 //   leverage         l_i = g_i M^{-1} g_i^T with M = G_{(2)}^T G_{(2)} = L D L^T (Lemma lev_est)
 #include <algorithm>
