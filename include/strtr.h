@@ -44,7 +44,7 @@ typedef enum {
   STR_ERR_INVALID_ARG = 1,  /* NULL pointer, bad enum, negative size */
   STR_ERR_SHAPE = 2,        /* order, dims or ranks outside the supported range */
   STR_ERR_DTYPE = 3,        /* unsupported element type for this call */
-  STR_ERR_SINGULAR = 4,     /* a normal-equation matrix had a non-positive Cholesky pivot */
+  STR_ERR_SINGULAR = 4,     /* a normal-equation matrix had a pivot too small to factor or invert */
   STR_ERR_NONFINITE = 5,    /* NaN/Inf found in a slab (only when check_finite is on) */
   STR_ERR_CAPACITY = 6,     /* the temporal core would exceed t_capacity rows */
   STR_ERR_OOM = 7,          /* device allocation failed */
@@ -207,7 +207,7 @@ enum {
   STR_K_MTTKRP = 0,   /* slab MTTKRP: tensor-core stage 1, or the SIMT kernel (sampled, FP64) */
   STR_K_REDUCE = 1,   /* fixed-order split reduction into P_n */
   STR_K_GRAM = 2,     /* core Gram and ring contraction */
-  STR_K_FACTOR = 3,   /* Cholesky factorisation */
+  STR_K_FACTOR = 3,   /* factorisation or inverse of Q_n (with the fused ring product) */
   STR_K_SOLVE = 4,    /* triangular row solves, leverage scores */
   STR_K_SKETCH = 5,   /* draws, sign flips, weighted sampled Gram */
   STR_K_DFT = 6,      /* KSRFT mixing / unmixing */
