@@ -98,6 +98,12 @@ def test_tensor_core_path_order5_segments():
     _run((12, 10, 9, 7), 14, (5, 5, 5, 5, 5), 6, 4, compute="f32", slab="f32", sweeps=2, seed=12, tol=1e-5)
 
 
+@pytest.mark.parametrize("compute,slab,tol", [("f64", "f64", 1e-10), ("f32", "f32", 1e-5)])
+def test_tensor_train_boundary_ranks(compute, slab, tol):
+    """TT specialisation (R_1 = R_{N+1} = 1): the ring closes through rank 1."""
+    _run((16, 12, 8), 18, (1, 3, 2, 3), 6, 4, compute=compute, slab=slab, sweeps=2, seed=13, tol=tol)
+
+
 def test_host_slab_matches_device_slab():
     import torch
     p = lib()

@@ -42,6 +42,22 @@ def test_exact_recovery_fixed_point():
     assert tr.fit_error(X, st.cores) <= 1e-12
 
 
+def test_exact_recovery_tensor_train():
+    """TT format (R_1 = R_{N+1} = 1, Sec. 2): the TR definitions reduce to the
+    train, TR(G)(i) = G_1(i_1) .. G_N(i_N) as a 1 x 1 product, and noise-free
+    data with the true cores as init is again a fixed point of every update."""
+    dims, T, ranks = (6, 5, 4), 18, (1, 3, 2, 3)
+    G, X = _problem(dims, T, ranks, 4)
+    i = (2, 4, 1, 7)
+    prod = G[0][:, i[0], :] @ G[1][:, i[1], :] @ G[2][:, i[2], :] @ G[3][:, i[3], :]
+    assert prod.shape == (1, 1) and abs(X[i] - prod[0, 0]) <= 1e-12 * max(1.0, abs(prod[0, 0]))
+    st = stream.str_init(X[..., :6], [G[0], G[1], G[2], G[3][:, :6, :]])
+    for t0 in range(6, 18, 4):
+        stream.str_update(st, X[..., t0:t0 + 4])
+    for k in range(4):
+        assert np.linalg.norm(st.cores[k] - G[k]) <= 1e-9 * np.linalg.norm(G[k])
+
+
 def test_streamed_pq_equal_batch_with_frozen_cores():
     """Eq. partial: with the cores frozen, P_n and Q_n accumulated slab by slab
     equal X_[n] G^{!=n}_[2] and its Gram on the concatenated tensor."""
