@@ -9,8 +9,11 @@ Workload (one "step" = one STR update, every row of the hot path):
 
 Printed as one JSON line by rank 0.  `--impl reference` times the FP64 CPU
 oracle on the same workload (a bounded sample per step) instead.
-Secondary rows (same line): the plain FP64 GPU arm of the same workload, and
-rSTR-U/L/K updates on a 512x512xT BF16 workload (ranks 10, sketch size 2000).
+Secondary rows (same line): the plain FP64 GPU arm of the same workload,
+rSTR-U/L/K updates on a 512x512xT BF16 workload (ranks 10, sketch size 2000),
+batched updates of 256 uneven order-3 streams, the masked TR fit loss and its
+backward on a 32x32x32x32x100 FP32 tensor, and STR updates on a 60^5 stand-in
+of the paper's largest synthetic tensor (ranks 5, 5-slice slabs).
 """
 from __future__ import annotations
 
