@@ -67,6 +67,21 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(torch, value, world, device):
+    """The largest of every rank's value: the job ends when its slowest rank does."""
+    if world <= 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the max-over-ranks time."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------------------
 # workload construction (GPU)
 # ---------------------------------------------------------------------------
@@ -214,12 +229,8 @@ def main_ours(a):
     times, launches, _ = timed_updates(p, torch, ctx, lambda j: slab(X32, W2, j), a.steps, a.warmup,
                                        flush=flush)
     clk = clocks.stop()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * a.steps * E / (total_ms / 1e3)
+    total_ms = max_over_ranks(torch, sum(times), world, "cuda")
+    value = job_rate(a.steps * E, world, total_ms / 1e3)
     fit32 = ctx.fit_error(X32[..., :ctx.time_rows()])
     cores32 = ctx.cores()
     ctx.close()
@@ -285,9 +296,9 @@ def main_ours(a):
             ctx_e.update(host[(a.warmup + j) % nsl])
             ctx_e.core(1)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(torch, time.perf_counter() - t0, world, "cuda")
     ctx_e.close()
-    out["e2e"] = {"value": world * a.steps * E / e2e_s, "unit": "entries/s",
+    out["e2e"] = {"value": job_rate(a.steps * E, world, e2e_s), "unit": "entries/s",
                   "h2d_bytes_per_step": E * 4, "d2h_bytes_per_step": 4 + 64 * 64 * 8,
                   "note": "str_update with on_host=1 pinned slab (copy inside the call, status read) "
                           "+ str_get_core(1), wall clock"}
