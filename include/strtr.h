@@ -248,7 +248,14 @@ void str_destroy(str_ctx* ctx);
  *   tr_masked_loss_bwd writes grad_scale * dL/dG_n into grad_cores_dev[n]
  *   (device, core layout, same dtype): dL/dG_{n(2)} = -(M .* (X - TR(G)))_[n] G^{!=n}_[2]
  *   (with M == 1 this equals G_{n(2)} Q_n - P_n of Eq. partial).
- * Both recompute the subchains; nothing is stored between them.
+ * Both recompute the subchains; nothing is stored between them.  With the
+ * modes split into a prefix and a suffix such that K = R_1 R_{k+1} <= 64, one
+ * pass over X (and the mask) gives the loss and, for the backward, the sums of
+ * the masked residual against the suffix and prefix products, from which every
+ * core gradient follows as a small MTTKRP; otherwise the residual is formed
+ * in a scratch buffer first.  Results are reduced in a fixed order
+ * (deterministic for a given shape).  Scratch is library-owned (grow-only,
+ * shared by all calls of the process, serialised by a host lock).
  */
 str_status tr_masked_loss_fwd(int N, const int64_t* dims, const int* ranks, str_dtype dtype,
                               const void* const* cores_dev, const void* X_dev,
