@@ -95,6 +95,51 @@ def test_one_step_with_empty_history_is_an_als_sweep():
         np.testing.assert_allclose(st.cores[k], ref[k], rtol=1e-8, atol=1e-10)
 
 
+@pytest.mark.parametrize("sweeps", [2, 3])
+def test_sweeps_with_empty_history_are_als_sweeps(sweeps):
+    """Reading of "s sweeps per update" (P_old, Q_old frozen for the step; every
+    sweep recomputes G_N^new, then each P_n = P_n^old + increment with the
+    current cores): with P_old = Q_old = 0 and the whole tensor as the slab,
+    s sweeps of one STR step are s ALS sweeps (Alg. 1) in the order N, 1, ..,
+    N-1, each solve a plain lstsq of the explicit unfolded problem.  A sweep
+    that accumulated its increment on top of the previous sweep's P_n (instead
+    of the frozen P_n^old) would double-count the slab from the second sweep."""
+    dims, T, ranks = (4, 5, 3), 6, (2, 2, 3, 2)
+    G0 = synth.gaussian_cores(dims + (T,), ranks, 24)
+    X = synth.gaussian_tensor(dims + (T,), 25)
+    st = stream.State(cores=[g.copy() for g in G0[:3]] + [G0[3][:, :0, :]],
+                      P=[np.zeros((d, ranks[n] * ranks[(n + 1) % 4])) for n, d in enumerate(dims)],
+                      Q=[np.zeros((ranks[n] * ranks[(n + 1) % 4],) * 2) for n in range(3)])
+    stream.str_update(st, X, sweeps=sweeps)
+    ref = [g.copy() for g in G0]
+    for _ in range(sweeps):
+        for n in [4, 1, 2, 3]:
+            A = tr.subchain_unfold(ref, n)
+            sol = np.linalg.lstsq(A, tr.unfold_cyclic(X, n).T, rcond=None)[0].T
+            ref[n - 1] = tr.core_fold2(sol, ranks[n - 1], ranks[n % 4])
+    for k in range(4):
+        np.testing.assert_allclose(st.cores[k], ref[k], rtol=1e-8, atol=1e-10)
+    # P_n, Q_n after the step hold exactly one slab's worth (the last sweep's)
+    for n in range(1, 4):
+        before = _cores_before_mode(X, G0, ranks, sweeps, n)
+        np.testing.assert_allclose(st.P[n - 1], tr.mttkrp(X, before, n), rtol=1e-8, atol=1e-8)
+        np.testing.assert_allclose(st.Q[n - 1], tr.gram_explicit(before, n), rtol=1e-8, atol=1e-8)
+
+
+def _cores_before_mode(X, G0, ranks, sweeps, n):
+    """Cores as they stand when mode n is solved in the last of `sweeps` ALS
+    sweeps (order N, 1, .., N-1) from G0 with an empty temporal history."""
+    ref = [g.copy() for g in G0]
+    for sw in range(sweeps):
+        for k in [4, 1, 2, 3]:
+            if sw == sweeps - 1 and k == n:
+                return ref
+            A = tr.subchain_unfold(ref, k)
+            sol = np.linalg.lstsq(A, tr.unfold_cyclic(X, k).T, rcond=None)[0].T
+            ref[k - 1] = tr.core_fold2(sol, ranks[k - 1], ranks[k % 4])
+    return ref
+
+
 def test_sweeps_reduce_or_keep_error():
     dims, T, ranks = (8, 9), 40, (3, 3, 3)
     G, X = _problem(dims, T, ranks, 16, noise=1e-2)
@@ -217,10 +262,11 @@ def test_lemma_lev_est_inequality():
         assert np.all(q >= beta * pex * (1 - 1e-12))
 
 
-@pytest.mark.parametrize("sketch", ["uniform", "leverage"])
+@pytest.mark.parametrize("sketch", ["uniform", "leverage", "ksrft"])
 def test_rescaled_sketch_is_unbiased(sketch):
-    """E[sketched, rescaled Delta P_n] = exact Delta P_n (Eq. sampDS): the mean over
-    many independent draws lies within 4 standard errors."""
+    """E[sketched, rescaled Delta P_n] = exact Delta P_n (Eq. sampDS; for KSRFT the
+    scale of the operator in Definition SRFT, with fresh signs per draw): the
+    mean over many independent draws lies within 4.5 standard errors."""
     dims, ranks = (4, 3, 3), (2, 2, 2)
     G = synth.gaussian_cores(dims, ranks, 16)
     X = synth.gaussian_tensor(dims, 17)
@@ -234,14 +280,65 @@ def test_rescaled_sketch_is_unbiased(sketch):
         for k in range(1, 4):
             st.seed = seed
             st.idxs[:, k - 1] = stream._draw(st, k, dims[k - 1], 0)
-        Gs = stream.sampled_subchain(G, st.idxs, n)
-        Xs = stream.sampled_fibres(X, st.idxs, n)
+        if sketch == "ksrft":
+            D = [philox.signs(seed, d, k + 1, 0) for k, d in enumerate(dims)]
+            Gs = stream.sampled_subchain([stream.dft_mix_core(g, D[k]) for k, g in enumerate(G)], st.idxs, n)
+            Xs = stream.dft_unmix(stream.sampled_fibres(stream.dft_mix(X, D), st.idxs, n), D[n - 1])
+        else:
+            Gs = stream.sampled_subchain(G, st.idxs, n)
+            Xs = stream.sampled_fibres(X, st.idxs, n)
         dP, _ = stream._pq_increment(Xs, Gs, stream.sketch_weights(st, n, dims))
         samples.append(dP)
     S = np.array(samples)
     mean, se = S.mean(0), S.std(0, ddof=1) / np.sqrt(reps)
     exact = tr.mttkrp(X, G, n)
     assert np.all(np.abs(mean - exact) <= 4.5 * se + 1e-12)
+
+
+def _cartesian_rows(dims):
+    """Every multi-index (i_1, .., i_N) once, i_1 fastest: m = prod(dims) rows."""
+    N = len(dims)
+    out = np.empty((int(np.prod(dims)), N), dtype=np.int64)
+    for s in range(out.shape[0]):
+        r = s
+        for k in range(N):
+            out[s, k] = r % dims[k]
+            r //= dims[k]
+    return out
+
+
+@pytest.mark.parametrize("sketch", ["uniform", "ksrft"])
+def test_rstr_with_full_index_set_equals_str(sketch, monkeypatch):
+    """Full-index-set special case of the sketched updates (Alg. 5 with the
+    schedules of Algs. 7 and 9): if every draw returns the whole Cartesian index
+    set (m = I_1 .. I_{N-1} t_new rows, so each subchain row of mode n appears
+    I_n times and the rescale J_n / m is 1 / I_n), the sketched P_n, Q_n
+    increments and the sketched temporal normal equations equal STR's exactly
+    (for KSRFT because (x)_j F_j D_j is unitary), so rSTR-U and rSTR-K reproduce
+    STR (Alg. 4), step after step, to rounding."""
+    dims, T, ranks, t_new = (3, 4), 10, (2, 3, 2), 2
+    G, X = _problem(dims, T, ranks, 26, noise=0.05)
+    full = _cartesian_rows(dims + (t_new,))
+
+    def draw_all(st, k, size, tau):
+        assert size == full[:, k - 1].max() + 1
+        return full[:, k - 1].copy()
+
+    monkeypatch.setattr(stream, "_draw", draw_all)
+    init = [G[0], G[1], G[2][:, :t_new, :]]
+    rs = stream.rstr_init(X[..., :t_new], init, sketch, m=full.shape[0], seed=5)
+    ex = stream.str_init(X[..., :t_new], init)
+    for n in range(1, 3):
+        np.testing.assert_allclose(rs.P[n - 1], ex.P[n - 1], rtol=1e-11, atol=1e-11)
+        np.testing.assert_allclose(rs.Q[n - 1], ex.Q[n - 1], rtol=1e-11, atol=1e-11)
+    for t0 in range(t_new, T, t_new):
+        stream.rstr_update(rs, X[..., t0:t0 + t_new])
+        stream.str_update(ex, X[..., t0:t0 + t_new])
+        for k in range(3):
+            assert np.linalg.norm(rs.cores[k] - ex.cores[k]) <= 1e-10 * np.linalg.norm(ex.cores[k])
+    for n in range(1, 3):
+        np.testing.assert_allclose(rs.P[n - 1], ex.P[n - 1], rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(rs.Q[n - 1], ex.Q[n - 1], rtol=1e-10, atol=1e-10)
 
 
 @pytest.mark.parametrize("sketch", ["uniform", "leverage", "ksrft"])
