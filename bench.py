@@ -34,9 +34,9 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "STR/rSTR tensor entries/s per update, % roofline, rel. fit err vs FP64"
-# DRAM bytes (read + write) of one stage-1 launch on the order-4 workload, from the
-# ncu capture summarised in profiles/ncu_str_order4_update_kernels.md; set to None
-# whenever the stage-1 kernel changes until it is captured again
+# DRAM bytes (read + write) of one stage-1 launch on the order-4 workload, from an
+# ncu capture of this bench (dram__bytes_read.sum + dram__bytes_write.sum); set to
+# None whenever the stage-1 kernel changes until it is captured again
 STAGE1_DRAM_BYTES = 10549760
 W2 = synth.WORKLOADS["order4"]
 W3 = synth.WORKLOADS["rand3"]
@@ -253,7 +253,7 @@ def main_ours(a):
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_hbm, "unit": "GB/s",
                 "frac": round(achieved / peak_hbm, 4), "traffic": STAGE1_DRAM_BYTES,
                 "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch, ncu --set full "
-                                "on this workload (profiles/ncu_str_order4_update_kernels.md)",
+                                "on this workload",
                 "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured",
                 "algorithmic_per_launch": {"bytes": slab_bytes, "flop": 2.0 * E * RRk,
                                            "note": "one read of the 64^3 x 10 FP32 slab; 2 E R_1 R_2 flop"},

@@ -255,7 +255,11 @@ void str_destroy(str_ctx* ctx);
  * core gradient follows as a small MTTKRP; otherwise the residual is formed
  * in a scratch buffer first.  Results are reduced in a fixed order
  * (deterministic for a given shape).  Scratch is library-owned (grow-only,
- * shared by all calls of the process, serialised by a host lock).
+ * shared by all calls of the process): a host lock serialises the enqueueing,
+ * and each call's stream first waits for the previous call's last use of the
+ * scratch (a library event), so calls issued on different streams do not
+ * overlap on the GPU.  Under stream capture that wait is not recorded and the
+ * caller must order captured loss calls against others itself.
  */
 str_status tr_masked_loss_fwd(int N, const int64_t* dims, const int* ranks, str_dtype dtype,
                               const void* const* cores_dev, const void* X_dev,
@@ -269,13 +273,16 @@ str_status tr_masked_loss_bwd(int N, const int64_t* dims, const int* ranks, str_
  * tr_masked_loss_fwd_noalloc -- the paper has no counterpart; this is a service
  * entry point of the library.  Same arguments and result as
  * tr_masked_loss_fwd, but it allocates no device memory, for callers that
- * cannot call cudaMalloc: code running while a CUDA graph is captured, code
- * whose framework allocator owns all device memory, and latency-critical
- * loops that cannot take cudaMalloc's device synchronisation.
+ * cannot call cudaMalloc: code whose framework allocator owns all device
+ * memory (a raw cudaMalloc bypasses its budget and can fail once it has taken
+ * the free memory), and latency-critical loops that cannot take cudaMalloc's
+ * device synchronisation.
  * Its scratch is one fixed 32 MiB array in device global memory (held by every
  * GPU that loads the library until the process exits).  A problem whose
- * scratch does not fit returns STR_ERR_SHAPE before launching anything
- * (str_last_error() gives the size).  All calls share that array: calls that
+ * scratch does not fit, or whose 64 x 64 output blocks exceed the grid limits,
+ * returns STR_ERR_SHAPE before launching anything (str_last_error() says why).
+ * The modes are split into a prefix 1..N/2 and a suffix; the value agrees with
+ * tr_masked_loss_fwd (which may split elsewhere) to rounding.  All calls share that array: calls that
  * overlap on the GPU (other streams or host threads) race.  The first call on
  * each device looks up the array's address with that device current; make it
  * before any stream capture.

@@ -6,7 +6,7 @@ Test infrastructure only: see the package docstring.
 Every step uses the plain primitives of ``oracle.tr``: the subchain is
 materialised, the Gram matrix Q_n is formed explicitly from it, and each
 core solve uses the symmetric pseudo-inverse.  Readings of points the paper
-leaves open are marked "Reading:" (they are listed in the design notes).
+leaves open are marked "Reading:".
 """
 from __future__ import annotations
 

@@ -1482,6 +1482,31 @@ struct LossWs {
   void* p = nullptr;
   size_t cap = 0;
 } g_loss_ws[4];
+// recorded on a loss call's stream after its last use of g_loss_ws; the next
+// loss call's stream waits on it first, so calls on different streams run
+// their workspace use one after another on the GPU
+cudaEvent_t g_ws_done = nullptr;
+bool g_ws_recorded = false;
+
+// Orders stream s after the previous loss call's use of the workspace (not
+// inside a stream capture, where a wait on an event recorded outside it is not
+// allowed; the caller orders captured work itself).
+str_status ws_acquire(cudaStream_t s, bool* capturing) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  STR_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+  *capturing = cs != cudaStreamCaptureStatusNone;
+  if (!g_ws_done) STR_CUDA_TRY(cudaEventCreateWithFlags(&g_ws_done, cudaEventDisableTiming));
+  if (g_ws_recorded && !*capturing) STR_CUDA_TRY(wait_event(s, g_ws_done));
+  else str_mark_cross_wait(s);   // the caller may have ordered s after other streams
+  return STR_OK;
+}
+
+str_status ws_release(cudaStream_t s, bool capturing) {
+  if (capturing) return STR_OK;
+  STR_CUDA_TRY(cudaEventRecord(g_ws_done, s));
+  g_ws_recorded = true;
+  return STR_OK;
+}
 
 str_status ws_grow(int i, size_t bytes) {
   if (bytes <= g_loss_ws[i].cap) return STR_OK;
@@ -2332,6 +2357,13 @@ static str_status loss_bwd_fused(int N, const int64_t* dims, const str_ctx& t, c
   return STR_OK;
 }
 
+static str_status loss_fwd_body(int N, const int64_t* dims, const int* ranks, str_dtype dtype, const str_ctx& t,
+                                const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
+                                double* loss_dev, cudaStream_t s);
+static str_status loss_bwd_body(int N, const int64_t* dims, const int* ranks, str_dtype dtype, const str_ctx& t,
+                                const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
+                                double grad_scale, void* const* grad_cores_dev, cudaStream_t s);
+
 str_status tr_masked_loss_fwd(int N, const int64_t* dims, const int* ranks, str_dtype dtype,
                               const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
                               double* loss_dev, void* stream) {
@@ -2340,7 +2372,16 @@ str_status tr_masked_loss_fwd(int N, const int64_t* dims, const int* ranks, str_
   if (!loss_dev) return STR_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_ws_mu);
   cudaStream_t s = (cudaStream_t)stream;
-  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
+  bool capturing = false;
+  TRY(ws_acquire(s, &capturing));
+  const str_status st = loss_fwd_body(N, dims, ranks, dtype, t, cores_dev, X_dev, mask_bits, loss_dev, s);
+  const str_status rs = ws_release(s, capturing);
+  return st != STR_OK ? st : rs;
+}
+
+static str_status loss_fwd_body(int N, const int64_t* dims, const int* ranks, str_dtype dtype, const str_ctx& t,
+                                const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
+                                double* loss_dev, cudaStream_t s) {
   const int ks = loss_split(N, dims, t.R);
   const int kp = ks > 0 ? ks : N / 2;
   int64_t rows = 1, cols = 1;
@@ -2384,7 +2425,17 @@ str_status tr_masked_loss_bwd(int N, const int64_t* dims, const int* ranks, str_
   for (int k = 0; k < N; ++k) if (!grad_cores_dev[k]) return STR_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_ws_mu);
   cudaStream_t s = (cudaStream_t)stream;
-  str_mark_cross_wait(s);   // the caller may have ordered s after other streams
+  bool capturing = false;
+  TRY(ws_acquire(s, &capturing));
+  const str_status st = loss_bwd_body(N, dims, ranks, dtype, t, cores_dev, X_dev, mask_bits, grad_scale,
+                                      grad_cores_dev, s);
+  const str_status rs = ws_release(s, capturing);
+  return st != STR_OK ? st : rs;
+}
+
+static str_status loss_bwd_body(int N, const int64_t* dims, const int* ranks, str_dtype dtype, const str_ctx& t,
+                                const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
+                                double grad_scale, void* const* grad_cores_dev, cudaStream_t s) {
   const int ks = loss_split(N, dims, t.R);
   const int kp = ks > 0 ? ks : N / 2;
   int64_t rows = 1, cols = 1, count = 1;

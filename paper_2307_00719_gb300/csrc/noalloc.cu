@@ -1,9 +1,10 @@
 // Masked-loss forward that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured, code inside a framework whose caching allocator owns all
-// device memory (a raw cudaMalloc would bypass its budget), and latency-bound
-// loops that cannot afford cudaMalloc's implicit device synchronisation.
+// Some callers cannot call cudaMalloc: code inside a framework whose caching
+// allocator owns all device memory (a raw cudaMalloc would bypass its budget
+// and can fail once that allocator has taken the free memory), and
+// latency-bound loops that cannot afford cudaMalloc's implicit device
+// synchronisation.
 // For them, tr_masked_loss_fwd_noalloc computes the same value as
 // tr_masked_loss_fwd but keeps its scratch (the prefix/suffix product tables
 // and the per-block partial sums) in one fixed array in device global memory,
@@ -77,13 +78,24 @@ extern "C" str_status tr_masked_loss_fwd_noalloc(int N, const int64_t* dims, con
   R[N] = ranks[0];
   const int compute = dtype == STR_F64 ? 2 : 1;
   const size_t es = dtype == STR_F64 ? 8 : 4;
-  // same split of the modes as tr_masked_loss_fwd: prefix 1..kp, suffix kp+1..N
+  // a fixed split of the modes: prefix 1..kp, suffix kp+1..N with kp = N/2
+  // (tr_masked_loss_fwd may pick another split; the loss agrees to rounding)
   const int kp = N / 2;
   int64_t rows = 1, cols = 1;
   for (int k = 0; k < kp; ++k) rows *= dims[k];
   for (int k = kp; k < N; ++k) cols *= dims[k];
   const int K = R[0] * R[kp];
-  const int64_t nb = recon_blocks(rows, cols);
+  // 64 x 64 output blocks (grid x over rows, y over columns), counted in 64 bits
+  // and bounded before any byte size is formed from them
+  const int64_t gx = (rows + 63) / 64, gy = (cols + 63) / 64;
+  const int64_t nb_max = (int64_t)(STR_NOALLOC_SCRATCH_BYTES / (2 * sizeof(double)));
+  if (gx > 2147483647LL || gy > 65535 || gx > nb_max / gy) {
+    str_set_last_error_text(("tr_masked_loss_fwd_noalloc: " + std::to_string(gx) + " x " + std::to_string(gy) +
+                             " blocks of partial sums exceed the fixed scratch array or the grid limits")
+                                .c_str());
+    return STR_ERR_SHAPE;
+  }
+  const int64_t nb = gx * gy;
   const size_t off_suffix = round256((size_t)rows * K * es);
   const size_t off_blocks = off_suffix + round256((size_t)cols * K * es);
   const size_t off_sums = off_blocks + round256((size_t)nb * 2 * sizeof(double));

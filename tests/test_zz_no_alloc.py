@@ -1,11 +1,12 @@
 """The masked-loss forward that allocates no device memory.
 
-Some callers cannot call cudaMalloc (code running under CUDA graph capture,
-code whose framework allocator owns the device memory, loops that cannot take
-cudaMalloc's synchronisation).  tr_masked_loss_fwd_noalloc serves them from a
-fixed 32 MiB device array; here it is called through the C ABI and must give
-the same loss as tr_masked_loss_fwd, on two calls in a row, and must reject a
-problem whose scratch does not fit.  This file is collected last on purpose.
+Some callers cannot call cudaMalloc (code whose framework allocator owns the
+device memory, loops that cannot take cudaMalloc's synchronisation).
+tr_masked_loss_fwd_noalloc serves them from a fixed 32 MiB device array; here
+it is called through the C ABI and must give the same loss as
+tr_masked_loss_fwd on two calls in a row, leave the device's free memory
+unchanged on the second call, and reject a problem whose scratch does not fit.
+This file is collected last on purpose.
 """
 from ctypes import c_int, c_int64, c_void_p
 
@@ -52,12 +53,17 @@ def test_noalloc_loss_matches_allocating_entry_point(dtype_name, tol):
     ref = torch.zeros((), dtype=torch.float64, device="cuda")
     assert L.tr_masked_loss_fwd(N, d, r, code, ptrs, c_void_p(Xd.data_ptr()), c_void_p(bits.data_ptr()),
                                 c_void_p(ref.data_ptr()), stream) == 0
-    for _ in range(2):
-        out = torch.full((), -1.0, dtype=torch.float64, device="cuda")
+    outs = [torch.full((), -1.0, dtype=torch.float64, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    free = []
+    for out in outs:
         assert L.tr_masked_loss_fwd_noalloc(N, d, r, code, ptrs, c_void_p(Xd.data_ptr()),
                                             c_void_p(bits.data_ptr()), c_void_p(out.data_ptr()), stream) == 0
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         assert abs(out.item() - ref.item()) <= tol * abs(ref.item())
+    # the first call may load the array's module and kernels; the second allocates nothing
+    assert free[1] == free[0]
 
 
 def test_noalloc_rejects_scratch_beyond_its_limit():
