@@ -3,17 +3,23 @@
 
 Workload (one "step" = one STR update, every row of the hot path):
   order-4 tensor 64x64x64xT, T = 400, TR-ranks all 8, Gaussian cores, noise at
-  SNR 30 dB, initial decomposition on 40 slices, then updates of 10 slices,
-  5 sweeps per update, FP32 slab and FP32 slab-side arithmetic (FP64 Gram,
-  P_n/Q_n and solves).  Inputs are synthetic and already resident in HBM.
+  SNR 30 dB, initial cores = true cores + 0.05 N(0,1) on 40 slices, then
+  updates of 10 slices, 5 sweeps per update, FP32 slab and FP32 slab-side
+  arithmetic (FP64 Gram, P_n/Q_n state).  Inputs are synthetic, built on the
+  host in FP64 (the same bytes feed the CPU oracle) and already resident in HBM
+  when the timed region starts.
 
 Printed as one JSON line by rank 0.  `--impl reference` times the FP64 CPU
-oracle on the same workload (a bounded sample per step) instead.
+oracle on the same workload and the same input bytes (one update per step).
 Secondary rows (same line): the plain FP64 GPU arm of the same workload,
 rSTR-U/L/K updates on a 512x512xT BF16 workload (ranks 10, sketch size 2000),
 batched updates of 256 uneven order-3 streams, the masked TR fit loss and its
 backward on a 32x32x32x32x100 FP32 tensor, and STR updates on a 60^5 stand-in
-of the paper's largest synthetic tensor (ranks 5, 5-slice slabs).
+of the paper's largest synthetic tensor (ranks 5, 5-slice slabs).  Every row
+states its step roofline (t_bound / t_update, t_bound = max(F_alg / pipe
+peak, B_alg / HBM peak) with the pipe peaks measured in this run) and, at
+N = 1 on rank 0, its relative fit error against the FP64 oracle run on the
+same bytes for the first updates (the CPU-oracle leg).
 """
 from __future__ import annotations
 
@@ -41,23 +47,28 @@ STAGE1_DRAM_BYTES = 10549760
 W2 = synth.WORKLOADS["order4"]
 W3 = synth.WORKLOADS["rand3"]
 WORKLOAD_DESC = ("order4: 64x64x64xT, T=400, TR-ranks all 8, Gaussian cores, SNR 30 dB, "
-                 "init on 40 slices, updates of 10 slices, 5 sweeps, FP32 slab")
+                 "init = true cores + 0.05 N(0,1) on 40 slices, updates of 10 slices, 5 sweeps, FP32 slab")
 FLUSH_BYTES = 256 << 20     # > 129 MB L2
+INIT_PERTURB = 0.05
+CHECK_UPDATES = 3           # updates compared with the oracle (order-4 rows)
+LOSS_NOISE = 1e-2
+BATCH_NOISE = 1e-2
 
 
-def args_parse():
+def args_parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-rstr", action="store_true", help="skip the rSTR rows")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU arm")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-streams row")
     ap.add_argument("--no-loss", action="store_true", help="skip the masked-loss row")
     ap.add_argument("--no-large", action="store_true", help="skip the 60^5 stand-in row")
-    return ap.parse_args()
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -82,33 +93,60 @@ def job_rate(units_per_rank, world, seconds):
     return world * units_per_rank / seconds
 
 
+def step_roofline(t_ms, flop, pipe_peak_tflops, nbytes, hbm_gbs, pipe):
+    """Step roofline of one update: t_bound = max(F_alg / pipe peak, B_alg / HBM
+    peak); frac_step = t_bound / t_update."""
+    t_f = flop / (pipe_peak_tflops * 1e12) if pipe_peak_tflops else 0.0
+    t_b = nbytes / (hbm_gbs * 1e9)
+    t_bound = max(t_f, t_b)
+    return {"t_bound_us": round(t_bound * 1e6, 3), "t_update_us": round(t_ms * 1e3, 2),
+            "frac_step": round(t_bound / (t_ms / 1e3), 5), "bound": pipe if t_f >= t_b else "hbm",
+            "flop_alg": flop, "bytes_alg": nbytes, "pipe_peak_tflops": pipe_peak_tflops, "hbm_gbs": hbm_gbs}
+
+
 # ---------------------------------------------------------------------------
-# workload construction (GPU)
+# inputs: built on the host in FP64 (the same bytes feed both arms and the oracle)
 # ---------------------------------------------------------------------------
-def build_tensor(p, torch, w, seed):
-    """X = TR(G_true) + noise, built on the GPU with the library's reconstruct."""
+def host_tr_tensor(G, t0=0, t1=None):
+    """TR(G) over temporal rows [t0, t1) as a float64 array X[i_1..i_N]: the
+    trace formula of the TR format, X(i) = Trace(G_1(i_1)..G_N(i_N)), for all
+    entries at once (the spatial slices multiplied left to right, then the
+    trace against the temporal core's slices)."""
+    T = G[0]
+    for g in G[1:-1]:
+        T = np.tensordot(T, g, axes=([T.ndim - 1], [0]))       # (R_1, I_1, .., I_k, R_{k+1})
+    GN = G[-1][:, t0:t1, :]                                     # (R_N, t, R_1)
+    return np.tensordot(T, GN, axes=([0, T.ndim - 1], [2, 0]))  # sum over r_1, r_N
+
+
+def host_workload(w, seed):
+    """True cores, X = TR(G) + noise (relative Frobenius level w.noise) over all
+    T slices, and the initial cores (true cores + 0.05 N(0,1), temporal core cut
+    to t_init rows)."""
     G = synth.gaussian_cores(tuple(w.dims) + (w.T,), w.ranks, seed)
-    truth = p.str_init_cores(G, X0=None, t_capacity=w.T)
-    X = truth.reconstruct(0, w.T)                          # FP64, i_1 fastest
-    truth.close()
+    X = host_tr_tensor(G)
     if w.noise > 0:
-        g = torch.Generator(device="cuda").manual_seed(seed + 100)
-        E = torch.randn(X.shape[::-1], generator=g, device="cuda", dtype=torch.float64)
-        E = E.permute(list(range(E.dim() - 1, -1, -1)))
-        X = X + (w.noise * torch.linalg.vector_norm(X) / torch.linalg.vector_norm(E)) * E
-    return G, p.paper_layout(X)
-
-
-def init_cores(p, torch, w, G, X, seed, iters=20):
-    """Initial decomposition of the first t_init slices by TR-ALS-NE on the GPU,
-    started from the true cores perturbed by 0.3 N(0,1)."""
+        X = synth.add_noise(X, synth.gaussian_tensor(X.shape, seed + 100), w.noise)
     rng = np.random.default_rng(seed + 200)
-    guess = [g + 0.3 * rng.standard_normal(g.shape) for g in G]
-    guess[-1] = guess[-1][:, :w.t_init, :]
-    ctx = p.str_init(p.paper_layout(X[..., :w.t_init]), w.ranks, guess, init_max_it=iters)
-    cores = ctx.cores()
-    ctx.close()
-    return cores
+    init = [g + INIT_PERTURB * rng.standard_normal(g.shape) for g in G]
+    init[-1] = init[-1][:, :w.t_init, :]
+    return G, X, init
+
+
+def to_device(torch, X, dtype=None):
+    """numpy X[i_1..i_N] -> CUDA tensor indexed the same way with i_1 fastest."""
+    rev = list(range(X.ndim - 1, -1, -1))
+    t = torch.from_numpy(np.ascontiguousarray(X.transpose(rev)))
+    t = t.to("cuda", dtype) if dtype is not None else t.to("cuda")
+    return t.permute(rev)
+
+
+def bf16_device(torch, X):
+    """BF16 copy of X whose values are exactly synth.to_bf16_values(X)."""
+    rev = list(range(X.ndim - 1, -1, -1))
+    bits = synth.bf16_bits(np.ascontiguousarray(X.transpose(rev)))
+    t = torch.from_numpy(bits.view(np.int16)).to("cuda").view(torch.bfloat16)
+    return t.permute(rev)
 
 
 def slab(X, w, j, dtype=None):
@@ -163,6 +201,65 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# peaks: HBM and BF16 from the driver's measurement file (else the fallback),
+# TF32 tensor, FP32 and FP64 FMA pipes measured here with CUDA events
+# ---------------------------------------------------------------------------
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "of measured"
+    except Exception:
+        return fallback, "of fallback"
+
+
+def event_ms(torch, fn, reps):
+    """Best of `reps` CUDA-event timings of fn() on the current stream."""
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def measure_peaks(p, torch):
+    hbm, hbm_src = measured_peak("hbm_gbs", 6800.0)
+    bf16, bf16_src = measured_peak("bf16_tflops", 1900.0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # TF32: cuBLAS FP32 GEMM with TF32 tensor cores allowed, 8192^3
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    n = 8192
+    A = torch.randn(n, n, device="cuda")
+    B = torch.randn(n, n, device="cuda")
+    C = torch.empty(n, n, device="cuda")
+    for _ in range(3):
+        torch.matmul(A, B, out=C)
+    ms = event_ms(torch, lambda: [torch.matmul(A, B, out=C) for _ in range(5)], 3) / 5
+    tf32 = 2.0 * n ** 3 / (ms / 1e3) / 1e12
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del A, B, C
+    # FP32 / FP64 FMA pipes: the library's probe kernel, 8 blocks of 256 threads per SM
+    ctas = 8 * sms
+    rates = {}
+    for dt, iters in (("f32", 20000), ("f64", 400)):
+        out = torch.empty(ctas, dtype=torch.float32 if dt == "f32" else torch.float64, device="cuda")
+        flop = p.fma_probe(dt, ctas, iters, out)
+        ms = event_ms(torch, lambda: p.fma_probe(dt, ctas, iters, out), 3)
+        rates[dt] = flop / (ms / 1e3) / 1e12
+    torch.cuda.synchronize()
+    return {"hbm_gbs": hbm, "hbm_note": hbm_src, "bf16_tflops": bf16, "bf16_note": bf16_src,
+            "tf32_tflops": round(tf32, 1), "tf32_note": "measured here: torch.matmul FP32 8192^3 with TF32 allowed",
+            "fp32_fma_tflops": round(rates["f32"], 2), "fp64_fma_tflops": round(rates["f64"], 3),
+            "fma_note": f"measured here: str_fma_probe, {ctas} blocks x 256 threads, 8 FMA chains per thread",
+            "sms": sms}
+
+
+# ---------------------------------------------------------------------------
 # timed loops
 # ---------------------------------------------------------------------------
 def timed_updates(p, torch, ctx, slabs, steps, warmup, randomized=False, flush=None, profile=False):
@@ -199,6 +296,13 @@ def _timed_updates(p, torch, ctx, slabs, steps, warmup, randomized, flush, profi
     return times, launches, st
 
 
+def str_flop(dims, t_new, ranks, sweeps):
+    """F_alg of one STR update: per mode 2 E R_n R_{n+1} (the MTTKRP), every mode, every sweep."""
+    E = int(np.prod(dims)) * t_new
+    N = len(ranks)
+    return 2.0 * E * sum(ranks[n] * ranks[(n + 1) % N] for n in range(N)) * sweeps
+
+
 def main_ours(a):
     import torch
     import paper_2307_00719_gb300 as p
@@ -208,12 +312,15 @@ def main_ours(a):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     seed = W2.seed + 1000 * rank                       # independent replica per rank
-    G, X = build_tensor(p, torch, W2, seed)
-    cores0 = init_cores(p, torch, W2, G, X, seed)
-    X32 = p.paper_layout(X.float())
+    G, Xh, cores0 = host_workload(W2, seed)
+    X = to_device(torch, Xh)                           # FP64, i_1 fastest
+    X32 = to_device(torch, Xh, torch.float32)
+    peaks = measure_peaks(p, torch)
+    hbm = peaks["hbm_gbs"]
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     E = int(np.prod(W2.dims)) * W2.t_new
     cap = W2.t_init + (a.warmup + a.steps + 2) * W2.t_new
+    F2 = str_flop(W2.dims, W2.t_new, W2.ranks, W2.sweeps)
 
     def make(compute, xsrc, profile=0):
         return p.str_init_cores(cores0, X0=p.paper_layout(xsrc[..., :W2.t_init]), compute=compute,
@@ -231,8 +338,6 @@ def main_ours(a):
     clk = clocks.stop()
     total_ms = max_over_ranks(torch, sum(times), world, "cuda")
     value = job_rate(a.steps * E, world, total_ms / 1e3)
-    fit32 = ctx.fit_error(X32[..., :ctx.time_rows()])
-    cores32 = ctx.cores()
     ctx.close()
 
     # ---- profile pass: per-class kernel times (same steps, events per launch) ----
@@ -242,19 +347,18 @@ def main_ours(a):
     ctxp.close()
     k_ms, k_n = pst["class_ms"], pst["class_launches"]
     mt_avg_ms = k_ms["mttkrp"] / max(1, k_n["mttkrp"])
-    peak_hbm = measured_peak("hbm_gbs", 6685.5)
     slab_bytes = E * 4                                  # one read of the FP32 slab per launch
     achieved = slab_bytes / (mt_avg_ms / 1e3) / 1e9
-    sm_clock = (clk.get("sm_mhz") or 1900.0)
     tot = sum(k_ms.values())
     c_avg_ms = k_ms["contract"] / max(1, k_n["contract"])
     RRk = W2.ranks[0] * W2.ranks[1]
+    ms_step = total_ms / a.steps
     roofline = {"kernel": "stage1_ws_kernel (tcgen05 kind::tf32, 3-term split, TMA-fed, warp-specialised)",
-                "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_hbm, "unit": "GB/s",
-                "frac": round(achieved / peak_hbm, 4), "traffic": STAGE1_DRAM_BYTES,
+                "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": STAGE1_DRAM_BYTES,
                 "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch, ncu --set full "
                                 "on this workload",
-                "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured",
+                "peak_note": f"HBM copy bandwidth, {peaks['hbm_note']}",
                 "algorithmic_per_launch": {"bytes": slab_bytes, "flop": 2.0 * E * RRk,
                                            "note": "one read of the 64^3 x 10 FP32 slab; 2 E R_1 R_2 flop"},
                 "avg_launch_ms": round(mt_avg_ms, 5), "launches": int(k_n["mttkrp"]),
@@ -262,16 +366,22 @@ def main_ours(a):
                 "stage2": {"kernel": "stage2_kernel (SIMT contraction with chain tables)",
                            "avg_launch_ms": round(c_avg_ms, 5), "launches": int(k_n["contract"]),
                            "read_gbs": round(E // W2.dims[0] * RRk * 4 / max(c_avg_ms, 1e-9) / 1e6, 1)},
-                "sm_mhz_median": sm_clock}
+                "step": step_roofline(ms_step, F2, peaks["tf32_tflops"], E * 4, hbm, "tf32"),
+                "step_note": ("t_bound = max(F_alg / TF32 peak, one FP32 slab read / HBM); F_alg = 2 E sum_n "
+                              "R_n R_{n+1} x 5 sweeps")}
     kernel_share = {k: round(v / tot, 4) for k, v in k_ms.items() if tot > 0 and v > 0}
 
     out = {"metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": a.steps,
-           "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+           "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "precision": ("FP32 slab arithmetic (3-term TF32 split on tcgen05, FP32 accumulate), FP64 Gram / "
+                         "P_n / Q_n state, FP32 factor of Q_n refined with a double-FP32 residual; fit error "
+                         "against the FP64 oracle in fit_err_vs_oracle"),
            "config": {"workload": WORKLOAD_DESC, "entries_per_update": E,
+                      "inputs": "host-built FP64 TR(G) + noise, rounded to FP32; same bytes as the oracle's",
                       "l2": "flushed between steps (256 MB write outside the timed events)",
                       "parallelism": f"replicas x{world} (independent streams, no collective)"},
-           "roofline": roofline, "kernel_time_share": kernel_share,
+           "roofline": roofline, "peaks": peaks, "kernel_time_share": kernel_share,
            "gpu_launches": int(launches), "clocks": clk}
 
     # ---- e2e: public API with pinned host slabs, status + core read back per step ----
@@ -303,115 +413,152 @@ def main_ours(a):
                   "note": "str_update with on_host=1 pinned slab (copy inside the call, status read) "
                           "+ str_get_core(1), wall clock"}
 
-    # ---- plain FP64 GPU arm (same steps): throughput and fit error reference ----
+    # ---- accuracy checks (GPU side): the first CHECK_UPDATES updates of each arm ----
+    tchk = W2.t_init + CHECK_UPDATES * W2.t_new
+    checks = {}
+    ctxc = make("f32", X32)
+    for j in range(CHECK_UPDATES):
+        ctxc.update(slab(X32, W2, j))
+    checks["order4_f32"] = {"gpu_fit": ctxc.fit_error(X32[..., :tchk]), "cores": ctxc.cores()}
+    ctxc.close()
+
+    # ---- plain FP64 GPU arm (same steps and warm-up as the headline) ----
     if not a.no_fp64:
-        X64 = X
-        ctx64 = make("f64", X64)
-        t64, _, _ = timed_updates(p, torch, ctx64, lambda j: slab(X64, W2, j), min(a.steps, 4), a.warmup,
-                                  flush=flush)
-        steps64 = min(a.steps, 4)
-        fit64 = ctx64.fit_error(X64[..., :ctx64.time_rows()])
-        out["fp64_arm"] = {"value": steps64 * E / (sum(t64) / 1e3), "unit": "entries/s",
-                           "ms_per_step": sum(t64) / steps64, "steps": steps64}
-        # the FP32 arm over the same first warmup+steps64 updates vs FP64
-        ctxc = make("f32", X32)
-        for j in range(a.warmup + steps64):
-            ctxc.update(slab(X32, W2, j))
-        fitc = ctxc.fit_error(X32[..., :ctxc.time_rows()])
-        core_rel = max(float(np.linalg.norm(c - d) / np.linalg.norm(d))
-                       for c, d in zip(ctxc.cores(), ctx64.cores()))
-        ctxc.close()
+        ctx64 = make("f64", X)
+        t64, l64, _ = timed_updates(p, torch, ctx64, lambda j: slab(X, W2, j), a.steps, a.warmup, flush=flush)
         ctx64.close()
-        out["fit_error"] = {"f32_arm": fitc, "f64_arm": fit64, "rel_diff": abs(fitc - fit64) / fit64,
-                            "max_core_rel_diff": core_rel, "f32_arm_after_all_steps": fit32,
-                            "updates_compared": a.warmup + steps64}
-    # ---- rSTR rows ----
+        ms64 = sum(t64) / a.steps
+        out["fp64_arm"] = {"value": a.steps * E / (sum(t64) / 1e3), "unit": "entries/s", "ms_per_step": ms64,
+                           "steps": a.steps, "warmup": a.warmup, "dtype": "f64", "gpu_launches": int(l64),
+                           "step": step_roofline(ms64, F2, peaks["fp64_fma_tflops"], E * 8, hbm, "fp64"),
+                           "step_note": "t_bound = max(F_alg / measured FP64 FMA peak, one FP64 slab read / HBM)"}
+        ctxc = make("f64", X)
+        for j in range(CHECK_UPDATES):
+            ctxc.update(slab(X, W2, j))
+        checks["order4_f64"] = {"gpu_fit": ctxc.fit_error(X[..., :tchk]), "cores": ctxc.cores()}
+        ctxc.close()
+        c32, c64 = checks["order4_f32"]["cores"], checks["order4_f64"]["cores"]
+        out["fp64_arm"]["f32_vs_f64_arm"] = {
+            "max_core_rel_diff": max(float(np.linalg.norm(u - v) / np.linalg.norm(v)) for u, v in zip(c32, c64)),
+            "fit_rel_diff": abs(checks["order4_f32"]["gpu_fit"] - checks["order4_f64"]["gpu_fit"]) /
+            checks["order4_f64"]["gpu_fit"], "updates": CHECK_UPDATES}
+    del X
+    # ---- secondary rows ----
     if not a.no_rstr:
-        out["rstr"] = rstr_rows(p, torch, flush, rank)
+        out["rstr"] = rstr_rows(p, torch, flush, rank, peaks, checks)
     if not a.no_batch:
-        out["batch"] = batch_rows(p, torch, flush, rank)
+        out["batch"] = batch_rows(p, torch, flush, rank, peaks, checks)
     if not a.no_loss:
-        out["loss"] = loss_rows(p, torch, flush, rank, peak_hbm)
+        out["loss"] = loss_rows(p, torch, flush, rank, peaks, checks)
     if not a.no_large:
-        out["standin_60x5"] = large_rows(p, torch, flush, rank, peak_hbm)
-    # ---- CPU oracle baseline (rank 0, N = 1) ----
+        out["standin_60x5"] = large_rows(p, torch, flush, rank, peaks)
+    # ---- CPU oracle leg (rank 0, N = 1): baseline timing and fit errors on the same bytes ----
     if rank == 0 and world == 1 and not a.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(X, cores0)
+        cpu, fits = cpu_oracle_leg(Xh, cores0, checks, a)
+        out["cpu_baseline"] = cpu
+        out["fit_err_vs_oracle"] = fits["order4_f32"]
+        if "order4_f64" in fits and "fp64_arm" in out:
+            out["fp64_arm"]["fit_err_vs_oracle"] = fits["order4_f64"]
+        for k in ("uniform", "leverage", "ksrft"):
+            if "rstr" in out and f"rstr_{k}" in fits:
+                out["rstr"][k]["fit_err_vs_oracle"] = fits[f"rstr_{k}"]
+        if "batch" in out and "batch" in fits:
+            out["batch"]["fit_err_vs_oracle"] = fits["batch"]
+        if "loss" in out and "loss" in fits:
+            out["loss"]["loss_vs_oracle"] = fits["loss"]
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def measured_peak(key, fallback):
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)[key])
-    except Exception:
-        return fallback
-
-
-def rstr_rows(p, torch, flush, rank, steps=4, warmup=2):
+def rstr_rows(p, torch, flush, rank, peaks, checks, steps=4, warmup=2, nchk=2):
     """rSTR-U/L/K updates on the 512x512xT BF16 workload (sketch 2000, Philox seed 7)."""
     seed = W3.seed + 1000 * rank
-    G, X = build_tensor(p, torch, W3, seed)
-    Xb = p.paper_layout(X.to(torch.bfloat16))
-    del X
+    G, Xh, _ = host_workload(W3, seed)
     rng = np.random.default_rng(seed + 300)
-    init = [g + 0.05 * rng.standard_normal(g.shape) for g in G]
+    init = [g + INIT_PERTURB * rng.standard_normal(g.shape) for g in G]
     init[-1] = init[-1][:, :W3.t_init, :]
+    Xb = bf16_device(torch, Xh)
     E = int(np.prod(W3.dims)) * W3.t_new
+    m, R = W3.sketch_m, W3.ranks[0]
+    # F_alg per update: sampled MTTKRPs 2 I_n m R^2 (spatial modes) + 2 t_new m R^2 (temporal),
+    # sketched Grams 2 m R^4 per mode (FP32 pipe, pair arithmetic); bytes: the BF16 slab once
+    f_mma = 2.0 * m * R * R * (sum(W3.dims) + W3.t_new)
+    f_gram = 2.0 * m * R ** 4 * len(W3.ranks)
     rows = {}
+    tchk = W3.t_init + nchk * W3.t_new
     for sk in ("uniform", "leverage", "ksrft"):
-        ctx = p.str_init_cores(init, X0=p.paper_layout(Xb[..., :W3.t_init]), compute="f32", sketch=sk,
-                               m=W3.sketch_m, seed=W3.philox_seed, async_status=1,
-                               t_capacity=W3.t_init + (steps + warmup + 2) * W3.t_new)
+        def make(profile=0):
+            return p.str_init_cores(init, X0=p.paper_layout(Xb[..., :W3.t_init]), compute="f32", sketch=sk,
+                                    m=m, seed=W3.philox_seed, async_status=1, profile=profile,
+                                    t_capacity=W3.t_init + (steps + warmup + 2) * W3.t_new)
+        ctx = make()
         times, launches, _ = timed_updates(p, torch, ctx, lambda j: slab(Xb, W3, j), steps, warmup,
                                            randomized=True, flush=flush)
-        ctxp = p.str_init_cores(init, X0=p.paper_layout(Xb[..., :W3.t_init]), compute="f32", sketch=sk,
-                                m=W3.sketch_m, seed=W3.philox_seed, async_status=1, profile=1,
-                                t_capacity=W3.t_init + (steps + warmup + 2) * W3.t_new)
+        ctx.close()
+        ctxp = make(profile=1)
         _, _, pst = timed_updates(p, torch, ctxp, lambda j: slab(Xb, W3, j), steps, warmup,
                                   randomized=True, flush=flush, profile=True)
-        tot = sum(pst["class_ms"].values())
-        rows[sk] = {"value": steps * E / (sum(times) / 1e3), "unit": "entries/s",
-                    "ms_per_step": sum(times) / steps, "gpu_launches_per_step": launches / steps,
-                    "kernel_time_share": {k: round(v / tot, 4) for k, v in pst["class_ms"].items() if v > 0}}
-        ctx.close()
         ctxp.close()
+        tot = sum(pst["class_ms"].values())
+        ms = sum(times) / steps
+        f = f_mma + f_gram + (5.0 * E * np.log2(E) if sk == "ksrft" else 0.0)
+        rows[sk] = {"value": steps * E / (sum(times) / 1e3), "unit": "entries/s",
+                    "ms_per_step": ms, "gpu_launches_per_step": launches / steps,
+                    "kernel_time_share": {k: round(v / tot, 4) for k, v in pst["class_ms"].items() if v > 0},
+                    "step": step_roofline(ms, f, peaks["tf32_tflops"], E * 2 + (E * 16 if sk == "ksrft" else 0),
+                                          peaks["hbm_gbs"], "tf32")}
+        # accuracy check: the first nchk updates, fit over the data seen, on the BF16 values and
+        # on the original FP64 values
+        ctxc = make()
+        for j in range(nchk):
+            ctxc.rupdate(slab(Xb, W3, j))
+        Xo = to_device(torch, Xh[..., :tchk])
+        checks[f"rstr_{sk}"] = {"gpu_fit_bf16_data": ctxc.fit_error(Xb[..., :tchk]),
+                                "gpu_fit_original_data": ctxc.fit_error(Xo)}
+        ctxc.close()
+        del Xo
+    checks["rstr_data"] = {"X": Xh[..., :tchk], "init": init, "updates": nchk}
     rows["workload"] = ("rand3: 512x512xT, T=200, TR-ranks all 10, BF16 slab, FP32 slab-side arithmetic, "
-                        "sketch size 2000, Philox seed 7, updates of 5 slices")
+                        "sketch size 2000, Philox seed 7, init = true cores + 0.05 N(0,1) on 40 slices, "
+                        "updates of 5 slices")
+    rows["step_note"] = ("t_bound = max((2 m R^2 (I_1 + I_2 + t_new) + 2 N m R^4 [+ 5 E log2 E for KSRFT]) / "
+                         "TF32 peak, BF16 slab [+ complex mixed slab] bytes / HBM)")
     return rows
 
 
-def batch_rows(p, torch, flush, rank, steps=4, warmup=6, count=256):
+def batch_rows(p, torch, flush, rank, peaks, checks, steps=4, warmup=6, count=256, nchk=16):
     """Batched streams: `count` independent order-3 streams of uneven sizes
     (spatial dims in [16,128], TR-ranks in {2..12}, each stream with its own
-    number of new slices in 1..16 per step, held for the run), BF16 slabs, FP32
-    slab-side arithmetic, one sweep.  One str_update_batch per step (all
-    contexts as concurrent branches of one replayed graph) against one
-    str_update per context per step (each context's own graph), same data."""
+    number of new slices in 1..16 per step, held for the run), Gaussian cores
+    plus noise at 1e-2 relative, initial cores = true cores + 0.05 N(0,1), BF16
+    slabs, FP32 slab-side arithmetic, one sweep.  One str_update_batch per step against one
+    str_update per context per step, same data."""
     specs = synth.uneven_streams(count=count, steps=1, seed=5 + 1000 * rank)
-    data, entries = [], 0
+    data, entries, flop, nbytes = [], 0, 0.0, 0
     for i, sp in enumerate(specs):
         tn = sp.t_news[0]
         T = sp.t_init + (warmup + steps + 1) * tn
         G = synth.gaussian_cores(tuple(sp.dims) + (T,), sp.ranks, 7000 + i)
-        truth = p.str_init_cores(G, X0=None, t_capacity=T)
-        Xb = p.paper_layout(truth.reconstruct(0, T).to(torch.bfloat16))
-        truth.close()
-        init = [g.copy() for g in G]
+        Xh = synth.add_noise(host_tr_tensor(G), synth.gaussian_tensor(tuple(sp.dims) + (T,), 7100 + i), BATCH_NOISE)
+        Xb = bf16_device(torch, Xh)
+        rng = np.random.default_rng(7200 + i)
+        init = [g + INIT_PERTURB * rng.standard_normal(g.shape) for g in G]
         init[-1] = init[-1][:, :sp.t_init, :]
-        data.append((sp, tn, Xb, init))
-        entries += int(np.prod(sp.dims)) * tn
+        data.append((sp, tn, Xb, init, Xh if i < nchk else None))
+        e = int(np.prod(sp.dims)) * tn
+        entries += e
+        flop += str_flop(sp.dims, tn, sp.ranks, 1)
+        nbytes += 2 * e
 
     def make():
         return [p.str_init_cores(init, X0=p.paper_layout(Xb[..., :sp.t_init]), compute="f32", sweeps=1,
                                  t_capacity=sp.t_init + (warmup + steps + 1) * tn, async_status=1)
-                for sp, tn, Xb, init in data]
+                for sp, tn, Xb, init, _ in data]
 
     def slabs(j):
-        return [Xb[..., sp.t_init + j * tn:sp.t_init + (j + 1) * tn] for sp, tn, Xb, _ in data]
+        return [Xb[..., sp.t_init + j * tn:sp.t_init + (j + 1) * tn] for sp, tn, Xb, _, _ in data]
 
     def run(step_fn):
         stream = torch.cuda.Stream()
@@ -436,24 +583,40 @@ def batch_rows(p, torch, flush, rank, steps=4, warmup=6, count=256):
     same = all(np.array_equal(a.core(n), b.core(n)) for a, b in zip(ctxs[:8], seq[:8]) for n in (1, 2, 3))
     for c in ctxs + seq:
         c.close()
+    # accuracy check: one batched update of every stream, fit of the first nchk streams
+    ctxs = make()
+    p.str_update_batch(ctxs, slabs(0))
+    fits = []
+    for (sp, tn, Xb, init, Xh), c in zip(data[:nchk], ctxs[:nchk]):
+        t1 = sp.t_init + tn
+        fits.append({"bf16_data": c.fit_error(Xb[..., :t1]),
+                     "original_data": c.fit_error(to_device(torch, Xh[..., :t1]))})
+    for c in ctxs:
+        c.close()
+    checks["batch"] = {"gpu": fits, "data": [(d[4], d[3], d[1], d[0].t_init) for d in data[:nchk]]}
+    ms = ms_batch / steps
     return {"value": steps * entries / (ms_batch / 1e3), "unit": "entries/s",
-            "ms_per_step": ms_batch / steps,
+            "ms_per_step": ms,
             "sequential": {"value": steps * entries / (ms_seq / 1e3), "ms_per_step": ms_seq / steps},
             "bit_identical_to_sequential": bool(same),
             "entries_per_step": entries,
+            "step": step_roofline(ms, flop, peaks["tf32_tflops"], nbytes, peaks["hbm_gbs"], "tf32"),
+            "step_note": "t_bound = max(sum over streams of 2 E sum_n R_n R_{n+1} / TF32 peak, BF16 slabs / HBM)",
             "workload": (f"{count} independent order-3 streams, spatial dims uniform in [16,128], TR-ranks "
-                         "in {2..12}, 1-16 new slices per step (fixed per stream), BF16 slabs, FP32 slab-side "
-                         "arithmetic, 1 sweep; one str_update_batch per step vs one str_update per stream")}
+                         "in {2..12}, 1-16 new slices per step (fixed per stream), Gaussian cores, noise 1e-2, "
+                         "init = true cores + 0.05 N(0,1), BF16 slabs, FP32 slab-side arithmetic, 1 sweep; one "
+                         "str_update_batch per step vs one str_update per stream")}
 
 
-def large_rows(p, torch, flush, rank, peak_hbm, steps=3, warmup=3):
+def large_rows(p, torch, flush, rank, peaks, steps=3, warmup=3):
     """Stand-in for the paper's largest synthetic tensor (60 x 60 x 60 x 60 x 60,
     Sec. 4.3): Gaussian TR cores of rank 5 plus Gaussian noise (relative 1e-3),
     decomposition of the first 12 slices (20%) given as the perturbed true cores,
     then STR updates of 5 slices (64.8 M entries, 259 MB FP32 per slab), one
     sweep, FP32 slab arithmetic.  The tensor is made on the device by the
-    library's reconstruction.  Reports the update rate and the stage-1 kernel's
-    achieved HBM bandwidth at this size."""
+    library's reconstruction (so this row has no oracle comparison: the oracle's
+    inputs never come from the library).  Reports the update rate and the
+    stage-1 kernel's achieved HBM bandwidth at this size."""
     dims, T, R, t_init, t_new = (60, 60, 60, 60), 60, 5, 12, 5
     seed = 77 + 1000 * rank
     G = synth.gaussian_cores(dims + (T,), (R,) * 5, seed)
@@ -486,32 +649,38 @@ def large_rows(p, torch, flush, rank, peak_hbm, steps=3, warmup=3):
     s1 = k_ms["mttkrp"] / max(1, k_n["mttkrp"])
     gbs = E * 4 / (s1 / 1e3) / 1e9
     tot = sum(k_ms.values())
-    return {"value": steps * E / (sum(times) / 1e3), "unit": "entries/s", "ms_per_step": sum(times) / steps,
+    ms = sum(times) / steps
+    hbm = peaks["hbm_gbs"]
+    return {"value": steps * E / (sum(times) / 1e3), "unit": "entries/s", "ms_per_step": ms,
             "gpu_launches_per_step": launches / steps,
             "stage1": {"kernel": "stage1_ws_kernel", "avg_launch_ms": round(s1, 5), "launches": int(k_n["mttkrp"]),
-                       "bytes_per_launch": E * 4, "achieved_gbs": round(gbs, 1), "peak": peak_hbm,
-                       "frac": round(gbs / peak_hbm, 4), "peak_note": "measured HBM copy bandwidth, of measured"},
+                       "bytes_per_launch": E * 4, "achieved_gbs": round(gbs, 1), "peak": hbm,
+                       "frac": round(gbs / hbm, 4), "peak_note": f"HBM copy bandwidth, {peaks['hbm_note']}"},
+            "step": step_roofline(ms, str_flop(dims, t_new, (R,) * 5, 1), peaks["tf32_tflops"], E * 4, hbm, "tf32"),
             "kernel_time_share": {k: round(v / tot, 4) for k, v in k_ms.items() if tot > 0 and v > 0},
+            "fit_err_vs_oracle": None,
+            "fit_err_note": "not compared: this row's tensor is made by the library on the device",
             "workload": ("60x60x60x60x60 stand-in (Sec. 4.3 largest synthetic tensor): TR-ranks 5, Gaussian cores, "
                          "noise 1e-3, init on 12 slices, updates of 5 slices (64.8 M entries, FP32), 1 sweep")}
 
 
-def loss_rows(p, torch, flush, rank, peak_hbm, steps=3, warmup=3):
+def loss_rows(p, torch, flush, rank, peaks, checks, steps=3, warmup=3):
     """Masked TR fit loss and its backward on the 32x32x32x32x100 FP32 tensor
     (TR-ranks 6, 30% of the entries hidden, mask as packed bits): one forward
     (loss) and one backward (gradients of all five cores) per step.  The tensor
-    is the TR tensor of Gaussian cores (no noise), made on the device by the
-    library's reconstruction."""
+    is the TR tensor of Gaussian cores plus Gaussian noise at 1e-2 relative
+    Frobenius norm (so the residual is well above FP32 rounding), built on the
+    host; the cores are the true cores rounded to FP32."""
     W = synth.WORKLOADS["masked5"]
     dims = tuple(W.dims) + (W.T,)
     seed = W.seed + 1000 * rank
     G = synth.gaussian_cores(dims, W.ranks, seed)
-    truth = p.str_init_cores(G, X0=None, t_capacity=W.T)
-    X = p.paper_layout(truth.reconstruct(0, W.T, dtype=torch.float32))
-    truth.close()
-    bits = torch.from_numpy(synth.pack_mask_bits(synth.bernoulli_keep_mask(dims, 0.3, seed))
-                            .view(np.int32)).cuda()
-    cores = [torch.from_numpy(a).to("cuda", torch.float32) for a in p.cores_to_abi(G)]
+    G32 = [g.astype(np.float32).astype(np.float64) for g in G]
+    Xh = synth.add_noise(host_tr_tensor(G), synth.gaussian_tensor(dims, seed + 100), LOSS_NOISE).astype(np.float32)
+    X = to_device(torch, Xh)
+    mask = synth.bernoulli_keep_mask(dims, 0.3, seed)
+    bits = torch.from_numpy(synth.pack_mask_bits(mask).view(np.int32)).cuda()
+    cores = [torch.from_numpy(a).to("cuda", torch.float32) for a in p.cores_to_abi(G32)]
     E = int(np.prod(dims))
 
     def timed(fn):
@@ -533,21 +702,28 @@ def loss_rows(p, torch, flush, rank, peak_hbm, steps=3, warmup=3):
     ms_f = timed(lambda: p.tr_masked_loss_fwd(cores, X, bits))
     ms_b = timed(lambda: p.tr_masked_loss_bwd(cores, X, bits, 1.0))
     loss = float(p.tr_masked_loss_fwd(cores, X, bits).item())
+    checks["loss"] = {"gpu": loss, "X": Xh, "cores": G32, "mask": mask}
     in_bytes = E * 4 + bits.numel() * 4
+    hbm = peaks["hbm_gbs"]
+    t_bound_ms = in_bytes / (hbm * 1e9) * 1e3
     return {"value": E / ((ms_f + ms_b) / 1e3), "unit": "entries/s", "ms_fwd": ms_f, "ms_bwd": ms_b,
-            "fwd_read_gbs": in_bytes / (ms_f / 1e3) / 1e9, "fwd_frac_of_measured_hbm": in_bytes / (ms_f / 1e3) / 1e9 / peak_hbm,
-            "t_bound_fused_fwd_bwd_ms": in_bytes / (peak_hbm * 1e9) * 1e3, "loss": loss,
-            "workload": ("masked5: 32x32x32x32x100 FP32 (104.9 M entries, 419 MB), TR-ranks all 6, Bernoulli(0.3) "
+            "fwd_read_gbs": in_bytes / (ms_f / 1e3) / 1e9, "fwd_frac_of_hbm": in_bytes / (ms_f / 1e3) / 1e9 / hbm,
+            "t_bound_fused_fwd_bwd_ms": t_bound_ms, "frac_step": t_bound_ms / (ms_f + ms_b), "loss": loss,
+            "step_note": "t_bound = one read of X and the mask bits / HBM (one fused pass serves fwd and bwd)",
+            "workload": ("masked5: 32x32x32x32x100 FP32 (104.9 M entries, 419 MB), TR-ranks all 6, noise 1e-2, "
+                         "Bernoulli(0.3) "
                          "hidden entries as packed mask bits; one tr_masked_loss_fwd + one tr_masked_loss_bwd "
                          "(all 5 core gradients) per step")}
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle (the reference arm and the cpu_baseline leg)
+# CPU oracle leg (the cpu_baseline and the fit errors against the oracle) and
+# the reference arm
 # ---------------------------------------------------------------------------
 def oracle_sample(Xh, cores0, nupd=1):
     """The FP64 oracle's STR update (Alg. 4, 5 sweeps) on the order4 workload:
-    initialisation stage on 40 slices (untimed), then `nupd` timed updates."""
+    initialisation stage on 40 slices (untimed), then `nupd` timed updates.
+    Returns (seconds, final state, temporal rows seen)."""
     from oracle import stream as ost
     st = ost.str_init(Xh[..., :W2.t_init], cores0)
     t = W2.t_init
@@ -555,7 +731,7 @@ def oracle_sample(Xh, cores0, nupd=1):
     for _ in range(nupd):
         ost.str_update(st, Xh[..., t:t + W2.t_new], sweeps=W2.sweeps)
         t += W2.t_new
-    return time.perf_counter() - t0
+    return time.perf_counter() - t0, st, t
 
 
 def cpu_threads():
@@ -565,49 +741,127 @@ def cpu_threads():
     return os.cpu_count()
 
 
-def cpu_baseline(X, cores0, nupd=2):
-    Xh = X[..., :W2.t_init + nupd * W2.t_new].double().cpu().numpy()
-    secs = oracle_sample(Xh, cores0, nupd)
+def _rel(a, b):
+    return abs(a - b) / abs(b) if b else None
+
+
+def single_thread_sample(Xh, cores0):
+    """One oracle update timed in a child process with every BLAS pool at one
+    thread (the variables must be set before numpy loads)."""
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "sample.npz")
+        np.savez(path, X=Xh[..., :W2.t_init + W2.t_new], **{f"G{k}": g for k, g in enumerate(cores0)})
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", path],
+                           capture_output=True, text=True, env=env, timeout=600)
+        if r.returncode != 0:
+            return {"error": (r.stderr.strip().splitlines() or ["failed"])[-1]}
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def main_oracle_sample(path):
+    z = np.load(path)
+    cores0 = [z[f"G{k}"] for k in range(len(W2.ranks))]
+    secs, _, _ = oracle_sample(z["X"], cores0, 1)
     E = int(np.prod(W2.dims)) * W2.t_new
-    return {"value": nupd * E / secs, "unit": "entries/s", "cores": cpu_threads(), "kind": "oracle",
-            "sample": f"{nupd} STR updates of 10 slices (5 sweeps) of the order4 workload, FP64 numpy oracle",
-            "seconds": secs}
+    print(json.dumps({"value": E / secs, "unit": "entries/s", "seconds": secs, "cores": cpu_threads()}))
+
+
+def cpu_oracle_leg(Xh, cores0, checks, a):
+    """The FP64 oracle on the host cores, on bounded samples of each row's
+    workload and the same bytes its GPU arm read: timing (the cpu_baseline) and
+    the relative fit error of each GPU arm against it."""
+    from oracle import loss as olo
+    from oracle import stream as ost
+    from oracle import tr as otr
+    fits = {}
+    E = int(np.prod(W2.dims)) * W2.t_new
+    # order-4, FP32 arm: the oracle on the FP32-rounded bytes; FP64 arm: on the FP64 bytes
+    X32h = Xh.astype(np.float32).astype(np.float64)
+    secs, st, t = oracle_sample(X32h, cores0, CHECK_UPDATES)
+    e_or = otr.fit_error(X32h[..., :t], st.cores)
+    g = checks["order4_f32"]
+    fits["order4_f32"] = {"gpu": g["gpu_fit"], "oracle": e_or, "rel_diff": _rel(g["gpu_fit"], e_or),
+                          "max_core_rel_diff": max(float(np.linalg.norm(u - v) / np.linalg.norm(v))
+                                                   for u, v in zip(g["cores"], st.cores)),
+                          "updates": CHECK_UPDATES, "data": "FP32-rounded slab values, as the GPU arm read them"}
+    cpu = {"value": CHECK_UPDATES * E / secs, "unit": "entries/s", "cores": cpu_threads(), "kind": "oracle",
+           "sample": (f"{CHECK_UPDATES} STR updates of 10 slices (5 sweeps) of the order4 workload, FP64 numpy "
+                      "oracle, after its initialisation stage (untimed)"), "seconds": secs}
+    if "order4_f64" in checks:
+        _, st64, t = oracle_sample(Xh, cores0, CHECK_UPDATES)
+        e64 = otr.fit_error(Xh[..., :t], st64.cores)
+        g = checks["order4_f64"]
+        fits["order4_f64"] = {"gpu": g["gpu_fit"], "oracle": e64, "rel_diff": _rel(g["gpu_fit"], e64),
+                              "max_core_rel_diff": max(float(np.linalg.norm(u - v) / np.linalg.norm(v))
+                                                       for u, v in zip(g["cores"], st64.cores)),
+                              "updates": CHECK_UPDATES, "data": "FP64 slab values"}
+    cpu["single_thread"] = single_thread_sample(Xh, cores0)
+    # rSTR rows: the oracle on the BF16 values and on the original values
+    if "rstr_data" in checks:
+        rd = checks["rstr_data"]
+        Xo = rd["X"]
+        Xr = synth.to_bf16_values(Xo)
+        for sk in ("uniform", "leverage", "ksrft"):
+            g = checks[f"rstr_{sk}"]
+            res = {"updates": rd["updates"]}
+            for name, Xd, gk in (("bf16_data", Xr, "gpu_fit_bf16_data"),
+                                 ("original_data", Xo, "gpu_fit_original_data")):
+                st = ost.rstr_init(Xd[..., :W3.t_init], rd["init"], sk, W3.sketch_m, W3.philox_seed)
+                t = W3.t_init
+                for _ in range(rd["updates"]):
+                    ost.rstr_update(st, Xd[..., t:t + W3.t_new])
+                    t += W3.t_new
+                e = otr.fit_error(Xd[..., :t], st.cores)
+                res[name] = {"gpu": g[gk], "oracle": e, "rel_diff": _rel(g[gk], e)}
+            fits[f"rstr_{sk}"] = res
+    # batched streams: the first streams, one update each
+    if "batch" in checks:
+        out = []
+        for (Xo, init, tn, t_init), g in zip(checks["batch"]["data"], checks["batch"]["gpu"]):
+            rec = {}
+            for name, Xd in (("bf16_data", synth.to_bf16_values(Xo)), ("original_data", Xo)):
+                st = ost.str_init(Xd[..., :t_init], init)
+                ost.str_update(st, Xd[..., t_init:t_init + tn])
+                e = otr.fit_error(Xd[..., :t_init + tn], st.cores)
+                rec[name] = _rel(g[name], e)
+            out.append(rec)
+        fits["batch"] = {"streams": len(out), "updates": 1,
+                         "max_rel_diff_bf16_data": max(r["bf16_data"] for r in out),
+                         "max_rel_diff_original_data": max(r["original_data"] for r in out),
+                         "first_stream": checks["batch"]["gpu"][0]}
+    # masked loss: the loss value on the same FP32 bytes and FP32-rounded cores
+    if "loss" in checks:
+        lc = checks["loss"]
+        ref = olo.masked_loss(lc["X"].astype(np.float64), lc["cores"], lc["mask"])
+        fits["loss"] = {"gpu": lc["gpu"], "oracle": ref, "rel_diff": _rel(lc["gpu"], ref)}
+    return cpu, fits
 
 
 def main_reference(a):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    # inputs: same recipe on the host (oracle builds TR(G) itself)
     from oracle import stream as ost
-    from oracle import tr as otr
-    nsl = a.warmup + a.steps
-    G = synth.gaussian_cores(tuple(W2.dims) + (W2.T,), W2.ranks, W2.seed)
-    tmax = W2.t_init + nsl * W2.t_new
-    Gt = G[:-1] + [G[-1][:, :tmax, :]]
-    Xt = otr.tr_full(Gt)
-    full = synth.gaussian_tensor(tuple(W2.dims) + (W2.T,), W2.seed + 100)[..., :tmax]
-    X = Xt + W2.noise * np.linalg.norm(Xt) * full / np.linalg.norm(full)
-    rng = np.random.default_rng(W2.seed + 200)
-    init = [g + 0.3 * rng.standard_normal(g.shape) for g in G]
-    init[-1] = init[-1][:, :W2.t_init, :]
+    _, X, init = host_workload(W2, W2.seed)
+    X = X.astype(np.float32).astype(np.float64)        # the FP32 slab values the GPU arm reads
     st = ost.str_init(X[..., :W2.t_init], init)
-    t = W2.t_init
-    for _ in range(a.warmup):
-        ost.str_update(st, X[..., t:t + W2.t_new], sweeps=W2.sweeps)
-        t += W2.t_new
+    nsl = (W2.T - W2.t_init) // W2.t_new
     times = []
-    for _ in range(a.steps):
+    for j in range(a.warmup + a.steps):
+        t = W2.t_init + (j % nsl) * W2.t_new
         t0 = time.perf_counter()
         ost.str_update(st, X[..., t:t + W2.t_new], sweeps=W2.sweeps)
-        times.append(time.perf_counter() - t0)
-        t += W2.t_new
+        if j >= a.warmup:
+            times.append(time.perf_counter() - t0)
     E = int(np.prod(W2.dims)) * W2.t_new
     value = a.steps * E / sum(times)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / a.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "entries_per_update": E},
+           "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "entries_per_update": E,
+                                           "inputs": "host-built FP64 TR(G) + noise, rounded to FP32; same "
+                                                     "bytes and initial cores as the GPU arm"},
            "cpu_baseline": {"value": value, "unit": "entries/s", "kind": "oracle", "cores": cpu_threads(),
                             "sample": "each step = one STR update of 10 slices (5 sweeps) by the FP64 oracle"},
            "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -616,7 +870,9 @@ def main_reference(a):
 
 if __name__ == "__main__":
     args = args_parse()
-    if args.impl == "reference":
+    if args.oracle_sample:
+        main_oracle_sample(args.oracle_sample)
+    elif args.impl == "reference":
         main_reference(args)
     else:
         main_ours(args)

@@ -292,6 +292,19 @@ str_status tr_masked_loss_fwd_noalloc(int N, const int64_t* dims, const int* ran
                                       const void* X_dev, const uint32_t* mask_bits,
                                       double* loss_dev, void* stream);
 
+/*
+ * str_fma_probe -- measurement utility; the paper has no counterpart.  Enqueues
+ * one kernel of `ctas` blocks of 256 threads in which every thread runs
+ * `iters` rounds of 32 fused multiply-adds of `dtype` (STR_F32 or STR_F64) in
+ * eight independent chains, and writes one sum per block to `out` (device,
+ * `ctas` elements of dtype, caller-owned).  *flop (host) receives the launch's
+ * floating-point operations, 64 * iters * 256 * ctas.  Timing the launch with
+ * CUDA events on `stream` gives the FMA pipe's rate, the denominator of the
+ * roofline for work on the FP32 or FP64 pipes.  STR_ERR_INVALID_ARG for NULL
+ * pointers or non-positive sizes, STR_ERR_DTYPE for other types.
+ */
+str_status str_fma_probe(str_dtype dtype, int ctas, int64_t iters, void* out, double* flop, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -107,6 +107,7 @@ _SIGS = [
                                    c_void_p, c_void_p, c_double, POINTER(c_void_p), c_void_p]),
     ("tr_masked_loss_fwd_noalloc", c_int, [c_int, POINTER(c_int64), POINTER(c_int), c_int,
                                            POINTER(c_void_p), c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("str_fma_probe", c_int, [c_int, c_int, c_int64, c_void_p, POINTER(c_double), c_void_p]),
 ]
 
 
@@ -446,6 +447,17 @@ def tr_masked_loss_bwd(cores_abi, X, mask_bits=None, grad_scale: float = 1.0, st
                                     c_void_p(mask_bits.data_ptr()) if mask_bits is not None else None,
                                     float(grad_scale), gptrs, _stream_handle(stream)), "tr_masked_loss_bwd")
     return grads
+
+
+def fma_probe(dtype: str, ctas: int, iters: int, out, stream=None) -> float:
+    """Enqueue the library's FMA-rate probe (``str_fma_probe``) writing into the
+    CUDA tensor ``out`` (``ctas`` elements of ``dtype``, "f32" or "f64");
+    returns the launch's floating-point operations."""
+    code = {"f32": STR_F32, "f64": STR_F64}[dtype]
+    flop = c_double(0.0)
+    _check(lib().str_fma_probe(code, int(ctas), int(iters), c_void_p(out.data_ptr()), byref(flop),
+                               _stream_handle(stream)), "str_fma_probe")
+    return float(flop.value)
 
 
 def _make_loss_fn():
