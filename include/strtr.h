@@ -221,9 +221,16 @@ typedef struct {
   int64_t time_rows;        /* temporal rows held */
   int64_t kernel_launches;  /* kernels launched by the last update */
   int64_t device_bytes;     /* device memory owned by the context */
-  double min_pivot_ratio;   /* smallest L_kk^2 / Q_kk seen by the last update's solves */
+  double min_pivot_ratio;   /* pivot / diagonal ratio (min over pivots) of the last factorisation of
+                             * the last update's solves (0 for a pivot too small to use) */
   int64_t class_launches[STR_K_CLASSES];  /* with opt.profile: launches per class */
   double class_ms[STR_K_CLASSES];         /* with opt.profile: summed event time per class */
+  int64_t fp64_fallbacks;   /* FP32 slab arithmetic: row blocks (CTAs) of the refined solves, since
+                             * the context was created, that took the FP64 fallback because Q_n was
+                             * too ill-conditioned for the FP32 inverse (pivot / diagonal ratio
+                             * below 2^-13, or a first refinement correction above 1e-3 of the
+                             * solution); their rows are solved with an FP64 inverse and one FP64
+                             * refinement step.  Orders R_n R_{n+1} > 128 have no fallback. */
 } str_stats;
 /* Fills *stats.  The profile counters cover the launches since the previous
  * str_get_stats call (they are reset by it); reading them waits for those

@@ -51,7 +51,7 @@ class StrTensor(Structure):
 class StrStats(Structure):
     _fields_ = [("steps", c_int64), ("time_rows", c_int64), ("kernel_launches", c_int64),
                 ("device_bytes", c_int64), ("min_pivot_ratio", c_double),
-                ("class_launches", c_int64 * 9), ("class_ms", c_double * 9)]
+                ("class_launches", c_int64 * 9), ("class_ms", c_double * 9), ("fp64_fallbacks", c_int64)]
 
 
 KERNEL_CLASSES = ("mttkrp", "reduce", "gram", "factor", "solve", "sketch", "dft", "other", "contract")
@@ -297,6 +297,7 @@ class Stream:
         out = {f: getattr(s, f) for f, _ in StrStats._fields_[:5]}
         out["class_launches"] = dict(zip(KERNEL_CLASSES, list(s.class_launches)))
         out["class_ms"] = dict(zip(KERNEL_CLASSES, list(s.class_ms)))
+        out["fp64_fallbacks"] = int(s.fp64_fallbacks)
         return out
 
     def sync(self):

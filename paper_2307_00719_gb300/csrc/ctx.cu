@@ -114,6 +114,7 @@ struct str_ctx {
   int* d_status = nullptr;
   int* h_status = nullptr;       // pinned
   double* d_pivot = nullptr;
+  unsigned* d_fallbacks = nullptr;   // CTAs of refined solves that took the FP64 fallback
   double* h_sums = nullptr;      // pinned (2 doubles)
   std::vector<void*> owned;
   size_t bytes = 0;
@@ -423,7 +424,8 @@ str_status apply_q(str_ctx* c, const double* Qm, int n, const double* Pm, int64_
       c->qsplit_of = Qm;
     }
     LCHK(c, STR_K_SOLVE, launch_apply_df((const float*)c->lfac.p, (const float*)c->qf.p, (const float*)c->qlo.p, n,
-                                         Pm, rows, out64, out32, ps && ps->part ? ps : nullptr, c->d_status, s));
+                                         Pm, rows, out64, out32, ps && ps->part ? ps : nullptr, c->d_status, s,
+                                         Qm, c->d_pivot, c->d_fallbacks));
   } else if (c->compute == 1) {
     LCHK(c, STR_K_SOLVE, launch_apply_mixed((const float*)c->lfac.p, Qm, n, Pm, rows, 1, out64, out32,
                                             ps && ps->part ? ps : nullptr, s));
@@ -507,7 +509,8 @@ str_status leverage(str_ctx* c, const double* G, int64_t I, int Ra, int Rb, doub
     LCHK(c, STR_K_SOLVE, launch_split_pair((double*)c->gram.p, (int64_t)RR * RR, (float*)c->qf.p, (float*)c->qlo.p, s));
     c->qsplit_of = (const double*)c->gram.p;
     LCHK(c, STR_K_SOLVE, launch_apply_df((const float*)c->lfac.p, (const float*)c->qf.p, (const float*)c->qlo.p, RR,
-                                         G, I, (double*)c->levx.p, nullptr, nullptr, c->d_status, s));
+                                         G, I, (double*)c->levx.p, nullptr, nullptr, c->d_status, s,
+                                         (const double*)c->gram.p, nullptr, c->d_fallbacks));
     LCHK(c, STR_K_SOLVE, launch_leverage_dot(G, (const double*)c->levx.p, I, RR, p_out, s));
     return STR_OK;
   }
@@ -987,6 +990,7 @@ str_status ctx_create(str_ctx** out, int N, const int64_t* dims, const int* rank
   }
   if ((st = dalloc_t(c, &c->d_status, 1)) != STR_OK) return fail(st);
   if ((st = dalloc_t(c, &c->d_pivot, 1)) != STR_OK) return fail(st);
+  if ((st = dalloc_t(c, &c->d_fallbacks, 1)) != STR_OK) return fail(st);
   if (cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess) return fail(STR_ERR_OOM);
   if (cudaMallocHost(&c->h_sums, 4 * sizeof(double)) != cudaSuccess) return fail(STR_ERR_OOM);
   *c->h_status = 0;
@@ -2147,6 +2151,9 @@ str_status str_get_stats(const str_ctx* c, str_stats* stats) {
   double piv = 0.0;
   if (cudaMemcpy(&piv, c->d_pivot, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return STR_ERR_CUDA;
   stats->min_pivot_ratio = piv;
+  unsigned fb = 0;
+  if (cudaMemcpy(&fb, c->d_fallbacks, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return STR_ERR_CUDA;
+  stats->fp64_fallbacks = fb;
   str_ctx* m = const_cast<str_ctx*>(c);
   // optional launch timeline (profiling mode): STRTR_TIMELINE names a file that
   // receives one line per timed launch: class, stream (0 caller, 1-2 side

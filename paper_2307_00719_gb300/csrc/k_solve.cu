@@ -97,6 +97,9 @@ cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double*
 // updates its entries: one barrier per pivot.  After n sweeps the matrix holds
 // -Q^{-1}.
 // ---------------------------------------------------------------------------
+// orders served by the refined solve with the FP64 fallback (apply_df_kernel)
+__host__ __device__ __forceinline__ bool apply_df_supported_d(int n) { return n >= 2 && n <= 128; }
+
 // fast reciprocal for the FP32 inverse (CUDA's approximate division, <= 2 ulp):
 // the FP32 inverse only seeds an FP64-residual refinement
 __device__ __forceinline__ float recip_fast(float x) { return __fdividef(1.0f, x); }
@@ -109,9 +112,13 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 __device__ __forceinline__ float ldq(const float* p, bool cg) { return cg ? __ldcg(p) : *p; }
 __device__ __forceinline__ double ldq(const double* p, bool cg) { return cg ? __ldcg(p) : *p; }
 
+// flag_singular: a pivot <= n eps max(diag) sets DEV_ERR_SINGULAR.  When the
+// refined solve that follows has the FP64 fallback (orders <= 128) the FP32
+// inverse only reports the pivot ratio (0 for such a pivot) and the fallback
+// decides singularity in FP64.
 template <typename T, int B, typename SRC>
 __device__ __forceinline__ void sweep_body(const SRC* __restrict__ Q, int n, T* __restrict__ W, int* status,
-                                           double* pivot_ratio, bool cg) {
+                                           double* pivot_ratio, bool cg, bool flag_singular) {
   __shared__ T col[2][16 * B];
   __shared__ T qd[16 * B];
   __shared__ T pivs[16 * B];   // pivot k as met (before any replacement)
@@ -197,7 +204,7 @@ __device__ __forceinline__ void sweep_body(const SRC* __restrict__ Q, int n, T* 
     T ratio = (T)1;
     for (int k = tid; k < n; k += 32) {
       const T p = pivs[k];
-      if (!(p > tol)) bad = 1;
+      if (!(p > tol)) { bad = 1; ratio = (T)0; }
       else if (qd[k] > (T)0) {
         const T r = p / qd[k];
         ratio = r < ratio ? r : ratio;
@@ -210,7 +217,7 @@ __device__ __forceinline__ void sweep_body(const SRC* __restrict__ Q, int n, T* 
       ratio = o < ratio ? o : ratio;
     }
     if (tid == 0) {
-      if (bad && status) atomicOr(status, DEV_ERR_SINGULAR);
+      if (bad && status && flag_singular) atomicOr(status, DEV_ERR_SINGULAR);
       if (pivot_ratio) *pivot_ratio = (double)ratio;
     }
   }
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
                                                             T* __restrict__ W, int* status,
                                                             double* pivot_ratio) {
   PDL_ENTRY();
-  sweep_body<T, B, double>(Q, n, W, status, pivot_ratio, false);
+  sweep_body<T, B, double>(Q, n, W, status, pivot_ratio, false, !apply_df_supported_d(n));
 }
 
 // ---------------------------------------------------------------------------
@@ -298,7 +305,8 @@ __global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ 
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    sweep_body<float, SB, float>(ff.Qf, pRa * pRb, ff.W, ff.status, ff.pivot_ratio, true);
+    sweep_body<float, SB, float>(ff.Qf, pRa * pRb, ff.W, ff.status, ff.pivot_ratio, true,
+                                 !apply_df_supported_d(pRa * pRb));
   }
 }
 
@@ -641,7 +649,98 @@ struct ApplyDF {
   double* out64 = nullptr;
   float* out32 = nullptr;
   int* status = nullptr;
+  const double* Q64 = nullptr;          // FP64 Q for the fallback (null: no fallback)
+  const double* pivot_ratio = nullptr;  // written by the FP32 inverse (null: not checked)
+  unsigned* fallbacks = nullptr;        // CTAs that took the FP64 fallback (counter)
 };
+
+// FP64 fallback of the refined solve, for a Q whose FP32 inverse cannot seed a
+// converging refinement (cond(Q) u_32 not small; see apply_df_kernel): the CTA
+// inverts Q in FP64 by the symmetric sweep in shared memory (two barriers per
+// pivot), then each of its rows takes g = p Q^{-1} and one FP64 refinement
+// step g += (p - g Q) Q^{-1}.  The right-hand side is formed from the split
+// partials in split order (and stored) as in the FP32 path.
+constexpr double kFallbackPivotRatio = 1.0 / 8192.0;   // smallest FP32 pivot / diagonal kept
+constexpr float kFallbackCorrection = 1e-3f;           // largest first correction kept, |dg| / |g|
+
+__device__ __noinline__ void apply_fp64_rows(const ApplyDF& a, double* sm) {
+  const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
+  double* W = sm;           // n x n: Q, then -Q^{-1}
+  double* cb = W + n * n;   // pivot column
+  double* pv = cb + n;      // right-hand side
+  double* gv = pv + n;      // solution
+  double* rv = gv + n;      // residual
+  __shared__ double s_tol;
+  __shared__ int s_bad;
+  for (int e = tid; e < n * n; e += nt) W[e] = a.Q64[e];
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < n; ++k) mx = fmax(mx, W[k * n + k]);
+    s_tol = (double)n * 2.220446049250313e-16 * mx;
+    s_bad = 0;
+  }
+  __syncthreads();
+  const double tol = s_tol;
+  for (int k = 0; k < n; ++k) {
+    for (int i = tid; i < n; i += nt) cb[i] = W[i * n + k];
+    __syncthreads();
+    double piv = cb[k];
+    if (!(piv > tol)) {
+      piv = 1.0;
+      if (tid == 0) s_bad = 1;
+    }
+    const double rcp = 1.0 / piv;
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, j = e - i * n;
+      double v;
+      if (i == k) v = (j == k) ? -rcp : cb[j] * rcp;
+      else if (j == k) v = cb[i] * rcp;
+      else v = fma(-cb[i] * rcp, cb[j], W[e]);
+      W[e] = v;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && s_bad && a.status) atomicOr(a.status, DEV_ERR_SINGULAR);
+  for (int64_t r = blockIdx.x; r < a.rows; r += gridDim.x) {
+    for (int c = tid; c < n; c += nt) {
+      double pc;
+      if (a.ps.part) {
+        pc = a.ps.base ? a.ps.base[r * n + c] : 0.0;
+        double acc = 0.0;
+        const float* pp = a.ps.part + r * n + c;
+        const int64_t st = a.rows * n;
+        for (int k = 0; k < a.ps.splits; ++k) acc += (double)pp[(int64_t)k * st];
+        pc += acc;
+        a.ps.pout[r * n + c] = pc;
+      } else {
+        pc = a.P[r * n + c];
+      }
+      pv[c] = pc;
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) {          // g = p Q^{-1}  (W = -Q^{-1})
+      double g = 0.0;
+      for (int k = 0; k < n; ++k) g = fma(-pv[k], W[k * n + c], g);
+      gv[c] = g;
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) {          // residual p - g Q  (Q symmetric)
+      double t = pv[c];
+      for (int k = 0; k < n; ++k) t = fma(-gv[k], a.Q64[(int64_t)k * n + c], t);
+      rv[c] = t;
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) {
+      double g = gv[c];
+      for (int k = 0; k < n; ++k) g = fma(-rv[k], W[k * n + c], g);
+      if (a.out64) a.out64[r * n + c] = g;
+      if (a.out32) a.out32[r * n + c] = (float)g;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && a.fallbacks) atomicAdd(a.fallbacks, 1u);
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -663,10 +762,19 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
   float* vf = (float*)(pd4 + 4 * n);        // n: FP32 vector of the current product
   float* red = vf + n;                      // 4 x n partial sums (x2 for pairs)
   __shared__ __align__(8) uint64_t bar;
+  __shared__ float s_dn[2], s_gn[2];
+  __shared__ int s_redo;
   const int tid = threadIdx.x, c0 = tid & 63, part = tid >> 6;
+  // a tiny FP32 pivot (or none recorded as usable): the FP32 inverse cannot seed
+  // the refinement, go straight to the FP64 fallback
+  if (a.Q64 && a.pivot_ratio && !(*a.pivot_ratio >= kFallbackPivotRatio)) {
+    apply_fp64_rows(a, (double*)sma);
+    return;
+  }
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_redo = 0;
   }
   __syncthreads();
   // even n: bulk copies (sizes in 16-byte units); odd n: plain loads
@@ -815,6 +923,9 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
     }
     __syncthreads();
     if (part == 0) {
+      // the first correction's size estimates the FP32 inverse's error on this
+      // row (the refined error is about its square): too large = fallback
+      float dn = 0.f, gn = 0.f;
 #pragma unroll
       for (int u = 0; u < CPT; ++u) {
         const int c = c0 + 64 * u;
@@ -823,13 +934,26 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
         const double gv = (double)g[u] + (double)d;
         if (a.out64) a.out64[r * n + c] = gv;
         if (a.out32) a.out32[r * n + c] = (float)gv;
+        dn = fmaf(d, d, dn);
+        gn = fmaf(g[u], g[u], gn);
       }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        dn += __shfl_xor_sync(0xffffffffu, dn, off);
+        gn += __shfl_xor_sync(0xffffffffu, gn, off);
+      }
+      if ((tid & 31) == 0) { s_dn[tid >> 5] = dn; s_gn[tid >> 5] = gn; }
     }
     __syncthreads();
+    if (tid == 0) {
+      const float dn = s_dn[0] + s_dn[1], gn = s_gn[0] + s_gn[1];
+      if (!(dn <= kFallbackCorrection * kFallbackCorrection * gn)) s_redo = 1;
+    }
   }
   if (!staged) {   // no row: the bulk copies still complete before exit
     mbar_wait(&bar, 0, 2000000000ull);
   }
+  if (a.Q64 && __syncthreads_or(s_redo)) apply_fp64_rows(a, (double*)sma);
 }
 
 size_t apply_df_smem(int n) {
@@ -855,10 +979,11 @@ cudaError_t launch_split_pair(const double* Q, int64_t count, float* hi, float* 
   return cudaGetLastError();
 }
 
-bool apply_df_supported(int n) { return n >= 2 && n <= 128; }
+bool apply_df_supported(int n) { return apply_df_supported_d(n); }
 
 cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, int n, const double* P, int64_t rows,
-                            double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s) {
+                            double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s,
+                            const double* Q64, const double* pivot_ratio, unsigned* fallbacks) {
   if (rows <= 0) return cudaSuccess;
   if (!apply_df_supported(n)) return cudaErrorInvalidValue;
   const size_t sm = apply_df_smem(n);
@@ -869,6 +994,7 @@ cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, 
   a.W = W32; a.Qh = Qh; a.Ql = Ql; a.n = n; a.rows = rows; a.P = P;
   if (ps) a.ps = *ps;
   a.out64 = out64; a.out32 = out32; a.status = status;
+  a.Q64 = Q64; a.pivot_ratio = pivot_ratio; a.fallbacks = fallbacks;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 4));
   launch_k(kern, (unsigned)blocks, 256, sm, s, a);
   return cudaGetLastError();

@@ -90,8 +90,11 @@ cudaError_t launch_apply_mixed(const float* W32, const double* Q, int n, const d
                                int iters, double* out64, float* out32, const PartialSum* ps, cudaStream_t s);
 // refined solve with Q as an FP32 pair (n <= 64, even); Q (FP64) -> pair
 bool apply_df_supported(int n);
+// Q64 (FP64 Q), pivot_ratio (from the FP32 inverse) and fallbacks (counter): the
+// FP64 fallback for an ill-conditioned Q (Q64 null = none)
 cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, int n, const double* P, int64_t rows,
-                            double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s);
+                            double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s,
+                            const double* Q64, const double* pivot_ratio, unsigned* fallbacks);
 cudaError_t launch_leverage_dot(const double* G, const double* X, int64_t rows, int n, double* p, cudaStream_t s);
 cudaError_t launch_split_pair(const double* Q, int64_t count, float* hi, float* lo, cudaStream_t s);
 

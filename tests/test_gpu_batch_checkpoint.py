@@ -65,6 +65,46 @@ def test_batch_graph_on_a_stream_equals_individual_updates():
             assert np.array_equal(a.core(n), b.core(n))
 
 
+def test_batch_matches_the_oracle():
+    """Batched updates of uneven order-3 streams (BF16 slabs, FP32 slab
+    arithmetic, one sweep), each against the FP64 oracle's STR (Alg. 4) on the
+    same BF16 values: cores within the FP32 tolerance 1e-5 after three steps,
+    on the default stream and as a captured graph on a side stream."""
+    import torch
+    from oracle import stream as ost
+    p = lib()
+    specs = synth.uneven_streams(count=6, steps=3, seed=11, dim_range=(16, 48), rank_range=(2, 5),
+                                 tnew_range=(1, 6), t_init=12)
+    for on_stream in (False, True):
+        made = []
+        for i, s in enumerate(specs):
+            T = s.t_init + sum(s.t_news)
+            G, X = problem(s.dims, T, s.ranks, 500 + i)
+            X = synth.to_bf16_values(X)
+            init = perturbed_init(G, s.t_init, 600 + i)
+            ctx = p.str_init_cores(init, X0=dev(X[..., :s.t_init], torch.bfloat16), compute="f32", t_capacity=T)
+            made.append((s, X, ctx, ost.str_init(X[..., :s.t_init], init)))
+        t = [s.t_init for s, _, _, _ in made]
+        st = torch.cuda.Stream()
+        for step in range(3):
+            slabs = [dev(X[..., t[i]:t[i] + s.t_news[step]], torch.bfloat16) for i, (s, X, _, _) in enumerate(made)]
+            if on_stream:
+                torch.cuda.synchronize()
+                with torch.cuda.stream(st):
+                    p.str_update_batch([c for _, _, c, _ in made], slabs)
+                st.synchronize()
+            else:
+                p.str_update_batch([c for _, _, c, _ in made], slabs)
+            for i, (s, X, _, ref) in enumerate(made):
+                ost.str_update(ref, X[..., t[i]:t[i] + s.t_news[step]])
+                t[i] += s.t_news[step]
+        for s, X, ctx, ref in made:
+            for n in (1, 2, 3):
+                a, b = ctx.core(n), ref.cores[n - 1]
+                assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+            ctx.close()
+
+
 @pytest.mark.parametrize("sketch", ["none", "leverage", "ksrft"])
 def test_checkpoint_resume_is_bit_identical(sketch):
     p = lib()

@@ -40,11 +40,11 @@ def test_masked_loss_fwd_bwd(dtype_name, tol):
         grads = p.tr_masked_loss_bwd(cores, dev(X, dt), mb, 1.0)
         gref = masked_loss_grad(X, G, mk)
         for n in range(5):
-            assert rel(_abi_to_paper(grads[n], 0, 0), gref[n]) <= tol * 10
+            assert rel(_abi_to_paper(grads[n], 0, 0), gref[n]) <= tol
     cf = closed_form_grad(X, G)
     grads = p.tr_masked_loss_bwd(cores, dev(X, dt), None, 1.0)
     for n in range(5):
-        assert rel(_abi_to_paper(grads[n], 0, 0), cf[n]) <= tol * 10
+        assert rel(_abi_to_paper(grads[n], 0, 0), cf[n]) <= tol
 
 
 def test_autograd_function():
@@ -72,7 +72,7 @@ def test_autograd_function():
     ((40, 40, 3, 3), (2, 8, 2, 2)),
     ((16, 16, 16, 16, 12), (4, 4, 4, 4, 4)),
 ])
-@pytest.mark.parametrize("dtype_name,tol", [("f64", 1e-12), ("f32", 2e-5)])
+@pytest.mark.parametrize("dtype_name,tol", [("f64", 1e-12), ("f32", 1e-5)])
 def test_masked_loss_tiles_and_groups(dims, ranks, dtype_name, tol):
     import torch
     p = lib()
@@ -90,4 +90,4 @@ def test_masked_loss_tiles_and_groups(dims, ranks, dtype_name, tol):
         grads = p.tr_masked_loss_bwd(cores, Xd, mb, 0.5)
         gref = masked_loss_grad(X, G, mk)
         for n in range(len(dims)):
-            assert rel(_abi_to_paper(grads[n], 0, 0), 0.5 * gref[n]) <= tol * 10, n
+            assert rel(_abi_to_paper(grads[n], 0, 0), 0.5 * gref[n]) <= tol, n
