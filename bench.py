@@ -533,8 +533,10 @@ def batch_rows(p, torch, flush, rank, peaks, checks, steps=4, warmup=6, count=25
     (spatial dims in [16,128], TR-ranks in {2..12}, each stream with its own
     number of new slices in 1..16 per step, held for the run), Gaussian cores
     plus noise at 1e-2 relative, initial cores = true cores + 0.05 N(0,1), BF16
-    slabs, FP32 slab-side arithmetic, one sweep.  One str_update_batch per step against one
-    str_update per context per step, same data."""
+    slabs, FP32 slab-side arithmetic, one sweep.  One str_update_batch per step
+    (the work-list launches, one CUDA graph per step) against one str_update per
+    context per step, same data.  Streams whose own update takes the tensor-core
+    MTTKRP differ from the batch (SIMT MTTKRP for every stream) by rounding."""
     specs = synth.uneven_streams(count=count, steps=1, seed=5 + 1000 * rank)
     data, entries, flop, nbytes = [], 0, 0.0, 0
     for i, sp in enumerate(specs):
@@ -580,7 +582,9 @@ def batch_rows(p, torch, flush, rank, peaks, checks, steps=4, warmup=6, count=25
     ms_batch = run(lambda j: p.str_update_batch(ctxs, slabs(j)))
     seq = make()
     ms_seq = run(lambda j: [c.update(x) for c, x in zip(seq, slabs(j))])
-    same = all(np.array_equal(a.core(n), b.core(n)) for a, b in zip(ctxs[:8], seq[:8]) for n in (1, 2, 3))
+    diff = max(float(np.linalg.norm(a.core(n) - b.core(n)) / np.linalg.norm(b.core(n)))
+               for a, b in zip(ctxs, seq) for n in (1, 2, 3))
+    launches = ctxs[0].stats()["kernel_launches"]
     for c in ctxs + seq:
         c.close()
     # accuracy check: one batched update of every stream, fit of the first nchk streams
@@ -598,7 +602,8 @@ def batch_rows(p, torch, flush, rank, peaks, checks, steps=4, warmup=6, count=25
     return {"value": steps * entries / (ms_batch / 1e3), "unit": "entries/s",
             "ms_per_step": ms,
             "sequential": {"value": steps * entries / (ms_seq / 1e3), "ms_per_step": ms_seq / steps},
-            "bit_identical_to_sequential": bool(same),
+            "max_core_rel_diff_vs_sequential": diff,
+            "gpu_launches_per_step": launches,
             "entries_per_step": entries,
             "step": step_roofline(ms, flop, peaks["tf32_tflops"], nbytes, peaks["hbm_gbs"], "tf32"),
             "step_note": "t_bound = max(sum over streams of 2 E sum_n R_n R_{n+1} / TF32 peak, BF16 slabs / HBM)",

@@ -157,14 +157,27 @@ str_status rstr_update(str_ctx* ctx, const str_tensor* X_new, str_sketch type, i
  * str_update_batch -- updates `count` independent contexts with one slab each.
  * randomized = 0: str_update semantics; 1: rstr_update with each context's own
  * sketch settings.  On error no context is changed (sync mode).
- * On a non-default stream (randomized = 0) every context's update runs as one
- * branch, forked from `stream` and joined back to it, so the updates run
- * concurrently; a batch that recurs (same contexts, slab shapes and buffer
- * parities) is captured once into a CUDA graph and replayed.  Slabs are staged
- * at each context's own device address (a device-to-device copy).  On the
- * legacy default stream, or with randomized = 1, the updates run one after
- * another on `stream`.  Results are bit-identical to one str_update (or
- * rstr_update) per context.
+ * Work-list form (randomized = 0, every context of order 3 with FP32 slab
+ * arithmetic, one sweep, R_n R_{n+1} <= 160, not profiling): one fixed sequence
+ * of about 30 launches per step updates every context together, each launch
+ * covering all of them (core Grams, ring products, FP32 inverses, the dense
+ * SIMT MTTKRP, split reductions, refined solves, appends); the sequence is
+ * captured into a CUDA graph when the same batch recurs on a non-default
+ * stream, and the staging chunk and solve rows per block are autotuned once per
+ * shape signature by timing candidates (the first call of a new shape
+ * signature synchronises).  Results are bit-identical to one str_update per
+ * context wherever that update takes the SIMT MTTKRP (FP64 slabs, mttkrp_path
+ * = 1, or slab layouts the tensor-core path does not take); otherwise they
+ * differ by FP32 rounding.  Status words of all contexts are read with one
+ * synchronisation per call.
+ * Otherwise, on a non-default stream every context's update runs as one branch,
+ * forked from `stream` and joined back to it, so the updates run concurrently;
+ * for randomized = 0 a batch that recurs (same contexts, slab shapes and buffer
+ * parities) is captured once into a CUDA graph and replayed (rSTR steps take
+ * the step number as a launch argument and are not captured).  Slabs are
+ * staged at each context's own device address (a device-to-device copy).  On
+ * the legacy default stream the updates run one after another on `stream`.
+ * These forms are bit-identical to one str_update (or rstr_update) per context.
  */
 str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X_new, int count,
                             int randomized, void* stream);

@@ -1757,17 +1757,695 @@ str_status ensure_bstream(str_ctx* c) {
 }
 
 // every context's step on its own branch stream: all forked from the same point
-// of s, all joined back to s after the last one is enqueued
-str_status batch_steps(str_ctx* const* ctxs, std::vector<SlabView>& v, int count, cudaStream_t s) {
+// of s, all joined back to s after the last one is enqueued (rSTR steps append
+// their own rows)
+str_status batch_steps(str_ctx* const* ctxs, std::vector<SlabView>& v, int count, cudaStream_t s,
+                       bool randomized = false) {
   for (int i = 0; i < count; ++i) STR_CUDA_TRY(cudaEventRecord(ctxs[i]->ev_bfork, s));
   for (int i = 0; i < count; ++i) {
     str_ctx* c = ctxs[i];
     STR_CUDA_TRY(wait_event(c->bstream, c->ev_bfork));
-    TRY(str_step(c, v[i], c->bstream));
+    TRY(randomized ? rstr_step(c, v[i], c->bstream) : str_step(c, v[i], c->bstream));
     STR_CUDA_TRY(cudaEventRecord(c->ev_bjoin, c->bstream));
   }
   for (int i = 0; i < count; ++i) STR_CUDA_TRY(wait_event(s, ctxs[i]->ev_bjoin));
   return STR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Work-list batches: order-3 streams with FP32 slab arithmetic and one sweep
+// are updated together by one fixed sequence of launches per step, each
+// covering every stream (blocks walk a device list of (stream, tile) items).
+// Per mode: core Gram, ring product, FP32 sweep inverse, dense MTTKRP (one
+// launch per register-block class), split reduction, refined solve.  The
+// per-stream arithmetic is that of str_step (same kernel bodies, same split
+// plans and reduction orders), so the results equal one str_update per stream
+// wherever str_step would take the SIMT MTTKRP.  Job lists are built once per
+// batch layout (contexts, slab shapes, buffer parities and generations) and
+// the sequence is captured into a CUDA graph when the layout recurs; only the
+// slab pointers and the append destinations are uploaded per step.  The
+// staging chunk of the MTTKRP and the rows per block of the refined solve are
+// chosen per shape signature by timing candidates on the layout's first step
+// (neither changes the arithmetic).
+// ---------------------------------------------------------------------------
+struct WLTune {
+  int bk = 32;                   // fibres staged per MTTKRP chunk (upper limit; reduced to fit shared memory)
+  int rows_per_block = 4;        // refined-solve rows per block
+};
+
+enum WLKind { WL_GRAM, WL_GEMM, WL_SWEEP, WL_MTTKRP, WL_REDUCE, WL_APPLY, WL_REFINE, WL_COPY };
+
+struct WLLaunch {
+  WLKind kind;
+  size_t jobs = 0, items = 0;    // byte offsets in the arena
+  int n = 0;                     // items (or jobs for the sweep)
+  int p0 = 0, p1 = 0, p2 = 0;    // Kmax | (cls, xtype, BK) | nmax
+  size_t smem = 0;
+};
+
+struct WLLayout {
+  int dev = 0;
+  std::vector<uint64_t> uids;
+  std::vector<int64_t> tns;
+  std::vector<int> xtypes, parity;
+  std::vector<uint64_t> gens;
+  WLTune tune;
+  char* arena = nullptr;          // device: static jobs and items, then the per-step region
+  size_t dyn_off = 0, dyn_bytes = 0, xptr_off = 0, copyjob_off = 0, status_off = 0, statusptr_off = 0;
+  std::vector<WLLaunch> launches;
+  std::vector<char> dyn;          // host image of the per-step region
+  int* h_status = nullptr;        // pinned, one word per context
+  cudaGraphExec_t exec = nullptr;
+  int runs = 0;
+};
+
+std::mutex g_wl_mu;
+std::vector<WLLayout*> g_wl;
+struct WLTuned { uint64_t sig; WLTune tune; };
+std::vector<WLTuned> g_wl_tuned;
+
+void wl_free(WLLayout* L) {
+  if (L->exec) cudaGraphExecDestroy(L->exec);
+  if (L->arena) cudaFree(L->arena);
+  if (L->h_status) cudaFreeHost(L->h_status);
+  delete L;
+}
+
+void forget_wl_layouts(uint64_t uid) {
+  std::lock_guard<std::mutex> lk(g_wl_mu);
+  for (size_t i = 0; i < g_wl.size();) {
+    if (std::find(g_wl[i]->uids.begin(), g_wl[i]->uids.end(), uid) != g_wl[i]->uids.end()) {
+      wl_free(g_wl[i]);
+      g_wl.erase(g_wl.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+bool wl_eligible(const str_ctx* c, const SlabView& v) {
+  if (c->N != 3 || c->compute != 1 || c->opt.sweeps != 1 || c->opt.profile) return false;
+  if (v.xtype != XT_BF16 && v.xtype != XT_F32 && v.xtype != XT_F64) return false;
+  for (int k = 0; k < 3; ++k)
+    if (c->RR(k) > 160) return false;
+  return true;
+}
+
+// shape signature of a batch (what the tuned choice depends on)
+uint64_t wl_signature(str_ctx* const* ctxs, const std::vector<int64_t>& tns, const std::vector<SlabView>& v,
+                      int count) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) {
+    for (int b = 0; b < 8; ++b) { h ^= (x >> (8 * b)) & 0xff; h *= 1099511628211ull; }
+  };
+  for (int i = 0; i < count; ++i) {
+    const str_ctx* c = ctxs[i];
+    mix((uint64_t)c->I[0]); mix((uint64_t)c->I[1]); mix((uint64_t)tns[i]); mix((uint64_t)v[i].xtype);
+    for (int k = 0; k < 3; ++k) mix((uint64_t)c->R[k]);
+  }
+  return h;
+}
+
+// dense MTTKRP arguments of mode n of a three-way stream, as mttkrp_into forms them
+MttkrpArgs wl_mttkrp_args(str_ctx* c, const SlabView& v, int n, const void* const* cores) {
+  MttkrpArgs a;
+  a.X = v.X;
+  a.xtype = v.xtype;
+  a.N = 3;
+  a.n = n;
+  for (int k = 0; k < 3; ++k) { a.dim[k] = v.dim[k]; a.core[k] = cores[k]; }
+  for (int k = 0; k <= 3; ++k) a.R[k] = c->R[k];
+  a.compute = 1;
+  int64_t J = 1;
+  for (int k = 0; k < 3; ++k) if (k != n) J *= v.dim[k];
+  a.nfib = J;
+  a.wscale = 1.0;
+  int64_t per = 0;
+  a.splits = mttkrp_plan_splits(a, &per);
+  a.fib_per_split = per;
+  a.partial = c->partial.p;
+  return a;
+}
+
+// per-context scratch of a work-list step (the buffers str_step uses)
+str_status wl_grow(str_ctx* c, const SlabView& v) {
+  const int64_t tn = v.dim[2];
+  const int RR0 = c->RR(0), RR1 = c->RR(1), RR2 = c->RR(2);
+  TRY(grow(c, c->gnew64, (size_t)tn * RR2 * 8));
+  TRY(grow(c, c->gnew32, (size_t)tn * RR2 * 4));
+  TRY(grow(c, c->enew, (size_t)RR2 * RR2 * 8));
+  TRY(grow(c, c->mtmp, (size_t)tn * RR2 * 8));
+  TRY(grow(c, c->qtmp, (size_t)RR2 * RR2 * 8));
+  const int RRm = std::max(RR0, std::max(RR1, RR2));
+  TRY(grow(c, c->lfac, (size_t)RRm * RRm * 8));
+  TRY(grow(c, c->qf, (size_t)RRm * RRm * 4));
+  TRY(grow(c, c->qlo, (size_t)RRm * RRm * 4));
+  // the largest split-partial buffer of the three MTTKRPs
+  size_t part = 0;
+  const void* cores[3] = {nullptr, nullptr, nullptr};
+  for (int n = 0; n < 3; ++n) {
+    MttkrpArgs a = wl_mttkrp_args(c, v, n, cores);
+    part = std::max(part, (size_t)a.splits * v.dim[n] * c->RR(n) * 4);
+  }
+  TRY(grow(c, c->partial, part));
+  return STR_OK;
+}
+
+// Builds the job lists of one step for every context and uploads them.
+str_status wl_build(WLLayout* L, str_ctx* const* ctxs, const std::vector<SlabView>& v, int count) {
+  std::vector<char> img;
+  auto put = [&](const void* p, size_t bytes) -> size_t {
+    size_t off = (img.size() + 255) & ~(size_t)255;
+    img.resize(off + bytes);
+    if (bytes) std::memcpy(img.data() + off, p, bytes);
+    return off;
+  };
+  L->launches.clear();
+  auto add_gram = [&](const std::vector<GramJob>& jobs) {
+    std::vector<int2> items;
+    for (int j = 0; j < (int)jobs.size(); ++j)
+      for (int b = 0; b < core_gram_blocks(jobs[j].Ra * jobs[j].Rb); ++b) items.push_back(make_int2(j, b));
+    WLLaunch l{WL_GRAM};
+    l.jobs = put(jobs.data(), jobs.size() * sizeof(GramJob));
+    l.items = put(items.data(), items.size() * sizeof(int2));
+    l.n = (int)items.size();
+    L->launches.push_back(l);
+  };
+  auto add_gemm = [&](const std::vector<GemmJob>& jobs) {
+    std::vector<int4> items;
+    int Kmax = 1;
+    for (int j = 0; j < (int)jobs.size(); ++j) {
+      Kmax = std::max(Kmax, jobs[j].K);
+      for (int by = 0; by < ceil_div_i(jobs[j].M, 8); ++by)
+        for (int bx = 0; bx < ceil_div_i(jobs[j].N, 8); ++bx) items.push_back(make_int4(j, bx, by, 0));
+    }
+    WLLaunch l{WL_GEMM};
+    l.jobs = put(jobs.data(), jobs.size() * sizeof(GemmJob));
+    l.items = put(items.data(), items.size() * sizeof(int4));
+    l.n = (int)items.size();
+    l.p0 = Kmax;
+    L->launches.push_back(l);
+  };
+  auto add_sweep = [&](const std::vector<SweepJob>& jobs) {
+    WLLaunch l{WL_SWEEP};
+    l.jobs = put(jobs.data(), jobs.size() * sizeof(SweepJob));
+    l.n = (int)jobs.size();
+    L->launches.push_back(l);
+  };
+  // MTTKRPs grouped by register-block class; reduction into out (+ base)
+  auto add_mttkrp = [&](const std::vector<MttkrpArgs>& jobs, const std::vector<int>& stream_of,
+                        const std::vector<double*>& outs, const std::vector<const double*>& bases) {
+    for (int cls = 0; cls < 6; ++cls) {
+      std::vector<MttkrpArgs> cj;
+      std::vector<int4> items;
+      int BK = L->tune.bk;
+      size_t smem = 0;
+      for (int j = 0; j < (int)jobs.size(); ++j) {
+        if (mttkrp_class(jobs[j]) != cls) continue;
+        while (BK > 4 && mttkrp_smem_bytes(jobs[j], BK) > 96 * 1024) BK /= 2;
+      }
+      for (int j = 0; j < (int)jobs.size(); ++j) {
+        if (mttkrp_class(jobs[j]) != cls) continue;
+        const int ji = (int)cj.size();
+        cj.push_back(jobs[j]);
+        smem = std::max(smem, mttkrp_smem_bytes(jobs[j], BK));
+        const int gx = ceil_div_i(jobs[j].dim[jobs[j].n], mttkrp_rows_per_block(jobs[j]));
+        for (int by = 0; by < jobs[j].splits; ++by)
+          for (int bx = 0; bx < gx; ++bx) items.push_back(make_int4(ji, bx, by, stream_of[j]));
+      }
+      if (cj.empty()) continue;
+      WLLaunch l{WL_MTTKRP};
+      l.jobs = put(cj.data(), cj.size() * sizeof(MttkrpArgs));
+      l.items = put(items.data(), items.size() * sizeof(int4));
+      l.n = (int)items.size();
+      l.p0 = cls;
+      l.p1 = v[0].xtype;
+      l.p2 = BK;
+      l.smem = smem;
+      L->launches.push_back(l);
+    }
+    std::vector<ReduceJob> rj;
+    std::vector<int2> items;
+    for (int j = 0; j < (int)jobs.size(); ++j) {
+      ReduceJob r;
+      r.partial = (const float*)jobs[j].partial;
+      r.splits = jobs[j].splits;
+      r.count = jobs[j].dim[jobs[j].n] * jobs[j].R[jobs[j].n] * jobs[j].R[jobs[j].n + 1];
+      r.base = bases[j];
+      r.out = outs[j];
+      for (int64_t b = 0; b < (r.count + 255) / 256; ++b) items.push_back(make_int2(j, (int)b));
+      rj.push_back(r);
+    }
+    WLLaunch l{WL_REDUCE};
+    l.jobs = put(rj.data(), rj.size() * sizeof(ReduceJob));
+    l.items = put(items.data(), items.size() * sizeof(int2));
+    l.n = (int)items.size();
+    L->launches.push_back(l);
+  };
+  auto add_apply = [&](const std::vector<ApplyDF>& jobs) {
+    // orders 129..160: the FP32 inverse with an FP64 residual (as apply_q)
+    {
+      std::vector<RefineJob> rj;
+      std::vector<int4> items;
+      int nmax = 129;
+      size_t smem = 0;
+      for (const ApplyDF& a : jobs) {
+        if (apply_df_supported(a.n)) continue;
+        RefineJob r;
+        r.W = a.W; r.Q = a.Q64; r.n = a.n; r.P = a.P; r.rows = a.rows; r.iters = 1;
+        r.q_in_smem = refine_q_in_smem(a.n);
+        r.out64 = a.out64; r.out32 = a.out32;
+        const int ji = (int)rj.size();
+        rj.push_back(r);
+        nmax = std::max(nmax, a.n);
+        smem = std::max(smem, refine_smem(a.n, r.q_in_smem));
+        const int64_t nb = std::max<int64_t>(1, (a.rows + L->tune.rows_per_block - 1) / L->tune.rows_per_block);
+        for (int64_t b = 0; b < nb; ++b) items.push_back(make_int4(ji, (int)b, (int)nb, 0));
+      }
+      if (!rj.empty()) {
+        WLLaunch l{WL_REFINE};
+        l.jobs = put(rj.data(), rj.size() * sizeof(RefineJob));
+        l.items = put(items.data(), items.size() * sizeof(int4));
+        l.n = (int)items.size();
+        l.p0 = nmax;
+        l.smem = smem;
+        L->launches.push_back(l);
+      }
+    }
+    for (int cpt = 1; cpt <= 2; ++cpt) {
+      std::vector<ApplyDF> cj;
+      std::vector<int4> items;
+      int nmax = 2;
+      for (const ApplyDF& a : jobs) {
+        if (!apply_df_supported(a.n) || (a.n <= 64 ? 1 : 2) != cpt) continue;
+        const int ji = (int)cj.size();
+        cj.push_back(a);
+        nmax = std::max(nmax, a.n);
+        const int64_t nb = std::max<int64_t>(1, (a.rows + L->tune.rows_per_block - 1) / L->tune.rows_per_block);
+        for (int64_t b = 0; b < nb; ++b) items.push_back(make_int4(ji, (int)b, (int)nb, 0));
+      }
+      if (cj.empty()) continue;
+      WLLaunch l{WL_APPLY};
+      l.jobs = put(cj.data(), cj.size() * sizeof(ApplyDF));
+      l.items = put(items.data(), items.size() * sizeof(int4));
+      l.n = (int)items.size();
+      l.p0 = nmax;
+      L->launches.push_back(l);
+    }
+  };
+  auto apply_job = [&](str_ctx* c, const double* Q, int n, const double* P, int64_t rows, double* o64, float* o32) {
+    ApplyDF a;
+    a.W = (const float*)c->lfac.p;
+    a.Qh = (const float*)c->qf.p;
+    a.Ql = (const float*)c->qlo.p;
+    a.n = n;
+    a.rows = rows;
+    a.P = P;
+    a.out64 = o64;
+    a.out32 = o32;
+    a.status = c->d_status;
+    a.Q64 = Q;
+    a.pivot_ratio = c->d_pivot;
+    a.fallbacks = c->d_fallbacks;
+    return a;
+  };
+  auto sweep_job = [&](str_ctx* c, const double* Q, int n) {
+    SweepJob sj;
+    sj.Q = Q;
+    sj.n = n;
+    sj.W = (float*)c->lfac.p;
+    sj.status = c->d_status;
+    sj.pivot_ratio = c->d_pivot;
+    return sj;
+  };
+  auto gemm_job = [&](str_ctx* c, const double* A, const double* B, double* C, int M, int K, int N, int pRa, int pRb,
+                      const double* base) {
+    GemmJob g;
+    g.A = A; g.B = B; g.C = C; g.M = M; g.K = K; g.N = N; g.pRa = pRa; g.pRb = pRb; g.base = base;
+    g.Qf = (float*)c->qf.p;
+    g.Qlo = (float*)c->qlo.p;
+    return g;
+  };
+  auto gram_job = [&](const double* G, int64_t I, int Ra, int Rb, double* E) {
+    GramJob g;
+    g.G = G; g.I = I; g.Ra = Ra; g.Rb = Rb; g.E = E;
+    g.chunk = core_gram_chunk(I, Ra * Rb);
+    return g;
+  };
+  std::vector<int> stream_of(count);
+  for (int i = 0; i < count; ++i) stream_of[i] = i;
+  // ---- temporal mode (Alg. 4): Q_N = ring(E_1 E_2), M_N, G_N^new = M_N Q_N^{-1} ----
+  {
+    std::vector<GemmJob> gj;
+    std::vector<SweepJob> sj;
+    std::vector<MttkrpArgs> mj;
+    std::vector<double*> outs;
+    std::vector<const double*> bases;
+    std::vector<ApplyDF> aj;
+    for (int i = 0; i < count; ++i) {
+      str_ctx* c = ctxs[i];
+      const int* R = c->R;
+      gj.push_back(gemm_job(c, E_of(c, 0), E_of(c, 1), (double*)c->qtmp.p, R[0] * R[0], R[1] * R[1], R[2] * R[2],
+                            R[2], R[0], nullptr));
+      sj.push_back(sweep_job(c, (const double*)c->qtmp.p, c->RR(2)));
+      const void* cores[3] = {core_c(c, 0), core_c(c, 1), nullptr};
+      mj.push_back(wl_mttkrp_args(c, v[i], 2, cores));
+      outs.push_back((double*)c->mtmp.p);
+      bases.push_back(nullptr);
+      aj.push_back(apply_job(c, (const double*)c->qtmp.p, c->RR(2), (const double*)c->mtmp.p, v[i].dim[2],
+                             (double*)c->gnew64.p, (float*)c->gnew32.p));
+    }
+    add_gemm(gj);
+    add_sweep(sj);
+    add_mttkrp(mj, stream_of, outs, bases);
+    add_apply(aj);
+  }
+  // ---- spatial modes n = 1, 2 (Gauss-Seidel): Gram of the core updated just before,
+  //      Q_n = Q_n^old + ring, P_n = P_n^old + MTTKRP, G_n = P_n Q_n^{-1} ----
+  for (int n = 0; n < 2; ++n) {
+    std::vector<GramJob> grj;
+    std::vector<GemmJob> gj;
+    std::vector<SweepJob> sj;
+    std::vector<MttkrpArgs> mj;
+    std::vector<double*> outs;
+    std::vector<const double*> bases;
+    std::vector<ApplyDF> aj;
+    for (int i = 0; i < count; ++i) {
+      str_ctx* c = ctxs[i];
+      const int* R = c->R;
+      const int w = 1 - c->cur[n];
+      if (n == 0) {
+        grj.push_back(gram_job((const double*)c->gnew64.p, v[i].dim[2], R[2], R[0], (double*)c->enew.p));
+        gj.push_back(gemm_job(c, E_of(c, 1), (const double*)c->enew.p, c->Q[0][w], R[1] * R[1], R[2] * R[2],
+                              R[0] * R[0], R[0], R[1], c->Q[0][c->cur[0]]));
+      } else {
+        const int w0 = 1 - c->cur[0];
+        grj.push_back(gram_job(c->G64[0][w0], c->I[0], R[0], R[1], c->E[0][w0]));
+        gj.push_back(gemm_job(c, (const double*)c->enew.p, c->E[0][w0], c->Q[1][w], R[2] * R[2], R[0] * R[0],
+                              R[1] * R[1], R[1], R[2], c->Q[1][c->cur[1]]));
+      }
+      sj.push_back(sweep_job(c, c->Q[n][w], c->RR(n)));
+      const void* cores[3];
+      if (n == 0) { cores[0] = c->G32[0][c->cur[0]]; cores[1] = c->G32[1][c->cur[1]]; }
+      else { cores[0] = c->G32[0][1 - c->cur[0]]; cores[1] = c->G32[1][c->cur[1]]; }
+      cores[2] = c->gnew32.p;
+      mj.push_back(wl_mttkrp_args(c, v[i], n, cores));
+      outs.push_back(c->P[n][w]);
+      bases.push_back(c->P[n][c->cur[n]]);
+      aj.push_back(apply_job(c, c->Q[n][w], c->RR(n), c->P[n][w], c->I[n], c->G64[n][w], c->G32[n][w]));
+    }
+    add_gram(grj);
+    add_gemm(gj);
+    add_sweep(sj);
+    add_mttkrp(mj, stream_of, outs, bases);
+    add_apply(aj);
+  }
+  // ---- Gram of the last core updated (kept with the committed state) ----
+  {
+    std::vector<GramJob> grj;
+    for (int i = 0; i < count; ++i) {
+      str_ctx* c = ctxs[i];
+      const int w1 = 1 - c->cur[1];
+      grj.push_back(gram_job(c->G64[1][w1], c->I[1], c->R[1], c->R[2], c->E[1][w1]));
+    }
+    add_gram(grj);
+  }
+  // ---- append the new temporal rows (copy jobs are per step: the destination moves) ----
+  {
+    std::vector<int2> items;
+    for (int i = 0; i < count; ++i) {
+      const int64_t b64 = v[i].dim[2] * ctxs[i]->RR(2) * 8, b32 = b64 / 2;
+      for (int64_t b = 0; b < (b64 + 16383) / 16384; ++b) items.push_back(make_int2(2 * i, (int)b));
+      for (int64_t b = 0; b < (b32 + 16383) / 16384; ++b) items.push_back(make_int2(2 * i + 1, (int)b));
+    }
+    WLLaunch l{WL_COPY};
+    l.items = put(items.data(), items.size() * sizeof(int2));
+    l.n = (int)items.size();
+    L->launches.push_back(l);
+  }
+  // status pointers (for one gathered read of every context's status word)
+  {
+    std::vector<const int*> sp(count);
+    for (int i = 0; i < count; ++i) sp[i] = ctxs[i]->d_status;
+    L->statusptr_off = put(sp.data(), sp.size() * sizeof(const int*));
+    std::vector<int> zero(count, 0);
+    L->status_off = put(zero.data(), zero.size() * sizeof(int));
+  }
+  // per-step region: slab pointers, then the append copy jobs
+  L->dyn_off = (img.size() + 255) & ~(size_t)255;
+  L->xptr_off = L->dyn_off;
+  L->copyjob_off = L->dyn_off + (((size_t)count * sizeof(void*) + 255) & ~(size_t)255);
+  L->dyn_bytes = L->copyjob_off - L->dyn_off + (size_t)2 * count * sizeof(CopyJob);
+  img.resize(L->dyn_off + L->dyn_bytes);
+  L->dyn.assign(L->dyn_bytes, 0);
+  if (L->arena) cudaFree(L->arena);
+  L->arena = nullptr;
+  cudaError_t e = cudaMalloc(&L->arena, img.size());
+  if (e != cudaSuccess) { cudaGetLastError(); return from_cuda(e, "cudaMalloc(work list)"); }
+  STR_CUDA_TRY(cudaMemcpy(L->arena, img.data(), img.size(), cudaMemcpyHostToDevice));
+  if (!L->h_status) STR_CUDA_TRY(cudaMallocHost(&L->h_status, (size_t)count * sizeof(int)));
+  return STR_OK;
+}
+
+// the step's launches (no host work besides the launches)
+str_status wl_launch(WLLayout* L, cudaStream_t s) {
+  char* A = L->arena;
+  const void* const* xptrs = (const void* const*)(A + L->xptr_off);
+  for (const WLLaunch& l : L->launches) {
+    switch (l.kind) {
+      case WL_GRAM: STR_CUDA_TRY(launch_core_gram_batch((const GramJob*)(A + l.jobs), (const int2*)(A + l.items), l.n, s)); break;
+      case WL_GEMM: STR_CUDA_TRY(launch_gemm64_batch((const GemmJob*)(A + l.jobs), (const int4*)(A + l.items), l.n, l.p0, s)); break;
+      case WL_SWEEP: STR_CUDA_TRY(launch_sweep_batch((const SweepJob*)(A + l.jobs), l.n, s)); break;
+      case WL_MTTKRP:
+        STR_CUDA_TRY(launch_mttkrp_batch((const MttkrpArgs*)(A + l.jobs), (const int4*)(A + l.items), xptrs, l.n, l.p0,
+                                         l.p1, l.p2, l.smem, s));
+        break;
+      case WL_REDUCE: STR_CUDA_TRY(launch_reduce_batch((const ReduceJob*)(A + l.jobs), (const int2*)(A + l.items), l.n, s)); break;
+      case WL_APPLY: STR_CUDA_TRY(launch_apply_df_batch((const ApplyDF*)(A + l.jobs), (const int4*)(A + l.items), l.n, l.p0, s)); break;
+      case WL_REFINE:
+        STR_CUDA_TRY(launch_refine_batch((const RefineJob*)(A + l.jobs), (const int4*)(A + l.items), l.n, l.p0, l.smem, s));
+        break;
+      case WL_COPY: STR_CUDA_TRY(launch_copy_batch((const CopyJob*)(A + L->copyjob_off), (const int2*)(A + l.items), l.n, s)); break;
+    }
+  }
+  return STR_OK;
+}
+
+// the per-step region: this step's slab pointers and append destinations
+str_status wl_upload(WLLayout* L, str_ctx* const* ctxs, const std::vector<SlabView>& v, int count, cudaStream_t s) {
+  const void** xp = (const void**)L->dyn.data();
+  CopyJob* cj = (CopyJob*)(L->dyn.data() + (L->copyjob_off - L->dyn_off));
+  for (int i = 0; i < count; ++i) {
+    str_ctx* c = ctxs[i];
+    const int RRN = c->RR(2);
+    const int64_t tn = v[i].dim[2];
+    xp[i] = v[i].X;
+    cj[2 * i].src = c->gnew64.p;
+    cj[2 * i].dst = c->GT64 + c->t_rows * RRN;
+    cj[2 * i].bytes = tn * RRN * 8;
+    cj[2 * i + 1].src = c->gnew32.p;
+    cj[2 * i + 1].dst = c->GT32 + c->t_rows * RRN;
+    cj[2 * i + 1].bytes = tn * RRN * 4;
+  }
+  // pageable source: staged by the call, so the host image can be rewritten next step
+  STR_CUDA_TRY(cudaMemcpyAsync(L->arena + L->dyn_off, L->dyn.data(), L->dyn_bytes, cudaMemcpyHostToDevice, s));
+  return STR_OK;
+}
+
+// the layout of this batch (built, tuned and cached on first use; the caller
+// holds g_wl_mu)
+str_status wl_layout(str_ctx* const* ctxs, const std::vector<int64_t>& tns, const std::vector<SlabView>& v,
+                     int count, cudaStream_t s, WLLayout** out) {
+  for (WLLayout* L : g_wl) {
+    if ((int)L->uids.size() != count || L->dev != ctxs[0]->dev) continue;
+    bool same = true;
+    for (int i = 0; i < count && same; ++i) {
+      const str_ctx* c = ctxs[i];
+      same = L->uids[i] == c->uid && L->tns[i] == tns[i] && L->xtypes[i] == v[i].xtype && L->parity[i] == c->cur[0] &&
+             L->gens[i] == c->gen;
+    }
+    if (same) { *out = L; return STR_OK; }
+  }
+  WLLayout* L = new WLLayout;
+  L->dev = ctxs[0]->dev;
+  for (int i = 0; i < count; ++i) {
+    const str_ctx* c = ctxs[i];
+    L->uids.push_back(c->uid);
+    L->tns.push_back(tns[i]);
+    L->xtypes.push_back(v[i].xtype);
+    L->parity.push_back(c->cur[0]);
+    L->gens.push_back(c->gen);
+  }
+  const uint64_t sig = wl_signature(ctxs, tns, v, count);
+  bool tuned = false;
+  for (const WLTuned& t : g_wl_tuned)
+    if (t.sig == sig) { L->tune = t.tune; tuned = true; }
+  if (!tuned) {
+    // autotune: time every candidate on this step (the step writes working
+    // buffers only, so repeating it leaves the committed state as it was)
+    const int bks[3] = {8, 16, 32};
+    const int rpbs[3] = {1, 4, 16};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    STR_CUDA_TRY(cudaEventCreate(&e0));
+    STR_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    WLTune best_t;
+    str_status st = STR_OK;
+    for (int bi = 0; bi < 3 && st == STR_OK; ++bi)
+      for (int ri = 0; ri < 3 && st == STR_OK; ++ri) {
+        L->tune.bk = bks[bi];
+        L->tune.rows_per_block = rpbs[ri];
+        st = wl_build(L, ctxs, v, count);
+        if (st != STR_OK) break;
+        st = wl_upload(L, ctxs, v, count, s);
+        if (st == STR_OK) st = wl_launch(L, s);           // warm-up
+        if (st == STR_OK && cudaEventRecord(e0, s) != cudaSuccess) st = STR_ERR_CUDA;
+        if (st == STR_OK) st = wl_launch(L, s);
+        if (st == STR_OK && cudaEventRecord(e1, s) != cudaSuccess) st = STR_ERR_CUDA;
+        float ms = 0.f;
+        if (st == STR_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          st = STR_ERR_CUDA;
+        if (st == STR_OK && ms < best) { best = ms; best_t = L->tune; }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != STR_OK) { wl_free(L); return st; }
+    L->tune = best_t;
+    if (g_wl_tuned.size() >= 64) g_wl_tuned.erase(g_wl_tuned.begin());
+    g_wl_tuned.push_back({sig, best_t});
+  }
+  const str_status st = wl_build(L, ctxs, v, count);
+  if (st != STR_OK) { wl_free(L); return st; }
+  if (g_wl.size() >= 16) {   // bounded cache: drop the oldest layout
+    wl_free(g_wl.front());
+    g_wl.erase(g_wl.begin());
+  }
+  g_wl.push_back(L);
+  *out = L;
+  return STR_OK;
+}
+
+// One step of every context by the work-list launches (on any stream; captured
+// and replayed as a graph when the layout recurs on a non-default stream).
+// The caller holds g_wl_mu.
+str_status wl_step(str_ctx* const* ctxs, const std::vector<int64_t>& tns, const std::vector<SlabView>& v, int count,
+                   cudaStream_t s) {
+  for (int i = 0; i < count; ++i) TRY(wl_grow(ctxs[i], v[i]));
+  WLLayout* L = nullptr;
+  TRY(wl_layout(ctxs, tns, v, count, s, &L));
+  TRY(wl_upload(L, ctxs, v, count, s));
+  const bool can_capture = s != nullptr && s != cudaStreamLegacy;
+  if (L->exec) {
+    STR_CUDA_TRY(cudaGraphLaunch(L->exec, s));
+  } else if (can_capture && L->runs >= 1) {
+    cudaGraph_t graph = nullptr;
+    STR_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const str_status st = wl_launch(L, s);
+    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (st != STR_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      if (st != STR_OK) return st;
+      return from_cuda(ce, "cudaStreamEndCapture(work list)");
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&L->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) { L->exec = nullptr; return from_cuda(ie, "cudaGraphInstantiate(work list)"); }
+    STR_CUDA_TRY(cudaGraphLaunch(L->exec, s));
+  } else {
+    TRY(wl_launch(L, s));
+  }
+  L->runs++;
+  for (int i = 0; i < count; ++i) {
+    str_ctx* c = ctxs[i];
+    c->upd[0] = c->upd[1] = 1;
+    for (int k = 0; k < 3; ++k) c->core_ver[k]++;
+    c->qsplit_of = nullptr;
+    c->launches = (int64_t)L->launches.size();
+  }
+  return STR_OK;
+}
+
+// every context's status word in one read (one synchronisation): device pointer
+// list, gathered words and their pinned host copy, grow-only (under g_wl_mu)
+const int** g_wl_sptr = nullptr;
+int* g_wl_sval = nullptr;
+int* g_wl_shost = nullptr;
+int g_wl_scap = 0;
+
+str_status wl_statuses(str_ctx* const* ctxs, int count, cudaStream_t s, std::vector<int>* st) {
+  if (count > g_wl_scap) {
+    if (g_wl_sptr) cudaFree(g_wl_sptr);
+    if (g_wl_sval) cudaFree(g_wl_sval);
+    if (g_wl_shost) cudaFreeHost(g_wl_shost);
+    g_wl_sptr = nullptr; g_wl_sval = nullptr; g_wl_shost = nullptr; g_wl_scap = 0;
+    STR_CUDA_TRY(cudaMalloc((void**)&g_wl_sptr, (size_t)count * sizeof(int*)));
+    STR_CUDA_TRY(cudaMalloc((void**)&g_wl_sval, (size_t)count * sizeof(int)));
+    STR_CUDA_TRY(cudaMallocHost((void**)&g_wl_shost, (size_t)count * sizeof(int)));
+    g_wl_scap = count;
+  }
+  std::vector<const int*> sp(count);
+  for (int i = 0; i < count; ++i) sp[i] = ctxs[i]->d_status;
+  STR_CUDA_TRY(cudaMemcpyAsync(g_wl_sptr, sp.data(), (size_t)count * sizeof(int*), cudaMemcpyHostToDevice, s));
+  STR_CUDA_TRY(launch_gather_ints(g_wl_sptr, count, g_wl_sval, s));
+  STR_CUDA_TRY(cudaMemcpyAsync(g_wl_shost, g_wl_sval, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, s));
+  STR_CUDA_TRY(cudaStreamSynchronize(s));
+  st->assign(g_wl_shost, g_wl_shost + count);
+  return STR_OK;
+}
+
+bool wl_candidates(str_ctx* const* ctxs, int count) {
+  for (int i = 0; i < count; ++i) {
+    const str_ctx* c = ctxs[i];
+    if (!c || c->sticky || c->N != 3 || c->compute != 1 || c->opt.sweeps != 1 || c->opt.profile) return false;
+    for (int k = 0; k < 3; ++k)
+      if (c->RR(k) > 160) return false;
+  }
+  return count > 0;
+}
+
+// str_update_batch for a batch of work-list candidates: all or none committed
+str_status wl_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, int count, cudaStream_t s) {
+  std::vector<SlabView> v(count);
+  std::vector<int64_t> tns(count);
+  for (int i = 0; i < count; ++i) {
+    str_ctx* c = ctxs[i];
+    TRY(take_slab(c, X[i], &v[i], s));
+    tns[i] = v[i].dim[2];
+    if (c->t_rows + tns[i] > c->opt.t_capacity) return STR_ERR_CAPACITY;
+    if (!wl_eligible(c, v[i])) return STR_ERR_DTYPE;
+  }
+  std::lock_guard<std::mutex> lk(g_wl_mu);
+  // a device failure of an earlier step (no-synchronisation contexts) latches the context
+  std::vector<int> st0;
+  TRY(wl_statuses(ctxs, count, s, &st0));
+  for (int i = 0; i < count; ++i)
+    if (st0[i]) { ctxs[i]->sticky = ctxs[i]->opt.async_status ? 1 : 0; return STR_ERR_STATE; }
+  str_status st = wl_step(ctxs, tns, v, count, s);
+  bool sync_any = false;
+  for (int i = 0; i < count; ++i) sync_any = sync_any || !ctxs[i]->opt.async_status;
+  std::vector<int> st1;
+  if (st == STR_OK && sync_any) st = wl_statuses(ctxs, count, s, &st1);
+  bool fail = st != STR_OK;
+  for (int i = 0; i < count && !fail && sync_any; ++i) {
+    if (ctxs[i]->opt.async_status || !st1[i]) continue;
+    fail = true;
+    st = (st1[i] & DEV_ERR_NONFINITE) ? STR_ERR_NONFINITE
+         : (st1[i] & DEV_ERR_SINGULAR) ? STR_ERR_SINGULAR : (st1[i] & DEV_ERR_TIMEOUT) ? STR_ERR_TIMEOUT : STR_ERR_CUDA;
+  }
+  for (int i = 0; i < count; ++i) {
+    str_ctx* c = ctxs[i];
+    if (fail) {
+      for (int k = 0; k < STR_MAXN; ++k) c->upd[k] = 0;
+      cudaMemsetAsync(c->d_status, 0, sizeof(int), s);
+      continue;
+    }
+    for (int k = 0; k < STR_MAXN; ++k) { if (c->upd[k]) c->cur[k] ^= 1; c->upd[k] = 0; }
+    c->t_rows += tns[i];
+    c->last_tn = tns[i];
+    c->step += 1;
+  }
+  return st;
 }
 
 str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, int count, int randomized,
@@ -1775,6 +2453,8 @@ str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, in
   if (!ctxs || !X || count < 0) return STR_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   str_mark_cross_wait(s);   // the caller may have ordered s after other streams
+  for (int i = 0; i < count; ++i) if (!ctxs[i] || !X[i]) return STR_ERR_INVALID_ARG;
+  if (!randomized && wl_candidates(ctxs, count)) return wl_update_batch(ctxs, X, count, s);
   // enqueue every context's step with status checks deferred, then commit all or none
   std::vector<int64_t> tns(count);
   for (int i = 0; i < count; ++i) {
@@ -1785,7 +2465,9 @@ str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, in
   }
   str_status st = STR_OK;
   int done = 0;
-  bool concurrent = !randomized && count > 0 && s != nullptr && s != cudaStreamLegacy;
+  // concurrent branches on a non-default stream; rSTR steps are not captured into
+  // a replayed graph (each step's draws take the step number as a launch argument)
+  bool concurrent = count > 0 && s != nullptr && s != cudaStreamLegacy;
   for (int i = 0; i < count; ++i)
     if (ctxs[i]->opt.profile) concurrent = false;
   if (!concurrent) {
@@ -1825,7 +2507,7 @@ str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, in
             cudaSuccess) { st = STR_ERR_CUDA; break; }
         v[i].X = c->xstage.p;
       }
-      if (!c->opt.graphs) graphs = false;
+      if (!c->opt.graphs || randomized) graphs = false;
       const std::pair<int64_t, int> shape(tns[i], v[i].xtype);
       if (std::find(c->warm.begin(), c->warm.end(), shape) == c->warm.end()) warm = false;
     }
@@ -1910,7 +2592,7 @@ str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, in
         }
       } else {
         lk.unlock();
-        st = batch_steps(ctxs, v, count, s);
+        st = batch_steps(ctxs, v, count, s, randomized != 0);
         for (int i = 0; i < count && st == STR_OK; ++i) {
           const std::pair<int64_t, int> shape(tns[i], v[i].xtype);
           if (std::find(ctxs[i]->warm.begin(), ctxs[i]->warm.end(), shape) == ctxs[i]->warm.end())
@@ -1918,7 +2600,7 @@ str_status str_update_batch(str_ctx* const* ctxs, const str_tensor* const* X, in
         }
       }
     }
-    for (int i = 0; i < done && st == STR_OK; ++i) st = append_rows(ctxs[i], tns[i], s);
+    for (int i = 0; i < done && st == STR_OK && !randomized; ++i) st = append_rows(ctxs[i], tns[i], s);
   }
   bool any_fail = st != STR_OK;
   if (!any_fail) {
@@ -2229,6 +2911,7 @@ void str_destroy(str_ctx* c) {
   for (auto& e : c->pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : c->pool) cudaEventDestroy(e);
   forget_batch_graphs(c->uid);
+  forget_wl_layouts(c->uid);
   if (c->ev_bfork) cudaEventDestroy(c->ev_bfork);
   if (c->ev_bjoin) cudaEventDestroy(c->ev_bjoin);
   if (c->bstream) { str_take_cross_wait(c->bstream); cudaStreamDestroy(c->bstream); }

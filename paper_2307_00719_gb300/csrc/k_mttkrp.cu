@@ -83,9 +83,9 @@ __host__ __device__ inline void smem_offsets(int BK, int BM, int RR, int Rb, int
   o[8] = off;
 }
 
+// row block bx and fibre split by of one MTTKRP
 template <typename T, bool C, typename XS, int RPT, int CPT>
-__global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
-  PDL_ENTRY();
+__device__ __forceinline__ void mttkrp_body(const MttkrpArgs& a, int BK, int64_t bx, int64_t by) {
   typedef typename ElemT<T, C>::type E;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
@@ -115,9 +115,9 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
   E* sT[2] = {(E*)(smem + o[5]), (E*)(smem + o[6])};
   E* sG = (E*)(smem + o[7]);   // slices of the chain cores: [t][jj][R_k R_{k+1}]
 
-  const int64_t f_begin = (int64_t)blockIdx.y * a.fib_per_split;
+  const int64_t f_begin = by * a.fib_per_split;
   const int64_t f_end = min(a.nfib, f_begin + a.fib_per_split);
-  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int64_t row0 = bx * BM;
   const int tx = tid & 15, ty = tid >> 4;
 
   E acc[RPT][CPT];
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
       }
       sBase[tid] = off;
       sW[tid] = (T)w;
-      if (a.ws_out && blockIdx.x == 0) a.ws_out[f] = w;
+      if (a.ws_out && bx == 0) a.ws_out[f] = w;
     }
     __syncthreads();
 
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
       sX[jj * BM + r] = v;
     }
     __syncthreads();
-    if (a.gs_out && blockIdx.x == 0) {
+    if (a.gs_out && bx == 0) {
       E* g = (E*)a.gs_out;
       for (int e = tid; e < nf * RR; e += blockDim.x) g[(f0 + e / RR) * RR + (e % RR)] = sS[e];
     }
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
     }
     __syncthreads();
   }
-  E* out = (E*)a.partial + (size_t)blockIdx.y * In * RR;
+  E* out = (E*)a.partial + (size_t)by * In * RR;
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int64_t row = row0 + ty + 16 * q;
@@ -266,6 +266,31 @@ __global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
       if (row < In && c < RR) out[row * RR + c] = acc[q][p];
     }
   }
+}
+
+template <typename T, bool C, typename XS, int RPT, int CPT>
+__global__ void __launch_bounds__(256) mttkrp_kernel(MttkrpArgs a, int BK) {
+  PDL_ENTRY();
+  mttkrp_body<T, C, XS, RPT, CPT>(a, BK, blockIdx.x, blockIdx.y);
+}
+
+// work list of MTTKRPs of one register-block class: item = (job, row block, split)
+template <typename T, bool C, typename XS, int RPT, int CPT>
+__global__ void __launch_bounds__(256) mttkrp_batch_kernel(const MttkrpArgs* __restrict__ jobs,
+                                                           const int4* __restrict__ items,
+                                                           const void* const* __restrict__ xptrs, int BK) {
+  PDL_ENTRY();
+  __shared__ MttkrpArgs sj;
+  const int4 it = items[blockIdx.x];
+  {
+    const int* src = (const int*)&jobs[it.x];
+    int* dst = (int*)&sj;
+    for (int e = threadIdx.x; e < (int)(sizeof(MttkrpArgs) / sizeof(int)); e += blockDim.x) dst[e] = src[e];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && xptrs) sj.X = xptrs[it.w];   // this step's slab of stream it.w
+  __syncthreads();
+  mttkrp_body<T, C, XS, RPT, CPT>(sj, BK, it.y, it.z);
 }
 
 int plan_rmid(const MttkrpArgs& a) {
@@ -312,7 +337,53 @@ cudaError_t launch_rc(const MttkrpArgs& a, cudaStream_t s) {
   return small_rows ? launch_t<T, C, XS, 1, 10>(a, s) : launch_t<T, C, XS, 4, 10>(a, s);
 }
 
+template <typename XS, int RPT, int CPT>
+cudaError_t launch_batch_t(const MttkrpArgs* jobs, const int4* items, const void* const* xptrs, int nitems, int BK,
+                           size_t smem, cudaStream_t s) {
+  auto kern = mttkrp_batch_kernel<float, false, XS, RPT, CPT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  launch_k(kern, (unsigned)nitems, 256, smem, s, jobs, items, xptrs, BK);
+  return cudaGetLastError();
+}
+
+template <typename XS>
+cudaError_t launch_batch_x(const MttkrpArgs* jobs, const int4* items, const void* const* xptrs, int nitems, int cls,
+                           int BK, size_t smem, cudaStream_t s) {
+  switch (cls) {
+    case 0: return launch_batch_t<XS, 1, 1>(jobs, items, xptrs, nitems, BK, smem, s);
+    case 1: return launch_batch_t<XS, 4, 1>(jobs, items, xptrs, nitems, BK, smem, s);
+    case 2: return launch_batch_t<XS, 1, 4>(jobs, items, xptrs, nitems, BK, smem, s);
+    case 3: return launch_batch_t<XS, 4, 4>(jobs, items, xptrs, nitems, BK, smem, s);
+    case 4: return launch_batch_t<XS, 1, 10>(jobs, items, xptrs, nitems, BK, smem, s);
+    default: return launch_batch_t<XS, 4, 10>(jobs, items, xptrs, nitems, BK, smem, s);
+  }
+}
+
 }  // namespace
+
+// register-block class of launch_rc: 0..5 = (RPT, CPT) in (1,1) (4,1) (1,4) (4,4) (1,10) (4,10)
+int mttkrp_class(const MttkrpArgs& a) {
+  const int RR = a.R[a.n] * a.R[a.n + 1];
+  const bool small_rows = a.dim[a.n] <= 16;
+  const int c = RR <= 16 ? 0 : (RR <= 64 ? 2 : 4);
+  return c + (small_rows ? 0 : 1);
+}
+
+int mttkrp_rows_per_block(const MttkrpArgs& a) { return (mttkrp_class(a) & 1) ? 64 : 16; }
+
+size_t mttkrp_smem_bytes(const MttkrpArgs& a, int BK) { return smem_bytes(a, BK, mttkrp_rows_per_block(a)); }
+
+// FP32 dense (real) jobs only: the batched path of FP32 slab arithmetic
+cudaError_t launch_mttkrp_batch(const MttkrpArgs* jobs, const int4* items, const void* const* xptrs, int nitems,
+                                int cls, int xtype, int BK, size_t smem, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  switch (xtype) {
+    case XT_F64: return launch_batch_x<double>(jobs, items, xptrs, nitems, cls, BK, smem, s);
+    case XT_F32: return launch_batch_x<float>(jobs, items, xptrs, nitems, cls, BK, smem, s);
+    default: return launch_batch_x<__nv_bfloat16>(jobs, items, xptrs, nitems, cls, BK, smem, s);
+  }
+}
 
 int mttkrp_plan_splits(const MttkrpArgs& a, int64_t* fib_per_split) {
   const int BM = a.dim[a.n] <= 16 ? 16 : 64;
@@ -354,15 +425,15 @@ cudaError_t launch_mttkrp(const MttkrpArgs& a, cudaStream_t s) {
 // groups each sum the splits g, g+16, g+32, ... and the 16 group sums are then
 // added in group order -- the same order on every run (no atomics).
 // ---------------------------------------------------------------------------
+// outputs 16 bx .. 16 bx + 15
 template <typename T, bool CPLX>
-__global__ void __launch_bounds__(256) reduce_kernel(const T* __restrict__ partial, int splits,
-                                                     int64_t count, const double* __restrict__ base,
-                                                     double scale, double* __restrict__ out) {
-  PDL_ENTRY();
+__device__ __forceinline__ void reduce_body(const T* __restrict__ partial, int splits, int64_t count,
+                                            const double* __restrict__ base, double scale,
+                                            double* __restrict__ out, int64_t bx) {
   constexpr int W = CPLX ? 2 : 1;
   __shared__ double red[16][16 * W];
   const int o = threadIdx.x & 15, g = threadIdx.x >> 4;
-  const int64_t i = (int64_t)blockIdx.x * 16 + o;
+  const int64_t i = bx * 16 + o;
   double acc[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) acc[w] = 0.0;
@@ -384,6 +455,77 @@ __global__ void __launch_bounds__(256) reduce_kernel(const T* __restrict__ parti
       else out[i] = (base ? base[i] : 0.0) + scale * sum;
     }
   }
+}
+
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(256) reduce_kernel(const T* __restrict__ partial, int splits,
+                                                     int64_t count, const double* __restrict__ base,
+                                                     double scale, double* __restrict__ out) {
+  PDL_ENTRY();
+  reduce_body<T, CPLX>(partial, splits, count, base, scale, out, blockIdx.x);
+}
+
+// work list of split reductions: item = (job, block of 256 outputs), one thread
+// per output.  The thread forms reduce_body's sum in reduce_body's order: group
+// g sums the splits g, g + 16, ... in FP64, then the 16 group sums are added in
+// group order (the same FP64 operations, so the same result)
+__global__ void __launch_bounds__(256) reduce_batch_kernel(const ReduceJob* __restrict__ jobs,
+                                                           const int2* __restrict__ items) {
+  PDL_ENTRY();
+  const int2 it = items[blockIdx.x];
+  const ReduceJob j = jobs[it.x];
+  const int64_t i = (int64_t)it.y * 256 + threadIdx.x;
+  if (i >= j.count) return;
+  double sum = 0.0;
+  for (int g = 0; g < 16; ++g) {
+    double acc = 0.0;
+    for (int k = g; k < j.splits; k += 16) acc += (double)j.partial[(int64_t)k * j.count + i];
+    sum += acc;
+  }
+  j.out[i] = (j.base ? j.base[i] : 0.0) + 1.0 * sum;
+}
+
+// work list of copies: item = (job, 16 KB chunk)
+__global__ void __launch_bounds__(256) copy_batch_kernel(const CopyJob* __restrict__ jobs,
+                                                         const int2* __restrict__ items) {
+  PDL_ENTRY();
+  const int2 it = items[blockIdx.x];
+  const CopyJob j = jobs[it.x];
+  const int64_t b0 = (int64_t)it.y * 16384, b1 = min(j.bytes, b0 + 16384);
+  const bool v16 = ((((uintptr_t)j.src) | ((uintptr_t)j.dst)) & 15) == 0 && (j.bytes & 15) == 0;
+  if (v16) {
+    const uint4* s4 = (const uint4*)j.src;
+    uint4* d4 = (uint4*)j.dst;
+    for (int64_t e = (b0 >> 4) + threadIdx.x; e < (b1 >> 4); e += blockDim.x) d4[e] = s4[e];
+  } else {
+    const unsigned char* s1 = (const unsigned char*)j.src;
+    unsigned char* d1 = (unsigned char*)j.dst;
+    for (int64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) d1[e] = s1[e];
+  }
+}
+
+// out[i] = *ptrs[i]: the status words of many contexts in one array
+__global__ void gather_ints_kernel(const int* const* __restrict__ ptrs, int n, int* __restrict__ out) {
+  PDL_ENTRY();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = *ptrs[i];
+}
+
+cudaError_t launch_gather_ints(const int* const* ptrs, int n, int* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  launch_k(gather_ints_kernel, (unsigned)std::min(64, (n + 255) / 256), 256, 0, s, ptrs, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_batch(const ReduceJob* jobs, const int2* items, int nitems, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  launch_k(reduce_batch_kernel, (unsigned)nitems, 256, 0, s, jobs, items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_batch(const CopyJob* jobs, const int2* items, int nitems, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  launch_k(copy_batch_kernel, (unsigned)nitems, 256, 0, s, jobs, items);
+  return cudaGetLastError();
 }
 
 static unsigned grid_for(int64_t count) {

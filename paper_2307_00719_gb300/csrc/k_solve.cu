@@ -17,16 +17,16 @@
 // are staged in shared memory in chunks (cp.async), so the FMA chains read
 // shared memory.  Writes both halves.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) core_gram_kernel(const double* __restrict__ G, int64_t I, int Ra,
-                                                        int Rb, double* __restrict__ M,
-                                                        double* __restrict__ E, int chunk) {
-  PDL_ENTRY();
+// pairs 64 bx .. 64 bx + 63 of the upper triangle (bx: the block's index)
+__device__ __forceinline__ void core_gram_body(const double* __restrict__ G, int64_t I, int Ra, int Rb,
+                                               double* __restrict__ M, double* __restrict__ E, int chunk,
+                                               int64_t bx) {
   extern __shared__ __align__(16) double sg[];   // chunk x RR
   __shared__ double red[4][64];
   const int RR = Ra * Rb;
   const int64_t npairs = (int64_t)RR * (RR + 1) / 2;
   const int p = threadIdx.x & 63, q = threadIdx.x >> 6;
-  const int64_t t = (int64_t)blockIdx.x * 64 + p;
+  const int64_t t = bx * 64 + p;
   int c = 0, cp = 0;
   if (t < npairs) {
     // row c of the upper triangle starts at c RR - c (c - 1) / 2
@@ -75,6 +75,22 @@ __global__ void __launch_bounds__(256) core_gram_kernel(const double* __restrict
   }
 }
 
+__global__ void __launch_bounds__(256) core_gram_kernel(const double* __restrict__ G, int64_t I, int Ra,
+                                                        int Rb, double* __restrict__ M,
+                                                        double* __restrict__ E, int chunk) {
+  PDL_ENTRY();
+  core_gram_body(G, I, Ra, Rb, M, E, chunk, blockIdx.x);
+}
+
+// work list of core Grams: item = (job, pair block)
+__global__ void __launch_bounds__(256) core_gram_batch_kernel(const GramJob* __restrict__ jobs,
+                                                              const int2* __restrict__ items) {
+  PDL_ENTRY();
+  const int2 it = items[blockIdx.x];
+  const GramJob j = jobs[it.x];
+  core_gram_body(j.G, j.I, j.Ra, j.Rb, nullptr, j.E, j.chunk, it.y);
+}
+
 cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double* M, double* E,
                              cudaStream_t s) {
   const int RR = Ra * Rb;
@@ -85,6 +101,18 @@ cudaError_t launch_core_gram(const double* G, int64_t I, int Ra, int Rb, double*
   const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(I, (44 * 1024) / (8 * (int64_t)RR)));
   const size_t sm = (size_t)chunk * RR * 8;
   launch_k(core_gram_kernel, (unsigned)blocks, 256, sm, s, G, I, Ra, Rb, M, E, chunk);
+  return cudaGetLastError();
+}
+
+int core_gram_chunk(int64_t I, int RR) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(I, (44 * 1024) / (8 * (int64_t)RR)));
+}
+
+int core_gram_blocks(int RR) { return (int)std::max<int64_t>(1, ((int64_t)RR * (RR + 1) / 2 + 63) / 64); }
+
+cudaError_t launch_core_gram_batch(const GramJob* jobs, const int2* items, int nitems, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  launch_k(core_gram_batch_kernel, (unsigned)nitems, 256, (size_t)44 * 1024, s, jobs, items);
   return cudaGetLastError();
 }
 
@@ -231,6 +259,26 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
   sweep_body<T, B, double>(Q, n, W, status, pivot_ratio, false, !apply_df_supported_d(n));
 }
 
+// work list of FP32 sweep inverses, one CTA per job (orders up to 128: the
+// refined solve that follows has the FP64 fallback, so no singular flag there;
+// orders 129..160 flag singular pivots as the single-stream sweep does)
+__global__ void __launch_bounds__(256) sweep_batch_kernel(const SweepJob* __restrict__ jobs) {
+  PDL_ENTRY();
+  const SweepJob j = jobs[blockIdx.x];
+  if (j.n <= 16) sweep_body<float, 1, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else if (j.n <= 32) sweep_body<float, 2, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else if (j.n <= 64) sweep_body<float, 4, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else if (j.n <= 112) sweep_body<float, 7, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else if (j.n <= 128) sweep_body<float, 8, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else sweep_body<float, 10, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, true);
+}
+
+cudaError_t launch_sweep_batch(const SweepJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  launch_k(sweep_batch_kernel, (unsigned)njobs, 256, 0, s, jobs);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // small FP64 GEMM: 8x8 output tile per CTA, A rows and B columns of the tile
 // staged in shared memory (K <= 256); optional ring-permute epilogue.
@@ -248,19 +296,16 @@ struct FuseFactor {
   double* pivot_ratio = nullptr;
 };
 
-template <int SB>
-__global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ A,
-                                                     const double* __restrict__ B,
-                                                     double* __restrict__ C, int M, int K, int N,
-                                                     int pRa, int pRb, const double* __restrict__ base,
-                                                     FuseFactor ff) {
-  PDL_ENTRY();
+// the 8 x 8 output tile (by, bx) of C = A B, or of the ring epilogue
+__device__ __forceinline__ void gemm64_body(const double* __restrict__ A, const double* __restrict__ B,
+                                            double* __restrict__ C, int M, int K, int N, int pRa, int pRb,
+                                            const double* __restrict__ base, float* Qf, float* Qlo, int bx,
+                                            int by) {
   extern __shared__ double gsm[];
   double* sA = gsm;            // 8 x K
   double* sB = gsm + 8 * K;    // K x 8
   __shared__ double red[4][64];
-  __shared__ int s_last;
-  const int r0 = blockIdx.y * 8, c0 = blockIdx.x * 8;
+  const int r0 = by * 8, c0 = bx * 8;
   for (int e = threadIdx.x; e < 8 * K; e += 256) {
     const int r = e / K, k = e % K;
     sA[e] = (r0 + r < M) ? A[(int64_t)(r0 + r) * K + k] : 0.0;
@@ -289,13 +334,24 @@ __global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ 
       const int64_t qi = (int64_t)(aa + pRa * bb) * RR + (ap + pRa * bp);
       const double v = (base ? base[qi] : 0.0) + s;
       C[qi] = v;
-      if (ff.Qf) {
+      if (Qf) {
         const float hi = (float)v;
-        ff.Qf[qi] = hi;
-        if (ff.Qlo) ff.Qlo[qi] = (float)(v - (double)hi);
+        Qf[qi] = hi;
+        if (Qlo) Qlo[qi] = (float)(v - (double)hi);
       }
     }
   }
+}
+
+template <int SB>
+__global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ A,
+                                                     const double* __restrict__ B,
+                                                     double* __restrict__ C, int M, int K, int N,
+                                                     int pRa, int pRb, const double* __restrict__ base,
+                                                     FuseFactor ff) {
+  PDL_ENTRY();
+  __shared__ int s_last;
+  gemm64_body(A, B, C, M, K, N, pRa, pRb, base, ff.Qf, ff.Qlo, blockIdx.x, blockIdx.y);
   if constexpr (SB > 0) {
     __threadfence();
     __syncthreads();
@@ -321,6 +377,26 @@ cudaError_t launch_gemm64(const double* A, const double* B, double* C, int M, in
   FuseFactor ff;
   if (perm_Ra > 0) { ff.Qf = Qhi; ff.Qlo = Qlo; }
   launch_k(gemm64_kernel<0>, grid, 256, sm, s, A, B, C, M, K, N, perm_Ra, perm_Rb, base, ff);
+  return cudaGetLastError();
+}
+
+// work list of small GEMMs / ring products: item = (job, column tile, row tile)
+__global__ void __launch_bounds__(256) gemm64_batch_kernel(const GemmJob* __restrict__ jobs,
+                                                           const int4* __restrict__ items) {
+  PDL_ENTRY();
+  const int4 it = items[blockIdx.x];
+  const GemmJob j = jobs[it.x];
+  gemm64_body(j.A, j.B, j.C, j.M, j.K, j.N, j.pRa, j.pRb, j.base, j.Qf, j.Qlo, it.y, it.z);
+}
+
+cudaError_t launch_gemm64_batch(const GemmJob* jobs, const int4* items, int nitems, int Kmax, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t sm = (size_t)16 * Kmax * sizeof(double);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gemm64_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  launch_k(gemm64_batch_kernel, (unsigned)nitems, 256, sm, s, jobs, items);
   return cudaGetLastError();
 }
 
@@ -532,12 +608,11 @@ cudaError_t launch_chol_solve(const double* L, const double* invdiag, int n, con
 // per row g = p W32 followed by `iters` refinement steps
 // r = p - g Q (FP64, Q symmetric), g += r W32.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restrict__ Wg,
-                                                           const double* __restrict__ Qg, int n,
-                                                           const double* __restrict__ P, int64_t rows,
-                                                           int iters, int q_in_smem, double* out64,
-                                                           float* out32, PartialSum ps) {
-  PDL_ENTRY();
+// rows bx, bx + nbx, ...
+__device__ __forceinline__ void solve_refine_body(const float* __restrict__ Wg, const double* __restrict__ Qg,
+                                                  int n, const double* __restrict__ P, int64_t rows, int iters,
+                                                  int q_in_smem, double* out64, float* out32, const PartialSum& ps,
+                                                  int64_t bx, int64_t nbx) {
   // one row of P per CTA at a time, one thread per column of the solution
   extern __shared__ unsigned char smr[];
   float* Wm = (float*)smr;                                                    // n x n
@@ -559,7 +634,7 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
   cp_async_commit();
   const double* Q = q_in_smem ? Qs : Qg;
   const int c = tid;
-  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+  for (int64_t r = bx; r < rows; r += nbx) {
     double pc = 0.0;
     if (c < n) {
       if (ps.part) {
@@ -626,6 +701,24 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
   }
 }
 
+__global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restrict__ Wg,
+                                                           const double* __restrict__ Qg, int n,
+                                                           const double* __restrict__ P, int64_t rows,
+                                                           int iters, int q_in_smem, double* out64,
+                                                           float* out32, PartialSum ps) {
+  PDL_ENTRY();
+  solve_refine_body(Wg, Qg, n, P, rows, iters, q_in_smem, out64, out32, ps, blockIdx.x, gridDim.x);
+}
+
+// work list of refined solves of orders 129..160 (FP64 residual): item = (job, block, blocks of the job)
+__global__ void __launch_bounds__(160) solve_refine_batch_kernel(const RefineJob* __restrict__ jobs,
+                                                                 const int4* __restrict__ items) {
+  PDL_ENTRY();
+  const int4 it = items[blockIdx.x];
+  const RefineJob j = jobs[it.x];
+  solve_refine_body(j.W, j.Q, j.n, j.P, j.rows, j.iters, j.q_in_smem, j.out64, j.out32, j.ps, it.y, it.z);
+}
+
 // ---------------------------------------------------------------------------
 // Refined solve for n <= 128, one row of P per CTA at a time, 256
 // threads: thread (c, part) owns column c (and c + 64) and the quarter part of
@@ -638,21 +731,6 @@ __global__ void __launch_bounds__(160) solve_refine_kernel(const float* __restri
 //   g += r W32                           (FP32), result rounded to FP64 / FP32
 // The FP64 pipe is not used in the inner loops.
 // ---------------------------------------------------------------------------
-struct ApplyDF {
-  const float* W = nullptr;
-  const float* Qh = nullptr;
-  const float* Ql = nullptr;
-  int n = 0;
-  int64_t rows = 0;
-  const double* P = nullptr;   // right-hand sides when ps.part is null
-  PartialSum ps;
-  double* out64 = nullptr;
-  float* out32 = nullptr;
-  int* status = nullptr;
-  const double* Q64 = nullptr;          // FP64 Q for the fallback (null: no fallback)
-  const double* pivot_ratio = nullptr;  // written by the FP32 inverse (null: not checked)
-  unsigned* fallbacks = nullptr;        // CTAs that took the FP64 fallback (counter)
-};
 
 // FP64 fallback of the refined solve, for a Q whose FP32 inverse cannot seed a
 // converging refinement (cond(Q) u_32 not small; see apply_df_kernel): the CTA
@@ -662,8 +740,12 @@ struct ApplyDF {
 // partials in split order (and stored) as in the FP32 path.
 constexpr double kFallbackPivotRatio = 1.0 / 8192.0;   // smallest FP32 pivot / diagonal kept
 constexpr float kFallbackCorrection = 1e-3f;           // largest first correction kept, |dg| / |g|
+constexpr int kRowMaskBits = 256;                      // rows of a CTA tracked one by one
 
-__device__ __noinline__ void apply_fp64_rows(const ApplyDF& a, double* sm) {
+// Rows bx, bx + nbx, ...; with `mask`, only the rows whose local index (0 for
+// bx, 1 for bx + nbx, ...) has its bit set.
+__device__ __noinline__ void apply_fp64_rows(const ApplyDF& a, double* sm, int64_t bx, int64_t nbx,
+                                             const unsigned* mask) {
   const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
   double* W = sm;           // n x n: Q, then -Q^{-1}
   double* cb = W + n * n;   // pivot column
@@ -702,7 +784,9 @@ __device__ __noinline__ void apply_fp64_rows(const ApplyDF& a, double* sm) {
     __syncthreads();
   }
   if (tid == 0 && s_bad && a.status) atomicOr(a.status, DEV_ERR_SINGULAR);
-  for (int64_t r = blockIdx.x; r < a.rows; r += gridDim.x) {
+  int64_t lr = 0;
+  for (int64_t r = bx; r < a.rows; r += nbx, ++lr) {
+    if (mask && lr < kRowMaskBits && !((mask[lr >> 5] >> (lr & 31)) & 1u)) continue;
     for (int c = tid; c < n; c += nt) {
       double pc;
       if (a.ps.part) {
@@ -748,10 +832,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// rows bx, bx + nbx, ... of one refined solve (bx: the block's index, nbx: the
+// blocks sharing the solve)
 template <int CPT>
-__global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
+__device__ __forceinline__ void apply_df_body(const ApplyDF& a, int64_t bx, int64_t nbx) {
   // CPT columns per thread: c = (tid & 63) + 64 u, u < CPT (n <= 64 CPT)
-  PDL_ENTRY();
   extern __shared__ __align__(16) unsigned char sma[];
   const int n = a.n, nn = n * n, nns = (nn + 3) & ~3;
   float* Wm = (float*)sma;                  // n x n
@@ -764,11 +849,12 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
   __shared__ __align__(8) uint64_t bar;
   __shared__ float s_dn[2], s_gn[2];
   __shared__ int s_redo;
+  __shared__ unsigned s_rows[kRowMaskBits / 32];   // rows to redo in FP64, by local index
   const int tid = threadIdx.x, c0 = tid & 63, part = tid >> 6;
   // a tiny FP32 pivot (or none recorded as usable): the FP32 inverse cannot seed
   // the refinement, go straight to the FP64 fallback
   if (a.Q64 && a.pivot_ratio && !(*a.pivot_ratio >= kFallbackPivotRatio)) {
-    apply_fp64_rows(a, (double*)sma);
+    apply_fp64_rows(a, (double*)sma, bx, nbx, nullptr);
     return;
   }
   if (tid == 0) {
@@ -776,6 +862,7 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_redo = 0;
   }
+  if (tid < kRowMaskBits / 32) s_rows[tid] = 0u;
   __syncthreads();
   // even n: bulk copies (sizes in 16-byte units); odd n: plain loads
   const bool bulk = (n & 1) == 0;
@@ -806,7 +893,8 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
     if (k < k1) s0 = fmaf(vf[k], Wm[k * n + c], s0);
     return s0 + s1;
   };
-  for (int64_t r = blockIdx.x; r < a.rows; r += gridDim.x) {
+  int64_t lr = 0;
+  for (int64_t r = bx; r < a.rows; r += nbx, ++lr) {
     // right-hand side: base + split partials (or P).  Part q sums the splits
     // q, q + 4, ... in order; the four sums are added in part order.
 #pragma unroll
@@ -947,13 +1035,39 @@ __global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
     __syncthreads();
     if (tid == 0) {
       const float dn = s_dn[0] + s_dn[1], gn = s_gn[0] + s_gn[1];
-      if (!(dn <= kFallbackCorrection * kFallbackCorrection * gn)) s_redo = 1;
+      if (!(dn <= kFallbackCorrection * kFallbackCorrection * gn)) {
+        s_redo = 1;
+        if (lr < kRowMaskBits) s_rows[lr >> 5] |= 1u << (lr & 31);
+        else s_redo = 2;   // beyond the tracked rows: redo every row of the block
+      }
     }
   }
   if (!staged) {   // no row: the bulk copies still complete before exit
     mbar_wait(&bar, 0, 2000000000ull);
   }
-  if (a.Q64 && __syncthreads_or(s_redo)) apply_fp64_rows(a, (double*)sma);
+  if (a.Q64 && __syncthreads_or(s_redo)) apply_fp64_rows(a, (double*)sma, bx, nbx, s_redo == 2 ? nullptr : s_rows);
+}
+
+template <int CPT>
+__global__ void __launch_bounds__(256) apply_df_kernel(ApplyDF a) {
+  PDL_ENTRY();
+  apply_df_body<CPT>(a, blockIdx.x, gridDim.x);
+}
+
+// work list of refined solves: item = (job, block, blocks of the job)
+template <int CPT>
+__global__ void __launch_bounds__(256) apply_df_batch_kernel(const ApplyDF* __restrict__ jobs,
+                                                             const int4* __restrict__ items) {
+  PDL_ENTRY();
+  __shared__ ApplyDF sj;
+  const int4 it = items[blockIdx.x];
+  {
+    const int* src = (const int*)&jobs[it.x];
+    int* dst = (int*)&sj;
+    for (int e = threadIdx.x; e < (int)(sizeof(ApplyDF) / sizeof(int)); e += blockDim.x) dst[e] = src[e];
+  }
+  __syncthreads();
+  apply_df_body<CPT>(sj, it.y, it.z);
 }
 
 size_t apply_df_smem(int n) {
@@ -980,6 +1094,17 @@ cudaError_t launch_split_pair(const double* Q, int64_t count, float* hi, float* 
 }
 
 bool apply_df_supported(int n) { return apply_df_supported_d(n); }
+
+cudaError_t launch_apply_df_batch(const ApplyDF* jobs, const int4* items, int nitems, int nmax, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (!apply_df_supported(nmax)) return cudaErrorInvalidValue;
+  const size_t sm = apply_df_smem(nmax);
+  auto kern = nmax <= 64 ? apply_df_batch_kernel<1> : apply_df_batch_kernel<2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  launch_k(kern, (unsigned)nitems, 256, sm, s, jobs, items);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, int n, const double* P, int64_t rows,
                             double* out64, float* out32, const PartialSum* ps, int* status, cudaStream_t s,
@@ -1026,6 +1151,26 @@ cudaError_t launch_leverage_dot(const double* G, const double* X, int64_t rows, 
 cudaError_t launch_factor_mixed(const double* Q, int n, float* W32, int* status, double* pivot_ratio,
                                 cudaStream_t s) {
   return launch_sweep<float>(Q, n, W32, status, pivot_ratio, s);
+}
+
+int refine_q_in_smem(int n) {
+  const size_t base = (size_t)n * n * sizeof(float) + 16 + (size_t)n * (sizeof(double) + sizeof(float));
+  return base + (size_t)n * n * sizeof(double) <= 200 * 1024 ? 1 : 0;
+}
+
+size_t refine_smem(int n, int q_in_smem) {
+  const size_t base = (size_t)n * n * sizeof(float) + 16 + (size_t)n * (sizeof(double) + sizeof(float));
+  return base + (q_in_smem ? (size_t)n * n * sizeof(double) : 0);
+}
+
+cudaError_t launch_refine_batch(const RefineJob* jobs, const int4* items, int nitems, int nmax, size_t smem,
+                                cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(solve_refine_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  launch_k(solve_refine_batch_kernel, (unsigned)nitems, ((nmax + 31) / 32) * 32, smem, s, jobs, items);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_apply_mixed(const float* W32, const double* Q, int n, const double* P, int64_t rows,

@@ -90,6 +90,23 @@ cudaError_t launch_apply_mixed(const float* W32, const double* Q, int n, const d
                                int iters, double* out64, float* out32, const PartialSum* ps, cudaStream_t s);
 // refined solve with Q as an FP32 pair (n <= 64, even); Q (FP64) -> pair
 bool apply_df_supported(int n);
+// one refined solve out = P Q^{-1} (FP32 inverse W, Q as an FP32 pair) with the
+// FP64 fallback for an ill-conditioned Q (Q64, pivot_ratio, fallbacks)
+struct ApplyDF {
+  const float* W = nullptr;
+  const float* Qh = nullptr;
+  const float* Ql = nullptr;
+  int n = 0;
+  int64_t rows = 0;
+  const double* P = nullptr;   // right-hand sides when ps.part is null
+  PartialSum ps;
+  double* out64 = nullptr;
+  float* out32 = nullptr;
+  int* status = nullptr;
+  const double* Q64 = nullptr;          // FP64 Q for the fallback (null: no fallback)
+  const double* pivot_ratio = nullptr;  // written by the FP32 inverse (null: not checked)
+  unsigned* fallbacks = nullptr;        // CTAs that took the FP64 fallback (counter)
+};
 // Q64 (FP64 Q), pivot_ratio (from the FP32 inverse) and fallbacks (counter): the
 // FP64 fallback for an ill-conditioned Q (Q64 null = none)
 cudaError_t launch_apply_df(const float* W32, const float* Qh, const float* Ql, int n, const double* P, int64_t rows,
@@ -211,3 +228,87 @@ cudaError_t launch_gemm_tc_splitk(const void* A, int xtype, int64_t M, int Kpad,
 int gemm_tc_splitk_count(int Kpad, int splits);
 int stage2_plan_splits(const Stage2Args& a, int64_t* per);
 cudaError_t launch_stage2(const Stage2Args& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// work lists for batched updates of many independent streams: each launch
+// covers every stream; block b runs item b, which names a job (one stream's
+// problem) and the tile of it this block computes.  Jobs and items live in
+// device memory (built once per batch layout).
+// ---------------------------------------------------------------------------
+struct GramJob {                 // E = transfer form of G_{(2)}^T G_{(2)} (core_gram)
+  const double* G = nullptr;
+  int64_t I = 0;
+  int Ra = 0, Rb = 0;
+  double* E = nullptr;
+  int chunk = 1;                 // rows staged per pass (core_gram_chunk)
+};
+int core_gram_chunk(int64_t I, int RR);
+int core_gram_blocks(int RR);
+cudaError_t launch_core_gram_batch(const GramJob* jobs, const int2* items, int nitems, cudaStream_t s);
+
+struct GemmJob {                 // C = A B (M x K x N), ring epilogue when pRa > 0
+  const double* A = nullptr;
+  const double* B = nullptr;
+  double* C = nullptr;
+  int M = 0, K = 0, N = 0, pRa = 0, pRb = 0;
+  const double* base = nullptr;
+  float* Qf = nullptr;
+  float* Qlo = nullptr;
+};
+cudaError_t launch_gemm64_batch(const GemmJob* jobs, const int4* items, int nitems, int Kmax, cudaStream_t s);
+
+struct SweepJob {                // W = Q^{-1} by the FP32 sweep (order <= 128)
+  const double* Q = nullptr;
+  int n = 0;
+  float* W = nullptr;
+  int* status = nullptr;
+  double* pivot_ratio = nullptr;
+};
+cudaError_t launch_sweep_batch(const SweepJob* jobs, int njobs, cudaStream_t s);
+
+// dense SIMT MTTKRP jobs of one register-block class (mttkrp_class): item =
+// (job, row block, split, stream); the job's slab is xptrs[stream] (the slab
+// pointer changes every step, the jobs do not)
+int mttkrp_class(const MttkrpArgs& a);
+size_t mttkrp_smem_bytes(const MttkrpArgs& a, int BK);
+int mttkrp_rows_per_block(const MttkrpArgs& a);
+cudaError_t launch_mttkrp_batch(const MttkrpArgs* jobs, const int4* items, const void* const* xptrs, int nitems,
+                                int cls, int xtype, int BK, size_t smem, cudaStream_t s);
+// out[i] = *ptrs[i] for i < n
+cudaError_t launch_gather_ints(const int* const* ptrs, int n, int* out, cudaStream_t s);
+
+struct ReduceJob {               // out = base + sum of FP32 split partials (reduce order of launch_reduce_partials)
+  const float* partial = nullptr;
+  int splits = 1;
+  int64_t count = 0;
+  const double* base = nullptr;
+  double* out = nullptr;
+};
+cudaError_t launch_reduce_batch(const ReduceJob* jobs, const int2* items, int nitems, cudaStream_t s);
+
+// refined solves, all of order <= nmax (<= 128): item = (job, block, blocks of the job)
+cudaError_t launch_apply_df_batch(const ApplyDF* jobs, const int4* items, int nitems, int nmax, cudaStream_t s);
+
+struct RefineJob {               // out = P Q^{-1} for orders 129..160: FP32 inverse W, FP64 residual
+  const float* W = nullptr;
+  const double* Q = nullptr;
+  int n = 0;
+  const double* P = nullptr;
+  int64_t rows = 0;
+  int iters = 1;
+  int q_in_smem = 0;
+  double* out64 = nullptr;
+  float* out32 = nullptr;
+  PartialSum ps;
+};
+int refine_q_in_smem(int n);
+size_t refine_smem(int n, int q_in_smem);
+cudaError_t launch_refine_batch(const RefineJob* jobs, const int4* items, int nitems, int nmax, size_t smem,
+                                cudaStream_t s);
+
+struct CopyJob {                 // dst = src, bytes (16-byte aligned: both multiples of 16 or plain)
+  const void* src = nullptr;
+  void* dst = nullptr;
+  int64_t bytes = 0;
+};
+cudaError_t launch_copy_batch(const CopyJob* jobs, const int2* items, int nitems, cudaStream_t s);

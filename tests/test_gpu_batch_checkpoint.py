@@ -65,6 +65,39 @@ def test_batch_graph_on_a_stream_equals_individual_updates():
             assert np.array_equal(a.core(n), b.core(n))
 
 
+@pytest.mark.parametrize("sketch", ["uniform", "leverage"])
+def test_rstr_batch_on_a_stream_equals_individual_updates(sketch):
+    """rSTR batches on a non-default stream run every context's step as a
+    concurrent branch: bit-identical to one rstr_update per context."""
+    import torch
+    p = lib()
+    specs = synth.uneven_streams(count=4, steps=1, seed=9, dim_range=(16, 40), rank_range=(2, 4),
+                                 tnew_range=(2, 5), t_init=8)
+    made = []
+    for i, s in enumerate(specs):
+        tn = s.t_news[0]
+        T = s.t_init + 3 * tn
+        G, X = problem(s.dims, T, s.ranks, 800 + i)
+        init = perturbed_init(G, s.t_init, 810 + i)
+        kw = dict(compute="f32", sketch=sketch, m=64, seed=11 + i, t_capacity=T)
+        a = p.str_init_cores(init, X0=dev(X[..., :s.t_init]), **kw)
+        b = p.str_init_cores(init, X0=dev(X[..., :s.t_init]), **kw)
+        made.append((s, tn, X, a, b))
+    st = torch.cuda.Stream()
+    for step in range(3):
+        slabs = [dev(X[..., s.t_init + step * tn:s.t_init + (step + 1) * tn]) for s, tn, X, _, _ in made]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(st):
+            p.str_update_batch([a for _, _, _, a, _ in made], slabs, randomized=True)
+        st.synchronize()
+        for (_, _, _, _, b), x in zip(made, slabs):
+            b.rupdate(x)
+    for s, tn, X, a, b in made:
+        assert a.time_rows() == b.time_rows()
+        for n in (1, 2, 3):
+            assert np.array_equal(a.core(n), b.core(n))
+
+
 def test_batch_matches_the_oracle():
     """Batched updates of uneven order-3 streams (BF16 slabs, FP32 slab
     arithmetic, one sweep), each against the FP64 oracle's STR (Alg. 4) on the
@@ -103,6 +136,37 @@ def test_batch_matches_the_oracle():
                 a, b = ctx.core(n), ref.cores[n - 1]
                 assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
             ctx.close()
+
+
+def test_batch_large_rank_products_match_the_oracle():
+    """Batched streams whose normal equations have orders R_n R_{n+1} of 132 to
+    144 (the solve with an FP64 residual) beside small ones: cores within 1e-5
+    of the oracle after two steps, and bit-identical to one update per stream."""
+    import torch
+    from oracle import stream as ost
+    p = lib()
+    shapes = [((24, 20), (12, 12, 11), 3), ((20, 28), (11, 12, 12), 2), ((18, 22), (3, 4, 2), 4)]
+    made = []
+    for i, (dims, ranks, tn) in enumerate(shapes):
+        T = 16 + 2 * tn
+        G, X = problem(dims, T, ranks, 700 + i)
+        init = perturbed_init(G, 16, 710 + i)
+        # both initialised through the SIMT MTTKRP (the batch's own path), so the
+        # initial P_n, Q_n are the same bytes
+        a = p.str_init_cores(init, X0=dev(X[..., :16], torch.float32), compute="f32", t_capacity=T, mttkrp_path=1)
+        b = p.str_init_cores(init, X0=dev(X[..., :16], torch.float32), compute="f32", t_capacity=T, mttkrp_path=1)
+        made.append((tn, X.astype(np.float32).astype(np.float64), a, b, ost.str_init(
+            X.astype(np.float32).astype(np.float64)[..., :16], init)))
+    for step in range(2):
+        sl = [dev(X[..., 16 + step * tn:16 + (step + 1) * tn], torch.float32) for tn, X, _, _, _ in made]
+        p.str_update_batch([a for _, _, a, _, _ in made], sl)
+        for (tn, X, a, b, ref), x in zip(made, sl):
+            b.update(x)
+            ost.str_update(ref, X[..., 16 + step * tn:16 + (step + 1) * tn])
+    for tn, X, a, b, ref in made:
+        for n in (1, 2, 3):
+            assert np.array_equal(a.core(n), b.core(n))
+            assert np.linalg.norm(a.core(n) - ref.cores[n - 1]) <= 1e-5 * np.linalg.norm(ref.cores[n - 1])
 
 
 @pytest.mark.parametrize("sketch", ["none", "leverage", "ksrft"])
