@@ -251,12 +251,223 @@ __device__ __forceinline__ void sweep_body(const SRC* __restrict__ Q, int n, T* 
   }
 }
 
+// Blocked form of the symmetric sweep: PB pivots K = {k0 .. k0 + PB - 1} per
+// barrier.  Sweeping a block of pivots equals sweeping them one after another
+// (the sweep operator composes), so with P = A_KK (its LDL^T pivots are the
+// Schur-complement pivots of the one-by-one sweep):
+//   A_IJ -= A_IK P^{-1} A_KJ,  A_KJ <- P^{-1} A_KJ,  A_IK <- A_IK P^{-1},  A_KK <- -P^{-1}.
+// Owners of the PB columns publish them (double-buffered, one barrier per
+// block); every thread factors P in registers (LDL^T, PB x PB) and updates its
+// B x B entries with a rank-PB product.  Padded pivots (k >= n) act as the
+// identity.  After every block the matrix holds -Q^{-1} as in sweep_body.
+template <typename T, int B, int PB, typename SRC>
+__device__ __forceinline__ void sweep_body_blocked(const SRC* __restrict__ Q, int n, T* __restrict__ W,
+                                                   int* status, double* pivot_ratio, bool cg,
+                                                   bool flag_singular) {
+  __shared__ T colb[2][PB][16 * B];
+  __shared__ T qd[16 * B];
+  __shared__ T pivs[16 * B];
+  __shared__ T s_tol;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T a[B][B];
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      a[i][j] = (r < n && c < n) ? (T)ldq(Q + (int64_t)r * n + c, cg) : (T)0;
+    }
+  for (int k = tid; k < n; k += 256) qd[k] = (T)ldq(Q + (int64_t)k * n + k, cg);
+  __syncthreads();
+  if (tid < 32) {
+    T mx = 0;
+    for (int k = tid; k < n; k += 32) mx = mx > qd[k] ? mx : qd[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const T o = __shfl_xor_sync(0xffffffffu, mx, off);
+      mx = mx > o ? mx : o;
+    }
+    if (tid == 0) s_tol = (T)n * (T)(sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07) * mx;
+  }
+  __syncthreads();
+  const T tol = s_tol;
+  int step = 0;
+#pragma unroll
+  for (int kb = 0; kb < B; ++kb) {
+#pragma unroll 1
+    for (int kq = 0; kq < 16 / PB; ++kq, ++step) {
+      const int k0 = kb * 16 + kq * PB;
+      if (k0 >= n) break;
+      const int par = step & 1;
+      // the block's columns (all rows; padded rows hold zeros)
+      if (tx >= kq * PB && tx < kq * PB + PB) {
+        const int j = tx - kq * PB;
+#pragma unroll
+        for (int i = 0; i < B; ++i) colb[par][j][ty + 16 * i] = a[i][kb];
+      }
+      __syncthreads();
+      // LDL^T of the pivot block P (padded pivots: identity)
+      T L[PB][PB], d[PB], rdq[PB];
+#pragma unroll
+      for (int r = 0; r < PB; ++r) {
+#pragma unroll
+        for (int c = 0; c < PB; ++c) L[r][c] = (T)0;
+      }
+#pragma unroll
+      for (int r = 0; r < PB; ++r) {
+        const bool pad = k0 + r >= n;
+        T dr = pad ? (T)1 : colb[par][r][k0 + r];
+#pragma unroll
+        for (int q = 0; q < r; ++q) dr -= L[r][q] * L[r][q] * d[q];
+        if (tid == 0 && !pad) pivs[k0 + r] = dr;
+        if (!(dr > tol)) dr = (T)1;   // recorded as singular after the loop
+        d[r] = dr;
+        const T rd = recip_fast(dr);
+        rdq[r] = rd;
+#pragma unroll
+        for (int i = r + 1; i < PB; ++i) {
+          T v = (k0 + i >= n) ? (T)0 : colb[par][r][k0 + i];
+#pragma unroll
+          for (int q = 0; q < r; ++q) v -= L[i][q] * L[r][q] * d[q];
+          L[i][r] = v * rd;
+        }
+      }
+      // P^{-1} = L^{-T} D^{-1} L^{-1}: M = L^{-1} (unit lower), Pi = M^T D^{-1} M
+      T M[PB][PB];
+#pragma unroll
+      for (int i = 0; i < PB; ++i) {
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+          T v = (i == j) ? (T)1 : (T)0;
+          if (j < i) {
+#pragma unroll
+            for (int q = j; q < i; ++q) v -= L[i][q] * (q == j ? (T)1 : M[q][j]);
+          }
+          M[i][j] = (j <= i) ? v : (T)0;
+        }
+      }
+      T Pi[PB][PB];
+#pragma unroll
+      for (int i = 0; i < PB; ++i)
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+          T v = (T)0;
+#pragma unroll
+          for (int q = 0; q < PB; ++q) v += M[q][i] * M[q][j] * rdq[q];
+          Pi[i][j] = v;
+        }
+      // Z = A_IK P^{-1} for the owned rows, A_KJ for the owned columns
+      T Z[B][PB], Y[B][PB];
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        T aik[PB];
+#pragma unroll
+        for (int r = 0; r < PB; ++r) aik[r] = colb[par][r][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+          T v = (T)0;
+#pragma unroll
+          for (int r = 0; r < PB; ++r) v = fma_t(aik[r], Pi[r][j], v);
+          Z[i][j] = v;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < B; ++c)
+#pragma unroll
+        for (int r = 0; r < PB; ++r) Y[c][r] = colb[par][r][tx + 16 * c];   // A_Kc (Q symmetric)
+#pragma unroll
+      for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+          T v = a[i][c];
+#pragma unroll
+          for (int r = 0; r < PB; ++r) v = fma_t(-Z[i][r], Y[c][r], v);
+          a[i][c] = v;
+        }
+      // the block's rows and columns (selects keep every register index static)
+      const bool krow = ty >= kq * PB && ty < kq * PB + PB;
+      const bool kcol = tx >= kq * PB && tx < kq * PB + PB;
+      const int rr = ty - kq * PB, cc = tx - kq * PB;
+      T pir[PB], pic = (T)0;
+#pragma unroll
+      for (int r = 0; r < PB; ++r) pir[r] = (T)0;
+#pragma unroll
+      for (int q = 0; q < PB; ++q)
+#pragma unroll
+        for (int r = 0; r < PB; ++r) {
+          if (rr == q) pir[r] = Pi[q][r];
+          if (rr == q && cc == r) pic = Pi[q][r];
+        }
+      if (krow) {
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+          T v = (T)0;
+#pragma unroll
+          for (int r = 0; r < PB; ++r) v = fma_t(pir[r], Y[c][r], v);
+          a[kb][c] = v;
+        }
+      }
+      if (kcol) {
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+          T z = (T)0;
+#pragma unroll
+          for (int r = 0; r < PB; ++r)
+            if (cc == r) z = Z[i][r];
+          a[i][kb] = z;
+        }
+        if (krow) a[kb][kb] = -pic;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      if (r < n && c < n) W[(int64_t)r * n + c] = -a[i][j];
+    }
+  __syncthreads();
+  if (tid < 32) {
+    int bad = 0;
+    T ratio = (T)1;
+    for (int k = tid; k < n; k += 32) {
+      const T p = pivs[k];
+      if (!(p > tol)) { bad = 1; ratio = (T)0; }
+      else if (qd[k] > (T)0) {
+        const T r = p / qd[k];
+        ratio = r < ratio ? r : ratio;
+      }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const T o = __shfl_xor_sync(0xffffffffu, ratio, off);
+      ratio = o < ratio ? o : ratio;
+    }
+    if (tid == 0) {
+      if (bad && status && flag_singular) atomicOr(status, DEV_ERR_SINGULAR);
+      if (pivot_ratio) *pivot_ratio = (double)ratio;
+    }
+  }
+}
+
+// the sweep used by the library: pairs of pivots per barrier up to order 128
+// (every thread factors the pivot block itself, so larger blocks trade the
+// barriers saved for redundant arithmetic), one by one above
+template <typename T, int B, typename SRC>
+__device__ __forceinline__ void sweep_any(const SRC* __restrict__ Q, int n, T* __restrict__ W, int* status,
+                                          double* pivot_ratio, bool cg, bool flag_singular) {
+  if constexpr (B <= 8) sweep_body_blocked<T, B, 2, SRC>(Q, n, W, status, pivot_ratio, cg, flag_singular);
+  else sweep_body<T, B, SRC>(Q, n, W, status, pivot_ratio, cg, flag_singular);
+}
+
 template <typename T, int B>
 __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __restrict__ Q, int n,
                                                             T* __restrict__ W, int* status,
                                                             double* pivot_ratio) {
   PDL_ENTRY();
-  sweep_body<T, B, double>(Q, n, W, status, pivot_ratio, false, !apply_df_supported_d(n));
+  sweep_any<T, B, double>(Q, n, W, status, pivot_ratio, false, !apply_df_supported_d(n));
 }
 
 // work list of FP32 sweep inverses, one CTA per job (orders up to 128: the
@@ -265,12 +476,12 @@ __global__ void __launch_bounds__(256) sweep_inverse_kernel(const double* __rest
 __global__ void __launch_bounds__(256) sweep_batch_kernel(const SweepJob* __restrict__ jobs) {
   PDL_ENTRY();
   const SweepJob j = jobs[blockIdx.x];
-  if (j.n <= 16) sweep_body<float, 1, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
-  else if (j.n <= 32) sweep_body<float, 2, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
-  else if (j.n <= 64) sweep_body<float, 4, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
-  else if (j.n <= 112) sweep_body<float, 7, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
-  else if (j.n <= 128) sweep_body<float, 8, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
-  else sweep_body<float, 10, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, true);
+  if (j.n <= 16) sweep_any<float, 1, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else if (j.n <= 32) sweep_any<float, 2, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else if (j.n <= 64) sweep_any<float, 4, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else if (j.n <= 112) sweep_any<float, 7, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else if (j.n <= 128) sweep_any<float, 8, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, false);
+  else sweep_any<float, 10, double>(j.Q, j.n, j.W, j.status, j.pivot_ratio, false, true);
 }
 
 cudaError_t launch_sweep_batch(const SweepJob* jobs, int njobs, cudaStream_t s) {
@@ -361,8 +572,8 @@ __global__ void __launch_bounds__(256) gemm64_kernel(const double* __restrict__ 
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    sweep_body<float, SB, float>(ff.Qf, pRa * pRb, ff.W, ff.status, ff.pivot_ratio, true,
-                                 !apply_df_supported_d(pRa * pRb));
+    sweep_any<float, SB, float>(ff.Qf, pRa * pRb, ff.W, ff.status, ff.pivot_ratio, true,
+                                !apply_df_supported_d(pRa * pRb));
   }
 }
 
@@ -851,12 +1062,6 @@ __device__ __forceinline__ void apply_df_body(const ApplyDF& a, int64_t bx, int6
   __shared__ int s_redo;
   __shared__ unsigned s_rows[kRowMaskBits / 32];   // rows to redo in FP64, by local index
   const int tid = threadIdx.x, c0 = tid & 63, part = tid >> 6;
-  // a tiny FP32 pivot (or none recorded as usable): the FP32 inverse cannot seed
-  // the refinement, go straight to the FP64 fallback
-  if (a.Q64 && a.pivot_ratio && !(*a.pivot_ratio >= kFallbackPivotRatio)) {
-    apply_fp64_rows(a, (double*)sma, bx, nbx, nullptr);
-    return;
-  }
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -871,6 +1076,18 @@ __device__ __forceinline__ void apply_df_body(const ApplyDF& a, int64_t bx, int6
     bulk_g2s(Wm, a.W, nn * 4, &bar);
     bulk_g2s(Qh, a.Qh, nn * 4, &bar);
     bulk_g2s(Ql, a.Ql, nn * 4, &bar);
+  }
+  // a tiny FP32 pivot (or none recorded as usable): the FP32 inverse cannot seed
+  // the refinement, go straight to the FP64 fallback (read while the copies run;
+  // the fallback reuses the staging area once they have landed)
+  if (a.Q64 && a.pivot_ratio && !(*a.pivot_ratio >= kFallbackPivotRatio)) {
+    const bool ok = !bulk || mbar_wait(&bar, 0, 2000000000ull);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0 && a.status) atomicOr(a.status, DEV_ERR_TIMEOUT);
+      return;
+    }
+    apply_fp64_rows(a, (double*)sma, bx, nbx, nullptr);
+    return;
   }
   bool staged = !bulk;
   if (!bulk) {
