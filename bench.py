@@ -68,6 +68,8 @@ def args_parse(argv=None):
     ap.add_argument("--no-loss", action="store_true", help="skip the masked-loss row")
     ap.add_argument("--no-large", action="store_true", help="skip the 60^5 stand-in row")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--evidence", default=None, choices=["stage1_r12", "sampling_m1e6", "batch256"],
+                    help="run one kernel-evidence workload (for ncu captures) and print its line")
     return ap.parse_args(argv)
 
 
@@ -873,9 +875,120 @@ def main_reference(a):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# kernel evidence at enlarged shapes (each prints one JSON line; run under ncu
+# with a kernel filter for the counters)
+# ---------------------------------------------------------------------------
+def evidence_stage1_r12(p, torch, steps=2, warmup=1):
+    """Stage 1 at a shape where its arithmetic intensity crosses the tensor
+    ridge: order 5, 60 x 60 x 60 x 60 spatial, TR-ranks 12 (R_k R_{k+1} = 144),
+    5-slice FP32 slabs (64.8 M entries, 259 MB), one sweep.  Algorithmic
+    intensity 2 R^2 / 4 = 72 flop/B; the 3-term TF32 split executes 3 times the
+    MMA work (216 flop/B, above the TF32 / HBM ridge)."""
+    dims, R, t_init, t_new = (60, 60, 60, 60), 12, 12, 5
+    T = t_init + (steps + warmup) * t_new
+    G = synth.gaussian_cores(dims + (T,), (R,) * 5, 88)
+    truth = p.str_init_cores(G, X0=None, t_capacity=T)
+    X = p.paper_layout(truth.reconstruct(0, T, dtype=torch.float32))
+    truth.close()
+    rng = np.random.default_rng(288)
+    init = [g + 0.05 * rng.standard_normal(g.shape) for g in G]
+    init[-1] = init[-1][:, :t_init, :]
+    E = int(np.prod(dims)) * t_new
+    ctx = p.str_init_cores(init, X0=X[..., :t_init], compute="f32", sweeps=1, async_status=1, profile=1,
+                           t_capacity=T)
+    times, _, st = timed_updates(p, torch, ctx, lambda j: X[..., t_init + j * t_new:t_init + (j + 1) * t_new],
+                                 steps, warmup)
+    ctx.close()
+    s1 = st["class_ms"]["mttkrp"] / max(1, st["class_launches"]["mttkrp"])
+    peaks = measure_peaks(p, torch)
+    flop_alg, flop_exec = 2.0 * E * R * R, 6.0 * E * R * R
+    return {"evidence": "stage1_r12", "workload": "60^4 x 5 FP32 slab, TR-ranks 12 (R_k R_{k+1} = 144), one sweep",
+            "ms_per_update": sum(times) / steps, "stage1_avg_launch_ms": s1, "stage1_launches": st["class_launches"]["mttkrp"],
+            "stage1_hbm_gbs": E * 4 / (s1 / 1e3) / 1e9, "stage1_alg_tflops": flop_alg / (s1 / 1e3) / 1e12,
+            "stage1_exec_tflops": flop_exec / (s1 / 1e3) / 1e12, "tf32_tflops": peaks["tf32_tflops"],
+            "hbm_gbs": peaks["hbm_gbs"], "hbm_note": peaks["hbm_note"],
+            "kernel_time_share": {k: round(v / sum(st["class_ms"].values()), 4)
+                                  for k, v in st["class_ms"].items() if v > 0}}
+
+
+def evidence_sampling_m1e6(p, torch, steps=2, warmup=1):
+    """Sampling, gather and sketched-Gram kernels at a sketch size of one
+    million rows: order 3, 500 x 500 spatial (the paper's 500^3 synthetic
+    tensor, Sec. 4.3), TR-ranks 10, 5-slice BF16 slabs, rSTR-U and rSTR-L with
+    m = 10^6."""
+    dims, R, t_init, t_new, m = (500, 500), 10, 20, 5, 1000000
+    T = t_init + (steps + warmup) * t_new
+    G = synth.gaussian_cores(dims + (T,), (R,) * 3, 99)
+    truth = p.str_init_cores(G, X0=None, t_capacity=T)
+    Xb = p.paper_layout(truth.reconstruct(0, T, dtype=torch.float32).to(torch.bfloat16))
+    truth.close()
+    rng = np.random.default_rng(299)
+    init = [g + 0.05 * rng.standard_normal(g.shape) for g in G]
+    init[-1] = init[-1][:, :t_init, :]
+    E = int(np.prod(dims)) * t_new
+    out = {"evidence": "sampling_m1e6", "workload": "500 x 500 x 5 BF16 slabs, TR-ranks 10, sketch size 10^6"}
+    for sk in ("uniform", "leverage"):
+        ctx = p.str_init_cores(init, X0=Xb[..., :t_init], compute="f32", sketch=sk, m=m, seed=7, profile=1,
+                               async_status=1, t_capacity=T)
+        times, _, st = timed_updates(p, torch, ctx, lambda j: Xb[..., t_init + j * t_new:t_init + (j + 1) * t_new],
+                                     steps, warmup, randomized=True)
+        ctx.close()
+        out[sk] = {"ms_per_update": sum(times) / steps,
+                   "class_ms_per_update": {k: round(v / steps, 4) for k, v in st["class_ms"].items() if v > 0},
+                   "gathered_bytes_per_update": 3 * m * dims[0] * 2 * 2,
+                   "note": "gathered fibres: m I_n BF16 values read and written per spatial mode"}
+    return out
+
+
+def evidence_batch256(p, torch, steps=3, warmup=2):
+    """The work-list batch alone: 256 uneven order-3 streams as in the bench's
+    batch row, a few steps (for ncu captures of the batched Gram, ring and
+    solve kernels)."""
+    specs = synth.uneven_streams(count=256, steps=1, seed=5)
+    data = []
+    for i, sp in enumerate(specs):
+        tn = sp.t_news[0]
+        T = sp.t_init + (warmup + steps + 1) * tn
+        Gc = synth.gaussian_cores(tuple(sp.dims) + (T,), sp.ranks, 7000 + i)
+        Xh = synth.add_noise(host_tr_tensor(Gc), synth.gaussian_tensor(tuple(sp.dims) + (T,), 7100 + i), BATCH_NOISE)
+        init = [g.copy() for g in Gc]
+        init[-1] = init[-1][:, :sp.t_init, :]
+        data.append((sp, tn, bf16_device(torch, Xh), init))
+    ctxs = [p.str_init_cores(init, X0=p.paper_layout(Xb[..., :sp.t_init]), compute="f32", sweeps=1, async_status=1,
+                             t_capacity=sp.t_init + (warmup + steps + 1) * tn) for sp, tn, Xb, init in data]
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    ms = []
+    with torch.cuda.stream(stream):
+        for j in range(warmup + steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p.str_update_batch(ctxs, [Xb[..., sp.t_init + j * tn:sp.t_init + (j + 1) * tn] for sp, tn, Xb, _ in data])
+            b.record(stream)
+            stream.synchronize()
+            if j >= warmup:
+                ms.append(a.elapsed_time(b))
+    launches = ctxs[0].stats()["kernel_launches"]
+    for c in ctxs:
+        c.close()
+    return {"evidence": "batch256", "ms_per_step": sum(ms) / len(ms), "gpu_launches_per_step": launches}
+
+
+def main_evidence(a):
+    import torch
+    import paper_2307_00719_gb300 as p
+    torch.cuda.set_device(0)
+    fn = {"stage1_r12": evidence_stage1_r12, "sampling_m1e6": evidence_sampling_m1e6,
+          "batch256": evidence_batch256}[a.evidence]
+    print(json.dumps(fn(p, torch)), flush=True)
+
+
 if __name__ == "__main__":
     args = args_parse()
-    if args.oracle_sample:
+    if args.evidence:
+        main_evidence(args)
+    elif args.oracle_sample:
         main_oracle_sample(args.oracle_sample)
     elif args.impl == "reference":
         main_reference(args)

@@ -273,7 +273,9 @@ void str_destroy(str_ctx* ctx);
  * pass over X (and the mask) gives the loss and, for the backward, the sums of
  * the masked residual against the suffix and prefix products, from which every
  * core gradient follows as a small MTTKRP; otherwise the residual is formed
- * in a scratch buffer first.  Results are reduced in a fixed order
+ * in a scratch buffer first.  The FP32 forward reconstructs each 128 x 128 tile
+ * of X on the tensor cores (TF32 with a 3-term split: FP32-accurate products);
+ * a device wait that gives up there makes the loss NaN.  Results are reduced in a fixed order
  * (deterministic for a given shape).  Scratch is library-owned (grow-only,
  * shared by all calls of the process): a host lock serialises the enqueueing,
  * and each call's stream first waits for the previous call's last use of the

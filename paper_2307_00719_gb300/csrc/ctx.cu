@@ -3082,6 +3082,20 @@ static str_status loss_fwd_body(int N, const int64_t* dims, const int* ranks, st
   TRY(ws_grow(0, (size_t)rows * K * es));
   TRY(ws_grow(1, (size_t)cols * K * es));
   LossPlan pl;
+  if (ks > 0 && t.compute == 1 && loss_fwd_tc_supported(rows, cols, K)) {
+    // FP32: the tile reconstructions on the tensor cores, one pass over X
+    const int nbl = loss_fwd_tc_blocks(rows, cols);
+    TRY(ws_grow(2, (size_t)(nbl + 1) * 8 + 64));
+    TRY(ws_grow(3, loss_fwd_tc_split_bytes(rows, cols)));
+    STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, 0, kp - 1, 0, 0, g_loss_ws[0].p, s));
+    STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, kp, N - 1, 0, 1, g_loss_ws[1].p, s));
+    double* part = (double*)g_loss_ws[2].p;
+    STR_CUDA_TRY(launch_loss_fwd_tc((const float*)g_loss_ws[0].p, (const float*)g_loss_ws[1].p, rows, cols, K,
+                                    (const float*)X_dev, mask_bits, (float*)g_loss_ws[3].p, part, s));
+    STR_CUDA_TRY(launch_sum_blocks(part, nbl, 1, part + nbl, 0.5, s));
+    STR_CUDA_TRY(cudaMemcpyAsync(loss_dev, part + nbl, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return STR_OK;
+  }
   if (ks > 0 && loss_pass_plan(t.compute, rows, cols, K, false, &pl)) {
     // one fused pass over X: per-CTA partial sums of r^2, summed in a fixed order
     const int64_t nbl = (int64_t)pl.nrg * pl.ncg;

@@ -174,6 +174,14 @@ struct LossPlan {
   size_t smem = 0;
 };
 bool loss_pass_plan(int compute, int64_t rows, int64_t cols, int K, bool bwd, LossPlan* pl);
+// masked-loss forward on the tensor cores (FP32 tables and X, K <= 64): per-CTA
+// partial sums of M (X - Lm Rm^T)^2 in loss_part[loss_fwd_tc_blocks()]; `split`
+// holds loss_fwd_tc_split_bytes() of TF32-split tables
+bool loss_fwd_tc_supported(int64_t rows, int64_t cols, int K);
+size_t loss_fwd_tc_split_bytes(int64_t rows, int64_t cols);
+int loss_fwd_tc_blocks(int64_t rows, int64_t cols);
+cudaError_t launch_loss_fwd_tc(const float* Lm, const float* Rm, int64_t rows, int64_t cols, int K, const float* X,
+                               const uint32_t* mask, float* split, double* loss_part, cudaStream_t s);
 cudaError_t launch_loss_pass(const void* Lm, const void* Rm, int compute, int64_t rows, int64_t cols, int K,
                              const void* X, const uint32_t* mask, const LossPlan& pl, bool bwd,
                              double* loss_part, void* Zpart, void* Wpart, cudaStream_t s);
