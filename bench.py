@@ -68,7 +68,7 @@ def args_parse(argv=None):
     ap.add_argument("--no-loss", action="store_true", help="skip the masked-loss row")
     ap.add_argument("--no-large", action="store_true", help="skip the 60^5 stand-in row")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--evidence", default=None, choices=["stage1_r12", "sampling_m1e6", "batch256"],
+    ap.add_argument("--evidence", default=None, choices=["stage1_r12", "sampling_m1e6", "batch256", "masked_loss"],
                     help="run one kernel-evidence workload (for ncu captures) and print its line")
     return ap.parse_args(argv)
 
@@ -975,12 +975,21 @@ def evidence_batch256(p, torch, steps=3, warmup=2):
     return {"evidence": "batch256", "ms_per_step": sum(ms) / len(ms), "gpu_launches_per_step": launches}
 
 
+def evidence_masked_loss(p, torch, steps=2, warmup=1):
+    """The masked-loss row alone (forward and backward on the 32^4 x 100 FP32
+    tensor), a few steps: for the launch list of the loss path."""
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    row = loss_rows(p, torch, flush, 0, {"hbm_gbs": measured_peak("hbm_gbs", 6800.0)[0]}, {}, steps=steps,
+                    warmup=warmup)
+    return {"evidence": "masked_loss", "ms_fwd": row["ms_fwd"], "ms_bwd": row["ms_bwd"], "loss": row["loss"]}
+
+
 def main_evidence(a):
     import torch
     import paper_2307_00719_gb300 as p
     torch.cuda.set_device(0)
     fn = {"stage1_r12": evidence_stage1_r12, "sampling_m1e6": evidence_sampling_m1e6,
-          "batch256": evidence_batch256}[a.evidence]
+          "batch256": evidence_batch256, "masked_loss": evidence_masked_loss}[a.evidence]
     print(json.dumps(fn(p, torch)), flush=True)
 
 
