@@ -2967,18 +2967,20 @@ static int loss_split(int N, const int64_t* dims, const int* R) {
 // problem in which a unit core stands for the other side's product:
 //   prefix modes: tensor Z(i_1..i_k, c), cores G_1..G_k, U;
 //   suffix modes: tensor W(c, i_{k+1}..i_N), cores V, G_{k+1}..G_N.
-static str_status loss_bwd_fused(int N, const int64_t* dims, const str_ctx& t, const LossPlan& pl,
+// tc: Z and W by the two tensor-core passes (FP32; pl unused), else by the SIMT
+// fused pass with plan pl.
+static str_status loss_bwd_fused(int N, const int64_t* dims, const str_ctx& t, const LossPlan& pl, bool tc,
                                  const void* const* cores_dev, const void* X_dev, const uint32_t* mask_bits,
                                  double grad_scale, void* const* grad_cores_dev, int64_t rows, int64_t cols,
                                  int kp, int K, size_t es, cudaStream_t s) {
   const int xt = es == 8 ? XT_F64 : XT_F32;
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const int64_t nbl = (int64_t)pl.nrg * pl.ncg;
+  const int64_t nbl = tc ? 0 : (int64_t)pl.nrg * pl.ncg;
   size_t off[7];
   off[0] = 0;                                                          // loss partials
   off[1] = off[0] + al((size_t)nbl * 8);                              // Zpart
-  off[2] = off[1] + al((size_t)pl.ncg * rows * K * es);                // Wpart (nrg > 1)
-  off[3] = off[2] + (pl.nrg > 1 ? al((size_t)pl.nrg * cols * K * es) : 0);  // Zt
+  off[2] = off[1] + (tc ? 0 : al((size_t)pl.ncg * rows * K * es));     // Wpart (nrg > 1)
+  off[3] = off[2] + (!tc && pl.nrg > 1 ? al((size_t)pl.nrg * cols * K * es) : 0);  // Zt
   off[4] = off[3] + al((size_t)rows * K * es);                         // W
   off[5] = off[4] + al((size_t)cols * K * es);                         // U, V
   off[6] = off[5] + 2 * al((size_t)K * K * es);
@@ -3017,19 +3019,27 @@ static str_status loss_bwd_fused(int N, const int64_t* dims, const str_ctx& t, c
     args.push_back(a);
   }
   TRY(ws_grow(3, off[6]));
-  TRY(ws_grow(2, part_bytes + 64));
+  // slot 2: the tensor-core passes' split tables and partials, then the reduced
+  // MTTKRPs' partials (stream order separates the two uses)
+  TRY(ws_grow(2, std::max(part_bytes + 64, tc ? loss_bwd_tc_ws_bytes(rows, cols, K) : (size_t)0)));
   char* b3 = (char*)g_loss_ws[3].p;
   void* Zpart = b3 + off[1];
   void* Zt = b3 + off[3];
   void* W = b3 + off[4];
-  void* Wpart = pl.nrg > 1 ? (void*)(b3 + off[2]) : W;
+  void* Wpart = !tc && pl.nrg > 1 ? (void*)(b3 + off[2]) : W;
   void* U = b3 + off[5];
   void* V = b3 + off[5] + al((size_t)K * K * es);
   STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, 0, kp - 1, 0, 0, g_loss_ws[0].p, s));
   STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, kp, N - 1, 0, 1, g_loss_ws[1].p, s));
-  STR_CUDA_TRY(launch_loss_pass(g_loss_ws[0].p, g_loss_ws[1].p, t.compute, rows, cols, K, X_dev, mask_bits, pl, true,
-                                (double*)(b3 + off[0]), Zpart, Wpart, s));
-  STR_CUDA_TRY(launch_loss_reduce(Zpart, pl.ncg, rows, Wpart, pl.nrg, cols, K, t.compute, Zt, W, s));
+  if (tc) {
+    STR_CUDA_TRY(launch_loss_bwd_tc((const float*)g_loss_ws[0].p, (const float*)g_loss_ws[1].p, rows, cols, K,
+                                    (const float*)X_dev, mask_bits, (float*)g_loss_ws[2].p, (float*)Zt, (float*)W,
+                                    s));
+  } else {
+    STR_CUDA_TRY(launch_loss_pass(g_loss_ws[0].p, g_loss_ws[1].p, t.compute, rows, cols, K, X_dev, mask_bits, pl,
+                                  true, (double*)(b3 + off[0]), Zpart, Wpart, s));
+    STR_CUDA_TRY(launch_loss_reduce(Zpart, pl.ncg, rows, Wpart, pl.nrg, cols, K, t.compute, Zt, W, s));
+  }
   STR_CUDA_TRY(launch_unit_cores(t.R[0], t.R[kp], t.compute, U, V, s));
   for (int n = 0; n < N; ++n) {
     if (n < kp && kp == 1) {
@@ -3150,10 +3160,13 @@ static str_status loss_bwd_body(int N, const int64_t* dims, const int* ranks, st
   const size_t es = dtype == STR_F64 ? 8 : 4;
   TRY(ws_grow(0, (size_t)rows * K * es));
   TRY(ws_grow(1, (size_t)cols * K * es));
-  LossPlan pl;
-  if (ks > 0 && loss_pass_plan(t.compute, rows, cols, K, true, &pl)) return loss_bwd_fused(N, dims, t, pl, cores_dev, X_dev,
-                                                                                mask_bits, grad_scale, grad_cores_dev,
-                                                                                rows, cols, kp, K, es, s);
+  LossPlan pl{};
+  if (ks > 0 && t.compute == 1 && loss_fwd_tc_supported(rows, cols, K))
+    return loss_bwd_fused(N, dims, t, pl, true, cores_dev, X_dev, mask_bits, grad_scale, grad_cores_dev, rows, cols,
+                          kp, K, es, s);
+  if (ks > 0 && loss_pass_plan(t.compute, rows, cols, K, true, &pl))
+    return loss_bwd_fused(N, dims, t, pl, false, cores_dev, X_dev, mask_bits, grad_scale, grad_cores_dev, rows, cols,
+                          kp, K, es, s);
   TRY(ws_grow(3, (size_t)count * es));
   STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, 0, kp - 1, 0, 0, g_loss_ws[0].p, s));
   STR_CUDA_TRY(launch_chain_table(cores_dev, t.compute, t.R, N, dims, kp, N - 1, 0, 1, g_loss_ws[1].p, s));

@@ -1258,6 +1258,8 @@ EncodeTiledFn encode_fn() {
 
 }  // namespace
 
+void* str_tensor_map_encoder() { return (void*)encode_fn(); }
+
 bool tc_supported(int K, int xtype, const void* base) {
   const int es = xtype == XT_BF16 ? 2 : 4;
   if (xtype != XT_BF16 && xtype != XT_F32) return false;

@@ -182,6 +182,15 @@ size_t loss_fwd_tc_split_bytes(int64_t rows, int64_t cols);
 int loss_fwd_tc_blocks(int64_t rows, int64_t cols);
 cudaError_t launch_loss_fwd_tc(const float* Lm, const float* Rm, int64_t rows, int64_t cols, int K, const float* X,
                                const uint32_t* mask, float* split, double* loss_part, cudaStream_t s);
+// masked-loss backward contractions on the tensor cores (same support as the
+// forward): Zt[k][row] = sum_c R(row, c) Rm[c][k] and W[c][k] = sum_row R(row, c)
+// Lm[row][k] of R = M .* (X - Lm Rm^T), by two passes over X; ws holds
+// loss_bwd_tc_ws_bytes() (split tables and per-CTA partials)
+size_t loss_bwd_tc_ws_bytes(int64_t rows, int64_t cols, int K);
+// the driver's cuTensorMapEncodeTiled, resolved once through the runtime (null if absent)
+void* str_tensor_map_encoder();
+cudaError_t launch_loss_bwd_tc(const float* Lm, const float* Rm, int64_t rows, int64_t cols, int K, const float* X,
+                               const uint32_t* mask, float* ws, float* Zt, float* W, cudaStream_t s);
 cudaError_t launch_loss_pass(const void* Lm, const void* Rm, int compute, int64_t rows, int64_t cols, int K,
                              const void* X, const uint32_t* mask, const LossPlan& pl, bool bwd,
                              double* loss_part, void* Zpart, void* Wpart, cudaStream_t s);

@@ -65,12 +65,19 @@ def test_autograd_function():
 
 # Shapes for the fused loss pass: ragged 64-row / 64-column tiles, a prefix of one
 # core (order 3 and order 4), a two-core prefix of 1600 rows over 9 columns (many
-# row groups, one column block), and a mid-size order-5 tensor.
+# row groups, one column block), and a mid-size order-5 tensor.  For the FP32
+# tensor-core passes (128 x 128 tiles): K = R_1 R_2 = 64 over 260 rows and 792
+# columns (three row tiles, seven column tiles, ragged); K = 36 over 131 rows (an
+# odd row count: unaligned columns of X) and 1050 columns; and 4096 rows over 2304
+# columns (576 tiles: each CTA walks several tiles and lane tiles).
 @pytest.mark.parametrize("dims,ranks", [
     ((70, 9, 13), (2, 3, 4)),
     ((31, 33, 5, 7), (3, 2, 4, 3)),
     ((40, 40, 3, 3), (2, 8, 2, 2)),
     ((16, 16, 16, 16, 12), (4, 4, 4, 4, 4)),
+    ((260, 24, 33), (8, 8, 3)),
+    ((131, 7, 150), (6, 6, 5)),
+    ((64, 64, 48, 48), (3, 2, 3, 2)),
 ])
 @pytest.mark.parametrize("dtype_name,tol", [("f64", 1e-12), ("f32", 1e-5)])
 def test_masked_loss_tiles_and_groups(dims, ranks, dtype_name, tol):
