@@ -547,15 +547,18 @@ __global__ void __launch_bounds__(256, 1) loss_bwd_tc_kernel(
 // ---------------------------------------------------------------------------
 // Warp-specialised form of the two backward passes (X 16-byte aligned with a
 // prefix row count that is a multiple of 4): 128 x 64 tiles (lanes x o) through
-// a two-stage shared-memory ring and two TMEM buffers.
+// two two-stage shared-memory rings and two TMEM buffers.  Ring A (the operand
+// rows and the X tile) is refilled once the epilogue has read its X tile (which
+// also means P is done); ring G (the G operand) once G is done, so the refill
+// of the next tiles' X does not wait for the G MMAs.
 //   warp 0 (producer): per tile, TMA loads of the other side's operand rows (64
 //     rows of B hi / lo), of the G operand (KG rows x 64 o of BT hi / lo; both
 //     128-byte swizzled, K-major: the tensor cores take TF32 operands K-major
 //     only) and of the X tile (one box of 128 rows x 64 columns for the Z pass;
 //     two 128-byte-swizzled boxes of 32 rows x 128 columns for the W pass, so
 //     that a lane's 16-byte reads of its column are conflict-free), all completing
-//     on the stage's full barrier; and an L2 prefetch of the X tile two tiles
-//     ahead.
+//     on the stage's full barriers (A: rows and X; G: the G operand); and an L2
+//     prefetch of the X tile two tiles ahead.
 //   warp 1 (MMA, one thread): P(t) = A B^T into TMEM buffer t % 2 (A = the
 //     lane-side rows, held in TMEM for the lane tile); G(t) = r(t) B from the G
 //     operand, accumulated in TMEM over the CTA's tiles of a lane tile.  Each is
@@ -571,8 +574,8 @@ constexpr int kWT = 64;                   // o-columns per tile
 constexpr int kWsBP = 32768;              // B operand: (hi, lo) x 2 chunks x (64 rows x 128 B)
 constexpr int kWsG = 32768;               // G operand: (hi, lo) x 2 chunks x (KG <= 64 rows x 128 B)
 constexpr int kWsX = 32768;               // X tile, 128 x 64 FP32
-constexpr int kWsStage = kWsBP + kWsG + kWsX;
-constexpr int kWsNS = 2;                  // ring stages
+constexpr int kWsA = kWsBP + kWsX;        // ring A stage
+constexpr int kWsNS = 2;                  // stages of each ring (= TMEM buffers)
 
 template <bool ZSIDE>
 __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
@@ -584,11 +587,13 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
   PDL_ENTRY();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + kWsNS * kWsStage);
-  uint64_t* full = bars;              // [kWsNS] producer -> MMA, epilogue (operands and X landed)
-  uint64_t* empty = bars + 3;         // [kWsNS] MMA -> producer (G(t) done: the stage is free)
+  unsigned char* ringG = smem + kWsNS * kWsA;
+  uint64_t* bars = (uint64_t*)(ringG + kWsNS * kWsG);
+  uint64_t* full = bars;              // [2] producer -> MMA, epilogue (operand rows and X landed)
+  uint64_t* fullg = bars + 2;         // [2] producer -> MMA (G operand landed)
+  uint64_t* emptyg = bars + 4;        // [2] MMA -> producer (G(t) done: the G stage is free)
   uint64_t* pfull = bars + 6;         // [2] MMA -> epilogue (P(t) in its TMEM buffer)
-  uint64_t* rfull = bars + 8;         // [2] epilogue -> MMA (r(t) in its buffer), 256 arrivals
+  uint64_t* rfull = bars + 8;         // [2] epilogue -> MMA, producer (r(t) written, X(t) read), 256 arrivals
   uint64_t* tfree = bars + 10;        // [2] MMA -> MMA (G(t) done: its TMEM buffer is free)
   uint64_t* gdone = bars + 12;        // MMA -> epilogue (last G of a lane tile done)
   uint64_t* aready = bars + 13;       // epilogue -> MMA (lane-side rows in TMEM), 256 arrivals
@@ -598,11 +603,10 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
 
   if (warp == 1) tmem_alloc(tslot, 512);
   if (tid == 0) {
-    for (int b = 0; b < kWsNS; ++b) {
-      mbar_init(&full[b], 1);
-      mbar_init(&empty[b], 1);
-    }
     for (int b = 0; b < 2; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&fullg[b], 1);
+      mbar_init(&emptyg[b], 1);
       mbar_init(&pfull[b], 1);
       mbar_init(&rfull[b], 256);
       mbar_init(&tfree[b], 1);
@@ -637,26 +641,23 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
       for (int64_t t = t0; t < min(t1, t0 + kWsNS); ++t) prefetch_x(t);
     for (int64_t t = t0; t < t1; ++t) {
       const int64_t j = t - t0;
-      const int s = (int)(j % kWsNS);
-      const uint32_t n = (uint32_t)(j / kWsNS);
+      const int s = (int)(j & 1);
+      const uint32_t n = (uint32_t)(j >> 1);
+      // ring A: free once the epilogue of tile t - 2 has read its X
       if (j >= kWsNS) {
-        const bool ok = mbar_wait(&empty[s], (n - 1) & 1u, kWaitNs);
+        const bool ok = mbar_wait(&rfull[s], (n - 1) & 1u, kWaitNs);
         if (__any_sync(0xffffffffu, !ok) || *s_fail) { if (lane == 0) *s_fail = 1; break; }
       }
       const int64_t l0 = (t / nOT) * kLT, o0 = (t % nOT) * kWT;
-      unsigned char* st = smem + (size_t)s * kWsStage;
+      unsigned char* st = smem + (size_t)s * kWsA;
       if (lane == 0) {
-        mbar_expect_tx(&full[s], (uint32_t)(nch * 2 * 8192 + 2 * 2 * KG * 128 + kLT * kWT * 4));
+        mbar_expect_tx(&full[s], (uint32_t)(nch * 2 * 8192 + kLT * kWT * 4));
         for (int c = 0; c < nch; ++c) {
           tma_load_2d(st + c * 8192, &tmBh, &full[s], c * 32, (int)o0);
           tma_load_2d(st + 16384 + c * 8192, &tmBl, &full[s], c * 32, (int)o0);
         }
-        for (int c = 0; c < 2; ++c) {
-          tma_load_2d(st + kWsBP + c * KG * 128, &tmGh, &full[s], (int)o0 + 32 * c, 0);
-          tma_load_2d(st + kWsBP + 16384 + c * KG * 128, &tmGl, &full[s], (int)o0 + 32 * c, 0);
-        }
         // the X tile (X as a 2-D tensor [suffix columns][prefix rows]; zero past its edges)
-        unsigned char* sx = st + kWsBP + kWsG;
+        unsigned char* sx = st + kWsBP;
         if (ZSIDE) {
           tma_load_2d(sx, &tmX, &full[s], (int)l0, (int)o0);             // [64 o][128 rows], unswizzled
         } else {
@@ -664,6 +665,20 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
           tma_load_2d(sx + 16384, &tmX, &full[s], (int)o0 + 32, (int)l0);
         }
         if (t + kWsNS < t1) prefetch_x(t + kWsNS);
+      }
+      __syncwarp();
+      // ring G: free once G(t - 2) is done
+      if (j >= kWsNS) {
+        const bool ok = mbar_wait(&emptyg[s], (n - 1) & 1u, kWaitNs);
+        if (__any_sync(0xffffffffu, !ok) || *s_fail) { if (lane == 0) *s_fail = 1; break; }
+      }
+      if (lane == 0) {
+        unsigned char* sg = ringG + (size_t)s * kWsG;
+        mbar_expect_tx(&fullg[s], (uint32_t)(2 * 2 * KG * 128));
+        for (int c = 0; c < 2; ++c) {
+          tma_load_2d(sg + c * KG * 128, &tmGh, &fullg[s], (int)o0 + 32 * c, 0);
+          tma_load_2d(sg + 16384 + c * KG * 128, &tmGl, &fullg[s], (int)o0 + 32 * c, 0);
+        }
       }
       __syncwarp();
     }
@@ -687,15 +702,15 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
           const int64_t jp = tp - t0;
           const int64_t lt = tp / nOT;
           const bool new_lt = lt != lt_p;
-          const int s = (int)(jp % kWsNS), b = (int)(jp & 1);
+          const int s = (int)(jp & 1), b = s;
           bool can = !new_lt || tp == t0 || tg == tp;
           if (can && jp >= 2) can = mbar_try_wait(&tfree[b], (uint32_t)((jp >> 1) - 1) & 1u);
           if (can && new_lt) can = mbar_try_wait(aready, m & 1u);
-          if (can) can = mbar_try_wait(&full[s], (uint32_t)(jp / kWsNS) & 1u);
+          if (can) can = mbar_try_wait(&full[s], (uint32_t)(jp >> 1) & 1u);
           if (can) {
             if (new_lt) ++m;
             tc_fence_after();
-            const uint64_t bh = desc_sw128(smem + (size_t)s * kWsStage), bl = desc_sw128(smem + (size_t)s * kWsStage + 16384);
+            const uint64_t bh = desc_sw128(smem + (size_t)s * kWsA), bl = desc_sw128(smem + (size_t)s * kWsA + 16384);
             const uint32_t d = tmem + 128u * b;
             for (int k8 = 0; k8 < ksteps; ++k8) {
               const uint64_t adv = (uint64_t)((k8 >> 2) * 8192 + (k8 & 3) * 32) >> 4;
@@ -712,12 +727,12 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
         }
         if (tg < tp) {
           const int64_t jg = tg - t0;
-          const int s = (int)(jg % kWsNS), b = (int)(jg & 1);
-          if (mbar_try_wait(&rfull[b], (uint32_t)(jg >> 1) & 1u)) {
+          const int s = (int)(jg & 1), b = s;
+          if (mbar_try_wait(&rfull[b], (uint32_t)(jg >> 1) & 1u) && mbar_try_wait(&fullg[s], (uint32_t)(jg >> 1) & 1u)) {
             tc_fence_after();
             const bool first = tg == t0 || tg / nOT != (tg - 1) / nOT;
-            const uint64_t gh = desc_sw128(smem + (size_t)s * kWsStage + kWsBP);
-            const uint64_t gl = desc_sw128(smem + (size_t)s * kWsStage + kWsBP + 16384);
+            const uint64_t gh = desc_sw128(ringG + (size_t)s * kWsG);
+            const uint64_t gl = desc_sw128(ringG + (size_t)s * kWsG + 16384);
             for (int k8 = 0; k8 < kWT / 8; ++k8) {
               const uint64_t adv = (uint64_t)((k8 >> 2) * KG * 128 + (k8 & 3) * 32) >> 4;
               const uint32_t a_hi = tmem + 128u * b + 8u * k8, a_lo = a_hi + 64u;
@@ -725,7 +740,7 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
               mma_tf32_ts(tmem + 256, a_hi, gl + adv, idG, 1u);
               mma_tf32_ts(tmem + 256, a_lo, gh + adv, idG, 1u);
             }
-            mma_commit(&empty[s]);
+            mma_commit(&emptyg[s]);
             mma_commit(&tfree[b]);
             // the last G of its lane tile: the epilogue may read G out
             if (tg == t1 - 1 || (tg + 1) / nOT != tg / nOT) mma_commit(gdone);
@@ -768,7 +783,7 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
     };
     for (int64_t t = t0; t < t1; ++t) {
       const int64_t j = t - t0;
-      const int s = (int)(j % kWsNS), b = (int)(j & 1);
+      const int s = (int)(j & 1), b = s;
       const int64_t lt = t / nOT;
       const int64_t l0 = lt * kLT, o0 = (t % nOT) * kWT;
       const int no = (int)min((int64_t)kWT, nO - o0);
@@ -812,11 +827,11 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
           mword = (uint32_t)((((uint64_t)hi << 32) | lo) >> (b0 & 31));
         }
       }
-      const bool ok1 = mbar_wait(&full[s], (uint32_t)(j / kWsNS) & 1u, kWaitNs);
+      const bool ok1 = mbar_wait(&full[s], (uint32_t)(j >> 1) & 1u, kWaitNs);
       const bool ok2 = ok1 && mbar_wait(&pfull[b], (uint32_t)(j >> 1) & 1u, kWaitNs);
       if (__any_sync(0xffffffffu, !ok2) || *s_fail) { fail = true; break; }
       tc_fence_after();
-      const float* sX = (const float*)(smem + (size_t)s * kWsStage + kWsBP + kWsG);
+      const float* sX = (const float*)(smem + (size_t)s * kWsA + kWsBP);
       const uint32_t pb = tmem + tl + 128u * b;
 #pragma unroll
       for (int c0 = 0; c0 < 32; c0 += 16) {
@@ -1017,7 +1032,7 @@ cudaError_t launch_loss_bwd_tc(const float* Lm, const float* Rm, int64_t rows, i
         !map2d(&mRl, Rlo, 64, cols, kWT) || !map2d(&mLTh, LTh, ldr, KG, KG) || !map2d(&mLTl, LTl, ldr, KG, KG) ||
         !map2d(&mRTh, RTh, ldc, KG, KG) || !map2d(&mRTl, RTl, ldc, KG, KG))
       return cudaErrorInvalidValue;
-    const size_t smw = 1024 + (size_t)kWsNS * kWsStage + 128;
+    const size_t smw = 1024 + (size_t)kWsNS * (kWsA + kWsG) + 128;
     e = cudaFuncSetAttribute(loss_bwd_ws_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(loss_bwd_ws_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
