@@ -269,13 +269,16 @@ void str_destroy(str_ctx* ctx);
  *   (device, core layout, same dtype): dL/dG_{n(2)} = -(M .* (X - TR(G)))_[n] G^{!=n}_[2]
  *   (with M == 1 this equals G_{n(2)} Q_n - P_n of Eq. partial).
  * Both recompute the subchains; nothing is stored between them.  With the
- * modes split into a prefix and a suffix such that K = R_1 R_{k+1} <= 64, one
- * pass over X (and the mask) gives the loss and, for the backward, the sums of
+ * modes split into a prefix and a suffix such that K = R_1 R_{k+1} <= 64, the
+ * loss takes one pass over X (and the mask), and the backward forms the sums of
  * the masked residual against the suffix and prefix products, from which every
  * core gradient follows as a small MTTKRP; otherwise the residual is formed
- * in a scratch buffer first.  The FP32 forward reconstructs each 128 x 128 tile
- * of X on the tensor cores (TF32 with a 3-term split: FP32-accurate products);
- * a device wait that gives up there makes the loss NaN.  Results are reduced in a fixed order
+ * in a scratch buffer first.  FP32: the forward reconstructs each 128 x 128 tile
+ * of X on the tensor cores (TF32 with a 3-term split), and the backward takes
+ * two passes over X, each reconstructing a tile, forming the residual and
+ * contracting it on the tensor cores without writing it to memory; FP64: one
+ * fused pass gives both sums.  A device wait that gives up makes the loss or
+ * the gradients NaN.  Results are reduced in a fixed order
  * (deterministic for a given shape).  Scratch is library-owned (grow-only,
  * shared by all calls of the process): a host lock serialises the enqueueing,
  * and each call's stream first waits for the previous call's last use of the
