@@ -889,6 +889,209 @@ __global__ void __launch_bounds__(320, 1) loss_bwd_ws_kernel(
   if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised forward (X 16-byte aligned with a prefix row count that is a
+// multiple of 4): sum M (X - P)^2 over 128 x 64 tiles (lanes = suffix columns,
+// o = prefix rows), three shared-memory stages and three TMEM buffers.
+//   warp 0 (producer): per tile, TMA loads of the 64 prefix rows of Lm (hi / lo)
+//     and of the X tile (two 128-byte-swizzled boxes of 32 rows x 128 columns),
+//     on the stage's full barrier; a stage is refilled once the epilogue is done
+//     with it.
+//   warp 1 (MMA, one thread): P(t) = Rm Lm^T into TMEM buffer t % 3 (the lane
+//     tile's Rm rows held in TMEM), once its stage has landed and the epilogue
+//     has read the buffer's previous tile.
+//   warps 2-9 (epilogue, one TMEM lane and 32 of the tile's o-columns per
+//     thread): the masked squared residuals, FP32 per tile and FP64 across
+//     tiles; at a lane-tile change, the new Rm rows into TMEM.
+// TMEM columns: P buffers 128 b .. 128 b + 127, b = 0..2 (hh | cross), Rm_hi
+// 384..447, Rm_lo 448..511.
+// ---------------------------------------------------------------------------
+constexpr int kFwNS = 3;
+constexpr int kFwStage = kWsBP + kWsX;
+
+__global__ void __launch_bounds__(320, 1) loss_fwd_ws_kernel(
+    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+    const __grid_constant__ CUtensorMap tmX, const float* __restrict__ Ahi, const float* __restrict__ Alo, int64_t nL,
+    int64_t nO, int K, int64_t xrows, const uint32_t* __restrict__ mask, int64_t nwords,
+    double* __restrict__ loss_part) {
+  PDL_ENTRY();
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + kFwNS * kFwStage);
+  uint64_t* full = bars;              // [3] producer -> MMA, epilogue
+  uint64_t* pfull = bars + 3;         // [3] MMA -> epilogue
+  uint64_t* rfree = bars + 6;         // [3] epilogue -> producer, MMA (stage and buffer read), 256 arrivals
+  uint64_t* aready = bars + 9;        // epilogue -> MMA (Rm rows in TMEM), 256 arrivals
+  uint32_t* tslot = (uint32_t*)(bars + 10);
+  volatile int* s_fail = (volatile int*)(tslot + 1);
+  __shared__ double red[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 1) tmem_alloc(tslot, 512);
+  if (tid == 0) {
+    for (int q = 0; q < kFwNS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&pfull[q], 1);
+      mbar_init(&rfree[q], 256);
+    }
+    mbar_init(aready, 256);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int64_t nLT = (nL + kLT - 1) / kLT, nOT = (nO + kWT - 1) / kWT, ntiles = nLT * nOT;
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(ntiles, t0 + per);
+  const int ksteps = (K + 7) / 8, nch = (K + 31) / 32;
+  double lsum = 0.0;
+
+  if (warp == 0) {
+    for (int64_t t = t0; t < t1; ++t) {
+      const int64_t j = t - t0;
+      const int s = (int)(j % kFwNS);
+      const uint32_t n = (uint32_t)(j / kFwNS);
+      if (j >= kFwNS) {
+        const bool ok = mbar_wait(&rfree[s], (n - 1) & 1u, kWaitNs);
+        if (__any_sync(0xffffffffu, !ok) || *s_fail) { if (lane == 0) *s_fail = 1; break; }
+      }
+      if (lane == 0) {
+        const int64_t l0 = (t / nOT) * kLT, o0 = (t % nOT) * kWT;
+        unsigned char* st = smem + (size_t)s * kFwStage;
+        mbar_expect_tx(&full[s], (uint32_t)(nch * 2 * 8192 + kLT * kWT * 4));
+        for (int c = 0; c < nch; ++c) {
+          tma_load_2d(st + c * 8192, &tmBh, &full[s], c * 32, (int)o0);
+          tma_load_2d(st + 16384 + c * 8192, &tmBl, &full[s], c * 32, (int)o0);
+        }
+        tma_load_2d(st + kWsBP, &tmX, &full[s], (int)o0, (int)l0);
+        tma_load_2d(st + kWsBP + 16384, &tmX, &full[s], (int)o0 + 32, (int)l0);
+      }
+      __syncwarp();
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idP = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kWT >> 3) << 17) | ((uint32_t)(kLT >> 4) << 24);
+      int64_t lt_p = -1;
+      uint32_t m = 0;
+      bool fail = false;
+      for (int64_t t = t0; t < t1; ++t) {
+        const int64_t j = t - t0;
+        const int s = (int)(j % kFwNS);
+        const uint32_t n = (uint32_t)(j / kFwNS);
+        const int64_t lt = t / nOT;
+        bool ok = true;
+        if (lt != lt_p) { ok = mbar_wait(aready, m & 1u, kWaitNs); ++m; }
+        if (ok && j >= kFwNS) ok = mbar_wait(&rfree[s], (n - 1) & 1u, kWaitNs);
+        if (ok) ok = mbar_wait(&full[s], n & 1u, kWaitNs);
+        if (!ok || *s_fail) { fail = true; break; }
+        tc_fence_after();
+        const uint64_t bh = desc_sw128(smem + (size_t)s * kFwStage), bl = desc_sw128(smem + (size_t)s * kFwStage + 16384);
+        const uint32_t d = tmem + 128u * s;
+        for (int k8 = 0; k8 < ksteps; ++k8) {
+          const uint64_t adv = (uint64_t)((k8 >> 2) * 8192 + (k8 & 3) * 32) >> 4;
+          const uint32_t a_hi = tmem + 384u + 8u * k8, a_lo = tmem + 448u + 8u * k8;
+          mma_tf32_ts(d, a_hi, bh + adv, idP, k8 > 0 ? 1u : 0u);
+          mma_tf32_ts(d + 64u, a_hi, bl + adv, idP, k8 > 0 ? 1u : 0u);
+          mma_tf32_ts(d + 64u, a_lo, bh + adv, idP, 1u);
+        }
+        mma_commit(&pfull[s]);
+        lt_p = lt;
+      }
+      if (fail) *s_fail = 1;
+    }
+  } else {
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const int li = 32 * quarter + lane;
+    const uint32_t tl = (uint32_t)(32 * quarter) << 16;
+    const int ka = 8 * ksteps;
+    bool fail = false;
+    int64_t cur_lt = -1;
+    for (int64_t t = t0; t < t1; ++t) {
+      const int64_t j = t - t0;
+      const int s = (int)(j % kFwNS);
+      const uint32_t n = (uint32_t)(j / kFwNS);
+      const int64_t lt = t / nOT;
+      const int64_t l0 = lt * kLT, o0 = (t % nOT) * kWT;
+      const int no = (int)min((int64_t)kWT, nO - o0);
+      const bool lane_ok = l0 + li < nL;
+      if (lt != cur_lt) {
+        // every P of the previous lane tile is done (this thread waited for it)
+        const float* ar = (half == 0 ? Ahi : Alo) + (l0 + li) * 64;
+        for (int c0 = 0; c0 < ka; c0 += 16) {
+          uint32_t v[16];
+#pragma unroll
+          for (int u = 0; u < 16; u += 4) {
+            const float4 q = lane_ok ? *(const float4*)(ar + c0 + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[u] = __float_as_uint(q.x); v[u + 1] = __float_as_uint(q.y);
+            v[u + 2] = __float_as_uint(q.z); v[u + 3] = __float_as_uint(q.w);
+          }
+          tmem_st_x16(tmem + tl + (half == 0 ? 384u : 448u) + (uint32_t)c0, v);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(aready);
+        cur_lt = lt;
+      }
+      uint32_t mword = 0xFFFFFFFFu;   // bit u = row o0 + 32 half + u of this lane's column
+      if (mask) {
+        const int64_t b0 = o0 + 32 * half + xrows * (l0 + li), w = b0 >> 5;
+        const uint32_t lo = (lane_ok && w < nwords) ? mask[w] : 0u;
+        const uint32_t hi = (lane_ok && w + 1 < nwords) ? mask[w + 1] : 0u;
+        mword = (uint32_t)((((uint64_t)hi << 32) | lo) >> (b0 & 31));
+      }
+      const bool ok1 = mbar_wait(&full[s], n & 1u, kWaitNs);
+      const bool ok2 = ok1 && mbar_wait(&pfull[s], n & 1u, kWaitNs);
+      if (__any_sync(0xffffffffu, !ok2) || *s_fail) { fail = true; break; }
+      tc_fence_after();
+      const unsigned char* xrow = smem + (size_t)s * kFwStage + kWsBP + half * 16384 + li * 128;
+      const uint32_t pb = tmem + tl + 128u * s;
+      float ts = 0.f;
+#pragma unroll
+      for (int c0 = 0; c0 < 32; c0 += 16) {
+        const int cb = 32 * half + c0;
+        uint32_t vh[16], vx[16];
+        tmem_ld_x16_nw(pb + (uint32_t)cb, vh);
+        tmem_ld_x16_nw(pb + 64u + (uint32_t)cb, vx);
+        float xv[16];
+#pragma unroll
+        for (int u = 0; u < 16; u += 4) {
+          const int unit = (c0 + u) >> 2;
+          const float4 q = *(const float4*)(xrow + ((unit ^ (li & 7)) << 4));
+          xv[u] = q.x; xv[u + 1] = q.y; xv[u + 2] = q.z; xv[u + 3] = q.w;
+        }
+        const uint32_t mb = (mword >> c0) & 0xFFFFu;
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const float p = __uint_as_float(vh[u]) + __uint_as_float(vx[u]);
+          const bool keep = lane_ok && (cb + u < no) && ((mb >> u) & 1u);
+          const float r = keep ? xv[u] - p : 0.f;
+          ts = fmaf(r, r, ts);
+        }
+      }
+      lsum += (double)ts;
+      tc_fence_before();
+      mbar_arrive(&rfree[s]);
+    }
+    if (fail) *s_fail = 1;
+  }
+  // fixed-order block sum of the epilogue threads' partials
+#pragma unroll
+  for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  tc_fence_before();
+  __syncthreads();
+  if (warp >= 2 && lane == 0) red[warp - 2] = lsum;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < 8; ++w) tot += red[w];
+    loss_part[blockIdx.x] = *s_fail ? (double)NAN : tot;
+  }
+  if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
 // out = sum over the CTAs that covered each lane tile (in CTA order) of their
 // partial: out[l * K + k] (W) or out[k * nL + l] (Z, transposed)
 __global__ void loss_bwd_tc_reduce_kernel(const float* __restrict__ part, int64_t nL, int64_t nOT, int64_t per,
@@ -927,6 +1130,10 @@ BwdPlan bwd_plan(int64_t nL, int64_t nO, int ow) {
 
 }  // namespace
 
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
 bool loss_fwd_tc_supported(int64_t rows, int64_t cols, int K) { return K >= 1 && K <= 64 && rows >= 1 && cols >= 1; }
 
 size_t loss_fwd_tc_split_bytes(int64_t rows, int64_t cols) { return (size_t)(rows + cols) * 64 * 2 * sizeof(float); }
@@ -948,19 +1155,41 @@ cudaError_t launch_loss_fwd_tc(const float* Lm, const float* Rm, int64_t rows, i
   const unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cols * 64 + 255) / 256, 152 * 8));
   launch_k(loss_split_kernel, gl, 256, 0, s, Lm, rows, K, Lhi, Llo);
   launch_k(loss_split_kernel, gr, 256, 0, s, Rm, cols, K, Rhi, Rlo);
+  const int vec = (rows % 4 == 0 && ((uintptr_t)X & 15) == 0) ? 1 : 0;
+  const int64_t nwords = (rows * cols + 31) / 32;
+  EncodeFn enc = (EncodeFn)str_tensor_map_encoder();
+  if (vec && enc && rows < INT32_MAX && cols < INT32_MAX && K <= 64) {
+    // warp-specialised form: the Lm rows and the X tiles by TMA (same grid, so the
+    // same number of partial sums)
+    auto map2d = [&](CUtensorMap* tm, const float* base, int64_t inner, int64_t outer, uint32_t bi, uint32_t bo,
+                     bool swz) {
+      cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+      cuuint64_t gstride[1] = {(cuuint64_t)inner * 4};
+      cuuint32_t box[2] = {bi, bo};
+      cuuint32_t estr[2] = {1, 1};
+      return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstride, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    CUtensorMap mLh, mLl, mX;
+    if (!map2d(&mLh, Lhi, 64, rows, 32, kWT, true) || !map2d(&mLl, Llo, 64, rows, 32, kWT, true) ||
+        !map2d(&mX, X, rows, cols, 32, 128, true))
+      return cudaErrorInvalidValue;
+    const size_t smf = 1024 + (size_t)kFwNS * kFwStage + 128;
+    cudaError_t e = cudaFuncSetAttribute(loss_fwd_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
+    if (e != cudaSuccess) return e;
+    launch_k(loss_fwd_ws_kernel, (unsigned)loss_fwd_tc_blocks(rows, cols), 320, smf, s, mLh, mLl, mX,
+             (const float*)Rhi, (const float*)Rlo, cols, rows, K, rows, mask, nwords, loss_part);
+    return cudaGetLastError();
+  }
   const size_t smem = 1024 + 8 * (size_t)kChunkBytes + (size_t)kLT * kXS * sizeof(float) + 64;
   cudaError_t e = cudaFuncSetAttribute(loss_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int vec = (rows % 4 == 0 && ((uintptr_t)X & 15) == 0) ? 1 : 0;
-  const int64_t nwords = (rows * cols + 31) / 32;
   launch_k(loss_fwd_tc_kernel, (unsigned)loss_fwd_tc_blocks(rows, cols), 128, smem, s, (const float*)Rhi,
            (const float*)Rlo, (const float*)Lhi, (const float*)Llo, rows, cols, K, X, mask, nwords, vec, loss_part);
   return cudaGetLastError();
 }
 
-typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 static int64_t round4(int64_t v) { return (v + 3) / 4 * 4; }
 static int kg_of(int K) { return (K + 15) / 16 * 16; }
 static size_t bwd_smem() {
