@@ -1512,6 +1512,35 @@ str_status ws_release(cudaStream_t s, bool capturing) {
   return STR_OK;
 }
 
+// side streams of the loss backward (per device, created on first use): the
+// reduced-trace MTTKRPs of the core gradients are independent and run
+// concurrently, forked from and joined back into the caller's stream by events
+constexpr int kLossSide = 4;
+struct LossSide {
+  int dev = -1;
+  cudaStream_t st[kLossSide] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kLossSide] = {};
+};
+LossSide g_loss_side[16];
+
+str_status loss_side(LossSide** out) {
+  int dev = 0;
+  STR_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 16) return STR_ERR_INVALID_ARG;
+  LossSide& ls = g_loss_side[dev];
+  if (ls.dev != dev) {
+    for (int i = 0; i < kLossSide; ++i) {
+      STR_CUDA_TRY(cudaStreamCreateWithFlags(&ls.st[i], cudaStreamNonBlocking));
+      STR_CUDA_TRY(cudaEventCreateWithFlags(&ls.join[i], cudaEventDisableTiming));
+    }
+    STR_CUDA_TRY(cudaEventCreateWithFlags(&ls.fork, cudaEventDisableTiming));
+    ls.dev = dev;
+  }
+  *out = &ls;
+  return STR_OK;
+}
+
 str_status ws_grow(int i, size_t bytes) {
   if (bytes <= g_loss_ws[i].cap) return STR_OK;
   if (g_loss_ws[i].p) cudaFree(g_loss_ws[i].p);
@@ -2986,9 +3015,10 @@ static str_status loss_bwd_fused(int N, const int64_t* dims, const str_ctx& t, c
   off[6] = off[5] + 2 * al((size_t)K * K * es);
   // the reduced MTTKRPs: arguments and the largest partial buffer, before any launch
   std::vector<MttkrpArgs> args;
+  std::vector<size_t> part_off;
   size_t part_bytes = 0;
   for (int n = 0; n < N; ++n) {
-    if (n < kp && kp == 1) { args.emplace_back(); continue; }
+    if (n < kp && kp == 1) { args.emplace_back(); part_off.push_back(0); continue; }
     MttkrpArgs a;
     a.xtype = xt;
     a.compute = t.compute;
@@ -3015,7 +3045,8 @@ static str_status loss_bwd_fused(int N, const int64_t* dims, const str_ctx& t, c
     const int64_t per = std::max<int64_t>(64, (J * gx + 303) / 304);
     a.fib_per_split = per;
     a.splits = (int)((J + per - 1) / per);
-    part_bytes = std::max(part_bytes, (size_t)a.splits * a.dim[a.n] * a.R[a.n] * a.R[a.n + 1] * es);
+    part_off.push_back(part_bytes);   // each mode its own partials: the modes run concurrently
+    part_bytes += al((size_t)a.splits * a.dim[a.n] * a.R[a.n] * a.R[a.n + 1] * es);
     args.push_back(a);
   }
   TRY(ws_grow(3, off[6]));
@@ -3041,19 +3072,35 @@ static str_status loss_bwd_fused(int N, const int64_t* dims, const str_ctx& t, c
     STR_CUDA_TRY(launch_loss_reduce(Zpart, pl.ncg, rows, Wpart, pl.nrg, cols, K, t.compute, Zt, W, s));
   }
   STR_CUDA_TRY(launch_unit_cores(t.R[0], t.R[kp], t.compute, U, V, s));
+  // the core gradients: mode n on the caller's stream (n = 0) or a side stream
+  LossSide* ls = nullptr;
+  TRY(loss_side(&ls));
+  STR_CUDA_TRY(cudaEventRecord(ls->fork, s));
+  bool used[kLossSide] = {};
   for (int n = 0; n < N; ++n) {
+    const int side = n == 0 ? -1 : (n - 1) % kLossSide;
+    cudaStream_t ss = side < 0 ? s : ls->st[side];
+    if (side >= 0 && !used[side]) {
+      STR_CUDA_TRY(wait_event(ss, ls->fork));
+      used[side] = true;
+    }
     if (n < kp && kp == 1) {
-      STR_CUDA_TRY(launch_prefix1_grad(Zt, dims[0], K, grad_scale, t.compute, grad_cores_dev[0], s));
+      STR_CUDA_TRY(launch_prefix1_grad(Zt, dims[0], K, grad_scale, t.compute, grad_cores_dev[0], ss));
       continue;
     }
     MttkrpArgs a = args[n];
     if (n < kp) { a.X = Zt; a.core[kp] = U; }
     else { a.X = W; a.core[0] = V; }
-    a.partial = g_loss_ws[2].p;
-    STR_CUDA_TRY(launch_mttkrp(a, s));
+    a.partial = (char*)g_loss_ws[2].p + part_off[n];
+    STR_CUDA_TRY(launch_mttkrp(a, ss));
     STR_CUDA_TRY(launch_reduce_partials_to(a.partial, t.compute, a.splits, a.dim[a.n] * a.R[a.n] * a.R[a.n + 1],
-                                           -grad_scale, grad_cores_dev[n], xt, s));
+                                           -grad_scale, grad_cores_dev[n], xt, ss));
   }
+  for (int i = 0; i < kLossSide; ++i)
+    if (used[i]) {
+      STR_CUDA_TRY(cudaEventRecord(ls->join[i], ls->st[i]));
+      STR_CUDA_TRY(wait_event(s, ls->join[i]));
+    }
   return STR_OK;
 }
 
