@@ -277,8 +277,11 @@ void str_destroy(str_ctx* ctx);
  * of X on the tensor cores (TF32 with a 3-term split), and the backward takes
  * two passes over X, each reconstructing a tile, forming the residual and
  * contracting it on the tensor cores without writing it to memory; FP64: one
- * fused pass gives both sums.  A device wait that gives up makes the loss or
- * the gradients NaN.  Results are reduced in a fixed order
+ * fused pass gives both sums.  The backward's per-core MTTKRPs run on
+ * library-owned streams, forked from and joined back into `stream` by events
+ * (under stream capture they become branches of the captured graph).  A device
+ * wait that gives up makes the loss or the gradients NaN.  Results are reduced
+ * in a fixed order
  * (deterministic for a given shape).  Scratch is library-owned (grow-only,
  * shared by all calls of the process): a host lock serialises the enqueueing,
  * and each call's stream first waits for the previous call's last use of the
