@@ -98,3 +98,35 @@ def test_masked_loss_tiles_and_groups(dims, ranks, dtype_name, tol):
         gref = masked_loss_grad(X, G, mk)
         for n in range(len(dims)):
             assert rel(_abi_to_paper(grads[n], 0, 0), 0.5 * gref[n]) <= tol, n
+
+
+def test_loss_calls_replay_from_a_captured_graph():
+    """The FP32 tensor-core forward and backward captured into a CUDA graph on a
+    side stream (after one eager call has grown the library's workspace): the
+    backward's per-core MTTKRPs on the library's side streams become branches of
+    the graph, and a replay gives the eager results bit for bit (fixed-order
+    reductions)."""
+    import torch
+    p = lib()
+    dims, ranks = (16, 16, 16, 16, 12), (4, 4, 4, 4, 4)
+    G = synth.gaussian_cores(dims, ranks, 21)
+    X = synth.gaussian_tensor(dims, 22)
+    mask = synth.bernoulli_keep_mask(dims, 0.3, 23)
+    bits = torch.from_numpy(synth.pack_mask_bits(mask).view(np.int32)).cuda()
+    cores = _abi_cores(G, torch.float32)
+    Xd = dev(X, torch.float32)
+    ref_loss = p.tr_masked_loss_fwd(cores, Xd, bits).item()
+    ref_grads = [g.clone() for g in p.tr_masked_loss_bwd(cores, Xd, bits, 1.0)]
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        loss = p.tr_masked_loss_fwd(cores, Xd, bits)
+        grads = p.tr_masked_loss_bwd(cores, Xd, bits, 1.0)
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        assert loss.item() == ref_loss
+        for g, r in zip(grads, ref_grads):
+            assert torch.equal(g, r)
+    assert abs(ref_loss - masked_loss(X, G, mask)) <= 1e-5 * ref_loss
