@@ -20,7 +20,10 @@ struct ChainArgs {
   int R[STR_MAXN + 1];
 };
 
-template <typename T>
+// RM: a bound on every rank of the chain (the register rows and the unrolled
+// loops are RM long; the sums run over the true ranks in the same order for any
+// RM, so the result does not depend on it)
+template <typename T, int RM>
 __global__ void chain_table_kernel(ChainArgs ca, int k0, int k1, int transpose, int64_t J,
                                    T* __restrict__ table) {
   PDL_ENTRY();
@@ -30,7 +33,7 @@ __global__ void chain_table_kernel(ChainArgs ca, int k0, int k1, int transpose, 
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / Rf;
     const int r = (int)(e % Rf);
-    T v[STR_MAXR], w[STR_MAXR];
+    T v[RM], w[RM];
     int64_t rem = j;
     // first factor: row r of G_{k0}(i_{k0})
     int cols = ca.R[k0 + 1];
@@ -39,7 +42,7 @@ __global__ void chain_table_kernel(ChainArgs ca, int k0, int k1, int transpose, 
       rem /= ca.dim[k0];
       const T* g = (const T*)ca.core[k0] + i * (int64_t)Rf * cols;
 #pragma unroll
-      for (int c = 0; c < STR_MAXR; ++c) v[c] = (c < cols) ? g[r + Rf * c] : (T)0;
+      for (int c = 0; c < RM; ++c) v[c] = (c < cols) ? g[r + Rf * c] : (T)0;
     }
     for (int k = k0 + 1; k <= k1; ++k) {
       const int64_t i = rem % ca.dim[k];
@@ -47,17 +50,17 @@ __global__ void chain_table_kernel(ChainArgs ca, int k0, int k1, int transpose, 
       const int Rk = ca.R[k], Rk1 = ca.R[k + 1];
       const T* g = (const T*)ca.core[k] + i * (int64_t)Rk * Rk1;
 #pragma unroll
-      for (int c = 0; c < STR_MAXR; ++c) {
+      for (int c = 0; c < RM; ++c) {
         T s = 0;
         if (c < Rk1) {
 #pragma unroll
-          for (int x = 0; x < STR_MAXR; ++x)
+          for (int x = 0; x < RM; ++x)
             if (x < Rk) s += v[x] * g[x + Rk * c];
         }
         w[c] = s;
       }
 #pragma unroll
-      for (int c = 0; c < STR_MAXR; ++c) v[c] = w[c];
+      for (int c = 0; c < RM; ++c) v[c] = w[c];
       cols = Rk1;
     }
     T* out = table + j * (int64_t)Rf * Rl;
@@ -114,8 +117,16 @@ cudaError_t launch_chain_table(const void* const* cores, int compute, const int*
   ChainArgs ca;
   for (int k = 0; k < STR_MAXN; ++k) { ca.core[k] = k < N ? cores[k] : nullptr; ca.dim[k] = k < N ? dims[k] : 1; }
   for (int k = 0; k <= STR_MAXN; ++k) ca.R[k] = k <= N ? R[k] : 1;
-  if (compute == 2) launch_k(chain_table_kernel<double>, blocks, 128, 0, s, ca, k0, k1, transpose, J, (double*)table);
-  else launch_k(chain_table_kernel<float>, blocks, 128, 0, s, ca, k0, k1, transpose, J, (float*)table);
+  int rmax = 1;
+  for (int k = k0; k <= k1 + 1; ++k) rmax = std::max(rmax, R[k]);
+  if (rmax <= 8) {
+    if (compute == 2) launch_k(chain_table_kernel<double, 8>, blocks, 128, 0, s, ca, k0, k1, transpose, J, (double*)table);
+    else launch_k(chain_table_kernel<float, 8>, blocks, 128, 0, s, ca, k0, k1, transpose, J, (float*)table);
+  } else {
+    if (compute == 2)
+      launch_k(chain_table_kernel<double, STR_MAXR>, blocks, 128, 0, s, ca, k0, k1, transpose, J, (double*)table);
+    else launch_k(chain_table_kernel<float, STR_MAXR>, blocks, 128, 0, s, ca, k0, k1, transpose, J, (float*)table);
+  }
   return cudaGetLastError();
 }
 
