@@ -1,27 +1,30 @@
-// Masked TR fit loss, forward, on the 5th-generation tensor cores (FP32 data).
+// Masked TR fit loss and its backward on the 5th-generation tensor cores
+// (FP32 data).
 //
 // With the modes split into a prefix (rows) and a suffix (columns), every entry
 // of the tensor ring is a dot product of two chain-table rows:
 //     TR(G)(r, c) = sum_k Lm[r][k] Rm[c][k],   K = R_1 R_{k+1} <= 64,
-// so the reconstruction of a 128-column x 128-row tile is one small GEMM
-//     P[c][r] = sum_k Rm[c][k] Lm[r][k]
-// (M = 128 columns, N = 128 rows, K padded to 8) on tcgen05.mma kind::tf32 with
-// the accumulator in TMEM.  FP32 accuracy comes from the 3-term split used by
-// the MTTKRP: Rm = Rm_hi + Rm_lo, Lm = Lm_hi + Lm_lo (each rounded to the
-// nearest TF32), P = Rm_hi Lm_hi + (Rm_hi Lm_lo + Rm_lo Lm_hi), the two groups
-// in separate TMEM columns.  Per tile, the operand tiles are staged, then every
-// thread issues asynchronous 16-byte copies of its column's 128 rows of X
-// (contiguous: X(r, c) at r + rows c) into a padded shared-memory tile, which
-// stay in flight while the MMAs run; the epilogue
-// thread that owns column c (its TMEM lane) then reads X from shared memory
-// (rows padded to 132 floats: conflict-free 16-byte reads) with its column's
-// mask bits, and accumulates sum M (X - P)^2.  One persistent CTA per SM walks
-// a contiguous range of tiles (column tile outer, so the Rm operand is staged
-// once per column tile).  Loss = 1/2 sum of the per-CTA partial sums (fixed
-// order).
+// so the reconstruction of a tile is one small GEMM on tcgen05.mma kind::tf32
+// with the accumulator in TMEM.  FP32 accuracy comes from the 3-term split used
+// by the MTTKRP: Rm = Rm_hi + Rm_lo, Lm = Lm_hi + Lm_lo (each rounded to the
+// nearest TF32), P = Rm_hi Lm_hi + (Rm_hi Lm_lo + Rm_lo Lm_hi), the two groups in
+// separate TMEM columns.  The loss is 1/2 sum M (X - P)^2; the backward needs
+// W = R^T Lm and Z = R Rm of the masked residual R = M (X - P), from which every
+// core gradient follows as a small MTTKRP (in the caller).
+//
+// Kernels (each walks a contiguous range of tiles per persistent CTA and sums in
+// a fixed order):
+//   loss_fwd_ws_kernel       forward, warp-specialised (TMA producer warp, MMA
+//                            warp, eight epilogue warps), X by TMA
+//   loss_bwd_ws_kernel<Z/W>  the two backward passes, warp-specialised, the
+//                            residual kept in TMEM as the A operand of G = r B
+//   loss_fwd_tc_kernel       forward for X that TMA cannot address (unaligned,
+//                            odd prefix row count): X copied asynchronously
+//                            into padded shared memory, one 128-thread CTA
+//   loss_bwd_tc_kernel<Z/W>  the backward passes for such X, X through registers
 //
 // A wait that times out (an mbarrier never completing) makes the CTA's partial
-// sum NaN, so the loss reads NaN instead of the kernel hanging.
+// sums NaN, so the loss or the gradients read NaN instead of the kernel hanging.
 #include <algorithm>
 #include <cmath>
 
@@ -67,6 +70,14 @@ __device__ __forceinline__ void stage_tile(unsigned char* sh, unsigned char* sl,
   }
 }
 
+// loss_fwd_tc_kernel: 128-column x 128-row tiles (M = 128 columns, N = 128 rows,
+// K padded to 8).  Per tile, the operand tiles are staged, then every thread
+// issues asynchronous copies of its column's 128 rows of X (contiguous: X(r, c)
+// at r + rows c) into a padded shared-memory tile, which stay in flight while the
+// MMAs run; the epilogue thread that owns column c (its TMEM lane) then reads X
+// from shared memory (rows padded to 132 floats: conflict-free 16-byte reads)
+// with its column's mask bits, and accumulates sum M (X - P)^2.  Column tile
+// outer, so the Rm operand is staged once per column tile.
 __global__ void __launch_bounds__(128, 1) loss_fwd_tc_kernel(const float* __restrict__ Rhi,
                                                              const float* __restrict__ Rlo,
                                                              const float* __restrict__ Lhi,
